@@ -1,0 +1,35 @@
+"""Named synthetic workloads (lattice, gauge-field recipe, right-hand sides, method
+parameters).  The paper's ensembles (Tables 1 and 2) are unavailable; these
+seeded fields stand in for them at c_sw = 1.0 (the value of Table 2), with the
+bare mass m0 chosen near the point where the smallest singular value of D
+reaches the stated target.
+
+``m0`` is the bare mass in D = 4 + m0 - (hopping)/2 + clover; it maps to the
+hopping parameter as m0 = 1/(2 kappa) - 4.
+"""
+
+WORKLOADS = {
+    # Plain method, FP64, two levels.
+    "8^4": dict(
+        dims=(8, 8, 8, 8), eps=0.3, gauge_seed=101, c_sw=1.0, m0=-0.25,
+        rhs="gaussian", rhs_seed=201, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(8,),
+        n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
+        precision="fp64"),
+    # Plain vs mixed precision, three levels.
+    "16^3x32": dict(
+        dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.55,
+        rhs="z2", rhs_seed=202, n_levels=3, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
+        n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
+        precision="fp16"),
+    # Multi-RHS: 12 spin-colour point sources.
+    "32^3x64": dict(
+        dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.7,
+        rhs="point12", rhs_seed=0, n_levels=3, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
+        n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
+        precision="bf16"),
+}
+
+
+def workload(name):
+    """A copy of the named workload's parameter dict."""
+    return dict(WORKLOADS[name])
