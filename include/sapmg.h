@@ -1,0 +1,193 @@
+/*
+ * sapmg.h -- C-ABI of the GB300 SAP-multilevel solver for the clover-improved
+ * Wilson-Dirac equation D z = b (Frommer, Kahl, Krieg, Leder, Rottmann,
+ * "Aggregation-based Multilevel Methods for Lattice QCD", Lattice 2011).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice dims (Lx, Ly, Lz, Lt), x fastest, periodic; the fermion field may be
+ * antiperiodic in t.  Every dim must be a multiple of 8 (an even number of
+ * 4^4 Schwarz blocks per direction, Sec. 2: two-colouring).
+ *
+ * Canonical layouts (what the caller passes unless MG_BLOCKED is set):
+ *   gauge  U : [V][mu = x,y,z,t][3][3] complex128, the forward links U_mu(x);
+ *   spinor   : [nrhs][V][spin 4][colour 3] complex (complex128 for MG_FP64,
+ *              complex64 otherwise), site = ((t*Lz + z)*Ly + y)*Lx + x;
+ *   coarse   : [nrhs][coarse site][2N] complex, coarse site canonical on the
+ *              lattice of aggregates, dof index chi*N + k (chirality chi of
+ *              gamma_5^c = diag(+1_N, -1_N), test vector k).
+ * Gamma matrices are in the chiral basis: gamma_k = [[0, -i s_k], [i s_k, 0]]
+ * (k = x, y, z), gamma_t = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1).
+ *
+ * Pointers: every field argument is a DEVICE pointer owned by the caller (for
+ * instance a torch tensor's data_ptr()), except where stated.  The library
+ * copies what it keeps; it never frees caller memory.  All work is issued on
+ * the stream given in mg_params.stream (NULL = legacy default stream) and is
+ * asynchronous unless stated; mg_solve synchronises.  A context is not
+ * thread-safe.
+ *
+ * Errors: 0 = MG_OK.  Negative codes are errors and leave outputs undefined;
+ * mg_last_error() returns a message.  MG_NOT_CONVERGED (positive) means the
+ * solve hit its iteration cap; the output holds the best iterate.
+ */
+#ifndef SAPMG_H
+#define SAPMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_OK 0
+#define MG_NOT_CONVERGED 1
+#define MG_ERR_ARG (-1)       /* null pointer, bad dims, unsupported option */
+#define MG_ERR_NONFINITE (-2) /* NaN or Inf in an input field */
+#define MG_ERR_OOM (-3)       /* device allocation failed */
+#define MG_ERR_CUDA (-4)      /* a CUDA call failed; see mg_last_error() */
+#define MG_ERR_TIMEOUT (-5)   /* a bounded device wait gave up */
+#define MG_ERR_STATE (-6)     /* the call needs a part the context was not set up with */
+
+/* Precisions.  MG_FP64: storage and arithmetic in binary64 (the plain form).
+ * MG_FP32 / MG_FP16 / MG_BF16: binary32 arithmetic with links, clover blocks,
+ * test vectors and coarse operators stored in that format (the mixed form).  */
+#define MG_FP64 0
+#define MG_FP32 1
+#define MG_FP16 2
+#define MG_BF16 3
+/* OR-ed into a prec argument: spinors are in the library's internal blocked
+ * layout (see mg_pack_spinor) instead of the canonical one. */
+#define MG_BLOCKED 0x100
+
+typedef struct mg_ctx mg_ctx;
+
+typedef struct {
+  int dims[4];              /* Lx, Ly, Lz, Lt; each a multiple of 8 */
+  int antiperiodic_t;       /* 1: fermion field antiperiodic in t */
+  int n_levels;             /* 1 (Schwarz-preconditioned FGMRES), 2 or 3 */
+  int agg2[4];              /* 3 levels: level-1 aggregate in coarse sites (default 2^4) */
+  int sap_block2[4];        /* 3 levels: level-1 Schwarz block in coarse sites (default 2^4) */
+  int n_vec[2];             /* test vectors N per non-coarsest level (Sec. 3) */
+  int setup_iters;          /* bootstrap part 1: smoother sweeps per level (Sec. 3) */
+  int n_mr;                 /* MR steps per Schwarz block solve (Sec. 2) */
+  int nu_post;              /* Schwarz sweeps per multilevel cycle */
+  int coarse_iters;         /* GMRES steps on the coarsest level (Sec. 4: 12) */
+  int inner_iters;          /* 3 levels: flexible GMRES steps on level 1 */
+  int fgmres_m;             /* outer restart length (Sec. 4: 25) */
+  double tol;               /* relative residual target (Sec. 4: 1e-10) */
+  int maxiter;              /* cap on preconditioned iterations per right-hand side */
+  int precision;            /* MG_FP64 (plain form) or MG_FP32 / MG_FP16 / MG_BF16 */
+  int nrhs_max;             /* right-hand sides solved together by mg_solve */
+  unsigned long long seed;  /* seed of the random initial test vectors */
+  void* stream;             /* cudaStream_t; NULL = default stream */
+  const double* init_vectors; /* optional device pointer: n_vec[0] canonical
+                                 complex128 fine fields used instead of the
+                                 random initial test vectors */
+  int verbose;
+} mg_params;
+
+typedef struct {
+  int iterations;      /* preconditioned Krylov iterations, summed over right-hand sides */
+  int restarts;        /* outer cycles (restarts or defect corrections), summed */
+  double relres;       /* largest final true relative residual ||b - D z||/||b|| (FP64) */
+  double seconds;      /* wall time of the call */
+  double precond_seconds;  /* device time in the multilevel preconditioner (profiling on) */
+} mg_solve_info;
+
+/* Fill *p with defaults: 1 level, 4 MR steps, 2 post sweeps, N = 8, 3 set-up
+ * sweeps, 12 coarse steps, 8 inner steps, FGMRES(20), tol 1e-10, maxiter 1000,
+ * MG_FP64, nrhs_max 1, agg2 = sap_block2 = 2^4.  dims must still be set. */
+int mg_default_params(mg_params* p);
+
+/* Build a solver context (Sec. 3, set-up part 1).
+ * U: device, canonical gauge field, complex128 (read during the call only; the
+ *    caller may free it afterwards).  c_sw: clover coefficient; m0: bare mass,
+ *    D = 4 + m0 - hopping/2 + clover (kappa = 1/(2 m0 + 8)).
+ * Builds the clover term, packs U in every precision the context needs, runs
+ * the bootstrap set-up (Schwarz sweeps on random or given test vectors, kept
+ * orthonormal; local orthonormalisation; D_c = P^dagger D P, recursively) and
+ * allocates all solve workspace.  Synchronises.  *out receives the context.
+ * Errors: MG_ERR_ARG (dims, params), MG_ERR_NONFINITE (U), MG_ERR_OOM, MG_ERR_CUDA. */
+int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx** out);
+
+/* out = D in (Sec. 1, Eq. 1.1) for nrhs fields.  prec: MG_FP64 (complex128
+ * fields, FP64 links) or the context's mixed precision / MG_FP32 (complex64
+ * fields; links and clover stored in that precision), optionally | MG_BLOCKED.
+ * in and out must not overlap.  Asynchronous. */
+int dirac_apply(mg_ctx* ctx, const void* in, void* out, int prec, int nrhs);
+
+/* n_sweeps red-black Schwarz sweeps (Sec. 2, Algorithm 1) on D z = b, updating z
+ * in place (z is the starting guess).  Each sweep: for colour 0 then 1,
+ * r = b - D z and z += (n_MR MR steps of the block system) on every block of
+ * that colour.  prec and layout as for dirac_apply.  Asynchronous. */
+int sap_smooth(mg_ctx* ctx, const void* b, void* z, int n_sweeps, int prec, int nrhs);
+
+/* Solve D z = b for nrhs right-hand sides to ||b - D z|| <= tol ||b|| (Sec. 4).
+ * b, z: device, canonical complex128.  Plain form (MG_FP64): FGMRES(m) in FP64
+ * with the FP64 multilevel cycle as right preconditioner.  Mixed form: FP64
+ * defect correction (r = b - D z recomputed in FP64) around FP32 FGMRES(m)
+ * whose preconditioner is the FP32/FP16/BF16 cycle.  Synchronises.
+ * info may be NULL.  Returns MG_OK, MG_NOT_CONVERGED or an error. */
+int mg_solve(mg_ctx* ctx, const double* b, double* z, int nrhs, mg_solve_info* info);
+
+/* Free every device buffer the context owns. */
+void mg_destroy(mg_ctx* ctx);
+
+/* Message of the last error (thread-local, valid until the next call). */
+const char* mg_last_error(void);
+
+/* sizeof(mg_params), for bindings that mirror the struct. */
+unsigned long mg_sizeof_params(void);
+
+/* ---- inspection and component entry points (used by the parity tests) ---- */
+
+/* Spinor layout conversion canonical <-> internal blocked (prec: MG_FP64 or
+ * MG_FP32 element type, same on both sides). */
+int mg_pack_spinor(mg_ctx* ctx, const void* canonical, void* blocked, int prec, int nrhs);
+int mg_unpack_spinor(mg_ctx* ctx, const void* blocked, void* canonical, int prec, int nrhs);
+
+/* The clover matrix A(x) = (4 + m0) + c_sw (i/2) sum sigma F (FP64) as two dense
+ * 6x6 chiral blocks: out device [V][chi][6][6] complex128, canonical sites,
+ * index within a block (spin - 2 chi)*3 + colour. */
+int mg_clover_export(mg_ctx* ctx, double* out);
+
+/* The locally orthonormalised test vectors defining P of level `level` (0:
+ * fine -> level 1, 1: level 1 -> level 2) as FP64 fields: out device
+ * [N][fine-level field] complex128 in that level's canonical layout. */
+int mg_get_vectors(mg_ctx* ctx, int level, double* out);
+
+/* The coarse operator of level `level` (1 or 2) as FP64 stencil: out device
+ * [coarse site][9][2N][2N] complex128, row-major (row i, column j); direction
+ * 0 = self, 1 + 2 mu = +mu, 2 + 2 mu = -mu (mu = x, y, z, t), i.e.
+ * (D_c x)(a) = sum_d M_d(a) x(a + offset_d). */
+int mg_get_coarse_op(mg_ctx* ctx, int level, double* out);
+
+/* v_c = P^dagger v (restriction) and v = P v_c (interpolation) between level
+ * `level` and level + 1, and v_out = D_c v_in on level `level` >= 1.
+ * Element type: complex128 for MG_FP64, complex64 otherwise (fine side
+ * canonical unless MG_BLOCKED).  Asynchronous. */
+int mg_restrict(mg_ctx* ctx, int level, const void* in, void* out, int prec);
+int mg_prolong(mg_ctx* ctx, int level, const void* in, void* out, int prec);
+int mg_coarse_apply(mg_ctx* ctx, int level, const void* in, void* out, int prec);
+
+/* Approximate solve on coarse level `level` >= 1 exactly as the cycle does it
+ * (fixed-step GMRES on the coarsest level, fixed-step flexible GMRES with the
+ * level's cycle otherwise), from zero. */
+int mg_coarse_solve(mg_ctx* ctx, int level, const void* in, void* out, int prec);
+
+/* One application of the multilevel cycle z = M v on the fine level (the
+ * outer solver's preconditioner).  prec: MG_FP64 for a plain-form context,
+ * MG_FP32 for a mixed one.  Asynchronous. */
+int mg_precondition(mg_ctx* ctx, const void* v, void* z, int prec);
+
+/* Per-kernel device timing with CUDA events around every launch of the
+ * selected kernel families (0 = off).  mg_get_profile returns, for each
+ * family (0 dirac, 1 Schwarz colour pass, 2 coarse apply, 3 restrict,
+ * 4 prolong, 5 BLAS), the launch count and the summed milliseconds. */
+int mg_set_profiling(mg_ctx* ctx, int on);
+int mg_get_profile(mg_ctx* ctx, int family, long long* launches, double* ms);
+int mg_reset_profile(mg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAPMG_H */

@@ -1,0 +1,22 @@
+"""GB300 SAP-multilevel solver for the clover-improved Wilson-Dirac equation.
+
+Frommer, Kahl, Krieg, Leder, Rottmann, "Aggregation-based Multilevel Methods
+for Lattice QCD" (Lattice 2011): red-black Schwarz (SAP) smoothing over 4^4
+blocks with local minimal-residual block solves, aggregation-based
+interpolation with a Galerkin coarse operator, bootstrap set-up, and an outer
+flexible GMRES.  The compute path is the C-ABI library libsapmg.so (hand-written
+sm_103a CUDA); this package is its Python binding plus a torch convenience
+wrapper.  PyTorch supplies device memory and streams only.
+"""
+
+from . import binding
+from .binding import (
+    MG_OK, MG_NOT_CONVERGED, MG_ERR_ARG, MG_ERR_NONFINITE, MG_ERR_OOM, MG_ERR_CUDA, MG_ERR_TIMEOUT,
+    MG_ERR_STATE, MG_FP64, MG_FP32, MG_FP16, MG_BF16, MG_BLOCKED, PRECISIONS, MgParams, MgSolveInfo,
+    MgError, mg_default_params, mg_setup, dirac_apply, sap_smooth, mg_solve, mg_destroy, mg_pack_spinor,
+    mg_unpack_spinor, mg_clover_export, mg_get_vectors, mg_get_coarse_op, mg_restrict, mg_prolong,
+    mg_coarse_apply, mg_coarse_solve, mg_precondition, mg_set_profiling, mg_get_profile, mg_reset_profile,
+)
+from .solver import Solver
+
+__all__ = [name for name in dir() if not name.startswith("_")]

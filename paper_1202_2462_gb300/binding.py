@@ -1,0 +1,223 @@
+"""ctypes binding of the C-ABI in include/sapmg.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and takes the
+same arguments, with torch tensors accepted wherever the C side takes a device
+pointer.  All computation happens in libsapmg.so; if the library is missing or
+cannot be loaded the first call raises, there is no fallback.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsapmg.so")
+
+MG_OK = 0
+MG_NOT_CONVERGED = 1
+MG_ERR_ARG = -1
+MG_ERR_NONFINITE = -2
+MG_ERR_OOM = -3
+MG_ERR_CUDA = -4
+MG_ERR_TIMEOUT = -5
+MG_ERR_STATE = -6
+
+MG_FP64 = 0
+MG_FP32 = 1
+MG_FP16 = 2
+MG_BF16 = 3
+MG_BLOCKED = 0x100
+
+PRECISIONS = {"fp64": MG_FP64, "fp32": MG_FP32, "fp16": MG_FP16, "bf16": MG_BF16}
+
+
+class MgParams(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int * 4),
+        ("antiperiodic_t", ctypes.c_int),
+        ("n_levels", ctypes.c_int),
+        ("agg2", ctypes.c_int * 4),
+        ("sap_block2", ctypes.c_int * 4),
+        ("n_vec", ctypes.c_int * 2),
+        ("setup_iters", ctypes.c_int),
+        ("n_mr", ctypes.c_int),
+        ("nu_post", ctypes.c_int),
+        ("coarse_iters", ctypes.c_int),
+        ("inner_iters", ctypes.c_int),
+        ("fgmres_m", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("maxiter", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("nrhs_max", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+        ("stream", ctypes.c_void_p),
+        ("init_vectors", ctypes.c_void_p),
+        ("verbose", ctypes.c_int),
+    ]
+
+
+class MgSolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("relres", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+        ("precond_seconds", ctypes.c_double),
+    ]
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGNATURES = {
+    "mg_default_params": (_I, [ctypes.POINTER(MgParams)]),
+    "mg_setup": (_I, [_VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(MgParams), ctypes.POINTER(_VP)]),
+    "dirac_apply": (_I, [_VP, _VP, _VP, _I, _I]),
+    "sap_smooth": (_I, [_VP, _VP, _VP, _I, _I, _I]),
+    "mg_solve": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(MgSolveInfo)]),
+    "mg_destroy": (None, [_VP]),
+    "mg_last_error": (ctypes.c_char_p, []),
+    "mg_sizeof_params": (ctypes.c_ulong, []),
+    "mg_pack_spinor": (_I, [_VP, _VP, _VP, _I, _I]),
+    "mg_unpack_spinor": (_I, [_VP, _VP, _VP, _I, _I]),
+    "mg_clover_export": (_I, [_VP, _VP]),
+    "mg_get_vectors": (_I, [_VP, _I, _VP]),
+    "mg_get_coarse_op": (_I, [_VP, _I, _VP]),
+    "mg_restrict": (_I, [_VP, _I, _VP, _VP, _I]),
+    "mg_prolong": (_I, [_VP, _I, _VP, _VP, _I]),
+    "mg_coarse_apply": (_I, [_VP, _I, _VP, _VP, _I]),
+    "mg_coarse_solve": (_I, [_VP, _I, _VP, _VP, _I]),
+    "mg_precondition": (_I, [_VP, _VP, _VP, _I]),
+    "mg_set_profiling": (_I, [_VP, _I]),
+    "mg_get_profile": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+    "mg_reset_profile": (_I, [_VP]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libsapmg.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        if handle.mg_sizeof_params() != ctypes.sizeof(MgParams):
+            raise RuntimeError("mg_params layout mismatch between binding and library")
+        _lib = handle
+    return _lib
+
+
+class MgError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib().mg_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(code, where):
+    if code < 0:
+        raise MgError(code, where)
+    return code
+
+
+# --- entry points with the C names ---------------------------------------------
+
+def mg_default_params():
+    p = MgParams()
+    _check(lib().mg_default_params(ctypes.byref(p)), "mg_default_params")
+    return p
+
+
+def mg_setup(U, c_sw, m0, params):
+    ctx = ctypes.c_void_p()
+    _check(lib().mg_setup(_ptr(U), float(c_sw), float(m0), ctypes.byref(params), ctypes.byref(ctx)), "mg_setup")
+    return ctx
+
+
+def dirac_apply(ctx, inp, out, prec, nrhs=1):
+    return _check(lib().dirac_apply(ctx, _ptr(inp), _ptr(out), prec, nrhs), "dirac_apply")
+
+
+def sap_smooth(ctx, b, z, n_sweeps, prec, nrhs=1):
+    return _check(lib().sap_smooth(ctx, _ptr(b), _ptr(z), n_sweeps, prec, nrhs), "sap_smooth")
+
+
+def mg_solve(ctx, b, z, nrhs=1):
+    info = MgSolveInfo()
+    code = _check(lib().mg_solve(ctx, _ptr(b), _ptr(z), nrhs, ctypes.byref(info)), "mg_solve")
+    return code, info
+
+
+def mg_destroy(ctx):
+    lib().mg_destroy(ctx)
+
+
+def mg_pack_spinor(ctx, canonical, blocked, prec, nrhs=1):
+    return _check(lib().mg_pack_spinor(ctx, _ptr(canonical), _ptr(blocked), prec, nrhs), "mg_pack_spinor")
+
+
+def mg_unpack_spinor(ctx, blocked, canonical, prec, nrhs=1):
+    return _check(lib().mg_unpack_spinor(ctx, _ptr(blocked), _ptr(canonical), prec, nrhs), "mg_unpack_spinor")
+
+
+def mg_clover_export(ctx, out):
+    return _check(lib().mg_clover_export(ctx, _ptr(out)), "mg_clover_export")
+
+
+def mg_get_vectors(ctx, level, out):
+    return _check(lib().mg_get_vectors(ctx, level, _ptr(out)), "mg_get_vectors")
+
+
+def mg_get_coarse_op(ctx, level, out):
+    return _check(lib().mg_get_coarse_op(ctx, level, _ptr(out)), "mg_get_coarse_op")
+
+
+def mg_restrict(ctx, level, inp, out, prec):
+    return _check(lib().mg_restrict(ctx, level, _ptr(inp), _ptr(out), prec), "mg_restrict")
+
+
+def mg_prolong(ctx, level, inp, out, prec):
+    return _check(lib().mg_prolong(ctx, level, _ptr(inp), _ptr(out), prec), "mg_prolong")
+
+
+def mg_coarse_apply(ctx, level, inp, out, prec):
+    return _check(lib().mg_coarse_apply(ctx, level, _ptr(inp), _ptr(out), prec), "mg_coarse_apply")
+
+
+def mg_coarse_solve(ctx, level, inp, out, prec):
+    return _check(lib().mg_coarse_solve(ctx, level, _ptr(inp), _ptr(out), prec), "mg_coarse_solve")
+
+
+def mg_precondition(ctx, v, z, prec):
+    return _check(lib().mg_precondition(ctx, _ptr(v), _ptr(z), prec), "mg_precondition")
+
+
+def mg_set_profiling(ctx, on):
+    return _check(lib().mg_set_profiling(ctx, int(on)), "mg_set_profiling")
+
+
+def mg_get_profile(ctx, family):
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(lib().mg_get_profile(ctx, family, ctypes.byref(n), ctypes.byref(ms)), "mg_get_profile")
+    return n.value, ms.value
+
+
+def mg_reset_profile(ctx):
+    return _check(lib().mg_reset_profile(ctx), "mg_reset_profile")
+
+
+PROFILE_FAMILIES = {"dirac": 0, "sap": 1, "coarse": 2, "restrict": 3, "prolong": 4, "blas": 5}

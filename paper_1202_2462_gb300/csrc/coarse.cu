@@ -1,0 +1,352 @@
+// Aggregation and coarse-grid kernels (Sec. 3):
+//   K3 restriction P^dagger, K4 interpolation P, K7 local orthonormalisation of
+//   the test vectors, K6 Galerkin assembly D_c = P^dagger D P, K5 the coarse
+//   stencil (D_c x)(a) = sum_d M_d(a) x(a + offset_d).
+//
+// Level 0 -> 1: aggregates are the 4^4 blocks of the fine layout, split by
+// chirality (spins {0,1} / {2,3}); coarse dof chi*N + k.  P is stored as the
+// locally orthonormal test vectors, block-major: Pv[blk][k][12][256].
+// Levels >= 1: fields are canonical [site][n2]; aggregates are a^4 boxes of
+// coarse sites; level-1 vectors are stored vector-major [k][site][n2].
+// Coarse operators: M[site][d][j][i] (column j, row i contiguous in i), with
+// d = 0 self, 1 + 2 mu the +mu neighbour, 2 + 2 mu the -mu neighbour.
+#include "internal.h"
+#include "coarse.h"
+#include "stencil.cuh"
+
+namespace sapmg {
+
+// ============================================================ level 0 -> 1
+// K3: rc[blk][chi*N + k] = sum over the block's sites and chirality chi of conj(v_k) r
+template <class R, class TS, class TV, class TC>
+__global__ void __launch_bounds__(256) restrict0_kernel(const TS* __restrict__ in, TC* __restrict__ out,
+                                                        const TV* __restrict__ Pv, int N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R (*red)[4] = reinterpret_cast<R (*)[4]>(smem_raw);        // [8 * N][4]
+  const int blk = blockIdx.x, loc = threadIdx.x;
+  const int wid = loc >> 5, lane = loc & 31;
+  const size_t off = (size_t)blockIdx.y * gridDim.x * 12 * 256;   // rhs stride (one field)
+  Cplx<R> r[12];
+  load_spinor<R>(in + off, blk, loc, r);
+  for (int k = 0; k < N; ++k) {
+    const TV* v = Pv + ((size_t)(blk * N + k) * 12) * 256 + loc;
+    Cplx<R> d0 = cmk<R>(0, 0), d1 = cmk<R>(0, 0);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) cfma_conj(d0, Io<R, TV>::ld(v + c * 256), r[c]);
+#pragma unroll
+    for (int c = 6; c < 12; ++c) cfma_conj(d1, Io<R, TV>::ld(v + c * 256), r[c]);
+    R a = warp_sum(d0.re), b = warp_sum(d0.im), c2 = warp_sum(d1.re), d = warp_sum(d1.im);
+    if (lane == 0) { R* q = red[wid * N + k]; q[0] = a; q[1] = b; q[2] = c2; q[3] = d; }
+  }
+  __syncthreads();
+  const int n2 = 2 * N;
+  TC* o = out + (size_t)blockIdx.y * gridDim.x * n2 + (size_t)blk * n2;
+  for (int t = loc; t < n2; t += 256) {
+    const int chi = t / N, k = t % N;
+    R sr = 0, si = 0;
+    for (int w = 0; w < 8; ++w) { sr += red[w * N + k][2 * chi]; si += red[w * N + k][2 * chi + 1]; }
+    Io<R, TC>::st(o + t, cmk(sr, si));
+  }
+}
+
+// K4: out(x) = sum_k v_k(x)|_chi e[blk][chi*N + k]   (overwrites out)
+template <class R, class TS, class TV, class TC>
+__global__ void __launch_bounds__(256) prolong0_kernel(const TC* __restrict__ in, TS* __restrict__ out,
+                                                       const TV* __restrict__ Pv, int N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<R>* e = reinterpret_cast<Cplx<R>*>(smem_raw);             // [2N]
+  const int blk = blockIdx.x, loc = threadIdx.x;
+  const int n2 = 2 * N;
+  const TC* ein = in + (size_t)blockIdx.y * gridDim.x * n2 + (size_t)blk * n2;
+  for (int t = loc; t < n2; t += 256) e[t] = Io<R, TC>::ldc(ein + t);
+  __syncthreads();
+  Cplx<R> o[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) o[c] = cmk<R>(0, 0);
+  for (int k = 0; k < N; ++k) {
+    const TV* v = Pv + ((size_t)(blk * N + k) * 12) * 256 + loc;
+    const Cplx<R> e0 = e[k], e1 = e[N + k];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) cfma(o[c], Io<R, TV>::ld(v + c * 256), e0);
+#pragma unroll
+    for (int c = 6; c < 12; ++c) cfma(o[c], Io<R, TV>::ld(v + c * 256), e1);
+  }
+  store_spinor<R>(out + (size_t)blockIdx.y * gridDim.x * 12 * 256, blk, loc, o);
+}
+
+template <class R, class TS, class TV, class TC>
+static int transfer0_run(bool restrict_, const Geom& g, const void* in, void* out, const void* Pv, int N, int nrhs,
+                         cudaStream_t s) {
+  dim3 grid(g.nblocks, nrhs);
+  if (restrict_) {
+    const size_t smem = sizeof(R) * 4 * 8 * N;
+    restrict0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TS*)in, (TC*)out, (const TV*)Pv, N);
+  } else {
+    const size_t smem = sizeof(Cplx<R>) * 2 * N;
+    prolong0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TC*)in, (TS*)out, (const TV*)Pv, N);
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+int launch_transfer0(bool restrict_, int prec, const Geom& g, const void* in, void* out, const void* Pv, int N,
+                     int nrhs, cudaStream_t s) {
+  switch (prec) {
+    case P64: return transfer0_run<double, double2, double2, double2>(restrict_, g, in, out, Pv, N, nrhs, s);
+    case P32: return transfer0_run<float, float2, float2, float2>(restrict_, g, in, out, Pv, N, nrhs, s);
+    case P16: return transfer0_run<float, float2, __half2, float2>(restrict_, g, in, out, Pv, N, nrhs, s);
+    case PBF: return transfer0_run<float, float2, __nv_bfloat162, float2>(restrict_, g, in, out, Pv, N, nrhs, s);
+    default: return MG_ERR_ARG;
+  }
+}
+
+// K7: modified Gram-Schmidt of the N vectors on every (block, chirality),
+// vectors k = 0..N-1 in order, each normalised to a positive real norm.
+// V: FP64 vector-major blocked fields [k][blk][12][256].
+__device__ __forceinline__ double2 block_sum2(double a, double b, double (*red)[2]) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[w][0] = a; red[w][1] = b; }
+  __syncthreads();
+  double sa = 0, sb = 0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { sa += red[q][0]; sb += red[q][1]; }
+  __syncthreads();
+  return make_double2(sa, sb);
+}
+
+__global__ void __launch_bounds__(256) block_gs0_kernel(double2* __restrict__ V, int N, long long fstride) {
+  __shared__ double red[8][2];
+  const int blk = blockIdx.x, chi = blockIdx.y, loc = threadIdx.x;
+  const size_t base = ((size_t)blk * 12 + 6 * chi) * 256 + loc;
+  for (int k = 0; k < N; ++k) {
+    double2* vk = V + k * fstride + base;
+    Cplx<double> x[6];
+    for (int c = 0; c < 6; ++c) { double2 t = vk[c * 256]; x[c] = cmk(t.x, t.y); }
+    for (int j = 0; j < k; ++j) {
+      const double2* vj = V + j * fstride + base;
+      Cplx<double> q[6], d = cmk(0.0, 0.0);
+      for (int c = 0; c < 6; ++c) { double2 t = vj[c * 256]; q[c] = cmk(t.x, t.y); cfma_conj(d, q[c], x[c]); }
+      const double2 s = block_sum2(d.re, d.im, red);
+      const Cplx<double> cs = cmk(s.x, s.y);
+      for (int c = 0; c < 6; ++c) x[c] = x[c] - cs * q[c];
+    }
+    double nn = 0;
+    for (int c = 0; c < 6; ++c) nn += x[c].re * x[c].re + x[c].im * x[c].im;
+    const double2 s = block_sum2(nn, 0.0, red);
+    const double inv = s.x > 0 ? 1.0 / sqrt(s.x) : 0.0;
+    for (int c = 0; c < 6; ++c) vk[c * 256] = make_double2(x[c].re * inv, x[c].im * inv);
+  }
+}
+
+int launch_block_gs0(const Geom& g, void* V64, int N, cudaStream_t s) {
+  dim3 grid(g.nblocks, 2);
+  block_gs0_kernel<<<grid, 256, 0, s>>>((double2*)V64, N, (long long)g.V * 12);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+// Reorder the FP64 vector-major vectors into the block-major storage Pv[blk][k][12][256].
+template <class TV>
+__global__ void store_p0_kernel(const double2* __restrict__ V, TV* __restrict__ Pv, int N, long long fstride) {
+  const int blk = blockIdx.x, k = blockIdx.y, loc = threadIdx.x;
+  const double2* src = V + k * fstride + (size_t)blk * 12 * 256 + loc;
+  TV* dst = Pv + ((size_t)(blk * N + k) * 12) * 256 + loc;
+  for (int c = 0; c < 12; ++c) {
+    const double2 t = src[c * 256];
+    Io<double, TV>::st(dst + c * 256, cmk(t.x, t.y));
+  }
+}
+
+int launch_store_p0(int prec, const Geom& g, const void* V64, void* Pv, int N, cudaStream_t s) {
+  dim3 grid(g.nblocks, N);
+  const long long fs = (long long)g.V * 12;
+  switch (prec) {
+    case P64: store_p0_kernel<double2><<<grid, 256, 0, s>>>((const double2*)V64, (double2*)Pv, N, fs); break;
+    case P32: store_p0_kernel<float2><<<grid, 256, 0, s>>>((const double2*)V64, (float2*)Pv, N, fs); break;
+    case P16: store_p0_kernel<__half2><<<grid, 256, 0, s>>>((const double2*)V64, (__half2*)Pv, N, fs); break;
+    case PBF: store_p0_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>((const double2*)V64, (__nv_bfloat162*)Pv, N, fs); break;
+    default: return MG_ERR_ARG;
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+// K6: D_c = P^dagger D P for level 0 -> 1, FP64.  CTA (a, j): column j = (chi', k)
+// of every 2N x 2N block row of aggregate a.  Each thread (site x of a) forms
+// the 9 partial images of u = v_k|_chi' (self: clover and hops inside a; +-mu:
+// the hop from the neighbouring aggregate across a's face) and projects each
+// onto the 2N columns of P on a.
+template <int MU, int S>
+__device__ __forceinline__ void assemble_hop(const Geom& g, const double2* __restrict__ U, const double2* vk,
+                                             int chi_p, int blk, int loc, bool inside, Cplx<double> (&w)[12]) {
+  int nb, nl;
+  neighbour(g, blk, loc, MU, S, nb, nl);
+  if ((nb == blk) != inside) return;
+  Cplx<double> u[12];
+  load_spinor<double>(vk, nb, nl, u);
+#pragma unroll
+  for (int c = 0; c < 12; ++c)
+    if ((c / 6) != chi_p) u[c] = cmk(0.0, 0.0);
+  Cplx<double> acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = cmk(0.0, 0.0);
+  if (S > 0) hop_fwd<MU>(U, blk, loc, u, acc);
+  else hop_bwd<MU>(U, nb, nl, u, acc);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) w[c] = w[c] - 0.5 * acc[c];
+}
+
+template <int MU>
+__device__ __forceinline__ void assemble_dir(const Geom& g, const double2* U, const double2* vk, int chi_p, int blk,
+                                             int loc, int d, Cplx<double> (&w)[12]) {
+  if (d == 0) {
+    assemble_hop<MU, 1>(g, U, vk, chi_p, blk, loc, true, w);
+    assemble_hop<MU, -1>(g, U, vk, chi_p, blk, loc, true, w);
+  } else if (d == 1 + 2 * MU) {
+    assemble_hop<MU, 1>(g, U, vk, chi_p, blk, loc, false, w);
+  } else if (d == 2 + 2 * MU) {
+    assemble_hop<MU, -1>(g, U, vk, chi_p, blk, loc, false, w);
+  }
+}
+
+__global__ void __launch_bounds__(256) assemble0_kernel(const double2* __restrict__ V, const double2* __restrict__ U,
+                                                        const double2* __restrict__ A, double2* __restrict__ M,
+                                                        Geom g, int N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double (*red)[4] = reinterpret_cast<double (*)[4]>(smem_raw);   // [8 * N][4]
+  const int blk = blockIdx.x, j = blockIdx.y, loc = threadIdx.x;
+  const int n2 = 2 * N, chi_p = j / N, k = j % N;
+  const int wid = loc >> 5, lane = loc & 31;
+  const long long fs = g.V * 12;
+  const double2* vk = V + k * fs;
+  for (int d = 0; d < 9; ++d) {
+    Cplx<double> w[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) w[c] = cmk(0.0, 0.0);
+    if (d == 0) {
+      Cplx<double> u[12];
+      load_spinor<double>(vk, blk, loc, u);
+#pragma unroll
+      for (int c = 0; c < 12; ++c)
+        if ((c / 6) != chi_p) u[c] = cmk(0.0, 0.0);
+      clover_apply<double>(A, blk, loc, u, w);
+    }
+    assemble_dir<0>(g, U, vk, chi_p, blk, loc, d, w);
+    assemble_dir<1>(g, U, vk, chi_p, blk, loc, d, w);
+    assemble_dir<2>(g, U, vk, chi_p, blk, loc, d, w);
+    assemble_dir<3>(g, U, vk, chi_p, blk, loc, d, w);
+    // project onto v_i|_chi on this block
+    for (int i = 0; i < N; ++i) {
+      const double2* vi = V + i * fs + (size_t)blk * 12 * 256 + loc;
+      Cplx<double> d0 = cmk(0.0, 0.0), d1 = cmk(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) { double2 t = vi[c * 256]; cfma_conj(d0, cmk(t.x, t.y), w[c]); }
+#pragma unroll
+      for (int c = 6; c < 12; ++c) { double2 t = vi[c * 256]; cfma_conj(d1, cmk(t.x, t.y), w[c]); }
+      double a = warp_sum(d0.re), b = warp_sum(d0.im), c2 = warp_sum(d1.re), e = warp_sum(d1.im);
+      if (lane == 0) { double* q = red[wid * N + i]; q[0] = a; q[1] = b; q[2] = c2; q[3] = e; }
+    }
+    __syncthreads();
+    double2* col = M + (((size_t)blk * 9 + d) * n2 + j) * n2;
+    for (int t = loc; t < n2; t += 256) {
+      const int chi = t / N, i = t % N;
+      double sr = 0, si = 0;
+      for (int q = 0; q < 8; ++q) { sr += red[q * N + i][2 * chi]; si += red[q * N + i][2 * chi + 1]; }
+      col[t] = make_double2(sr, si);
+    }
+    __syncthreads();
+  }
+}
+
+int launch_assemble0(const Geom& g, const void* V64, const void* U64, const void* A64, void* M64, int N,
+                     cudaStream_t s) {
+  dim3 grid(g.nblocks, 2 * N);
+  const size_t smem = sizeof(double) * 4 * 8 * N;
+  assemble0_kernel<<<grid, 256, smem, s>>>((const double2*)V64, (const double2*)U64, (const double2*)A64,
+                                           (double2*)M64, g, N);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+// ============================================================ coarse levels
+__device__ __forceinline__ int cg_coord(const CGeom& c, int site, int mu) {
+  int s = site;
+  for (int m = 0; m < mu; ++m) s /= c.L[m];
+  return s % c.L[mu];
+}
+
+// Site index of the neighbour of `site` in direction d (0 self, 1+2mu: +mu, 2+2mu: -mu).
+__device__ __forceinline__ int cg_neighbour(const CGeom& c, int site, int d) {
+  if (d == 0) return site;
+  const int mu = (d - 1) >> 1;
+  const int step = (d & 1) ? 1 : -1;
+  int stride = 1;
+  for (int m = 0; m < mu; ++m) stride *= c.L[m];
+  const int x = (site / stride) % c.L[mu];
+  const int nx = (x + step + c.L[mu]) % c.L[mu];
+  return site + (nx - x) * stride;
+}
+
+// K5: out[site][i] = sum_d sum_j M[site][d][j][i] x[nb_d(site)][j]
+template <class R, class TM, class TX>
+__global__ void __launch_bounds__(256) coarse_apply_kernel(const TM* __restrict__ M, const TX* __restrict__ x,
+                                                           TX* __restrict__ out, CGeom c) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int n2 = c.n2;
+  if (t >= (long long)c.nsites * n2) return;
+  const int site = (int)(t / n2), i = (int)(t % n2);
+  const size_t roff = (size_t)blockIdx.y * c.nsites * n2;
+  const TX* xr = x + roff;
+  Cplx<R> acc = cmk<R>(0, 0);
+  for (int d = 0; d < 9; ++d) {
+    const int nb = cg_neighbour(c, site, d);
+    const TM* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
+    const TX* xn = xr + (size_t)nb * n2;
+    for (int j = 0; j < n2; ++j) cfma(acc, Io<R, TM>::ld(m + (size_t)j * n2), Io<R, TX>::ld(xn + j));
+  }
+  Io<R, TX>::st(out + roff + t, acc);
+}
+
+int launch_coarse_apply(int prec, const CGeom& c, const void* M, const void* x, void* out, int nrhs, cudaStream_t s) {
+  const long long n = (long long)c.nsites * c.n2;
+  dim3 grid((unsigned)((n + 255) / 256), nrhs);
+  switch (prec) {
+    case P64: coarse_apply_kernel<double, double2, double2><<<grid, 256, 0, s>>>((const double2*)M, (const double2*)x, (double2*)out, c); break;
+    case P32: coarse_apply_kernel<float, float2, float2><<<grid, 256, 0, s>>>((const float2*)M, (const float2*)x, (float2*)out, c); break;
+    case P16: coarse_apply_kernel<float, __half2, float2><<<grid, 256, 0, s>>>((const __half2*)M, (const float2*)x, (float2*)out, c); break;
+    case PBF: coarse_apply_kernel<float, __nv_bfloat162, float2><<<grid, 256, 0, s>>>((const __nv_bfloat162*)M, (const float2*)x, (float2*)out, c); break;
+    default: return MG_ERR_ARG;
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+// Dense row-major FP64 export [site][9][i][j] of a column-major operator.
+template <class TM>
+__global__ void coarse_export_kernel(const TM* __restrict__ M, double2* __restrict__ out, CGeom c) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n2 = c.n2;
+  if (t >= (long long)c.nsites * 9 * n2 * n2) return;
+  const long long sd = t / (n2 * n2);
+  const int i = (int)((t / n2) % n2), j = (int)(t % n2);
+  const Cplx<double> v = Io<double, TM>::ld(M + (sd * n2 + j) * n2 + i);
+  out[t] = make_double2(v.re, v.im);
+}
+
+int launch_coarse_export(int prec, const CGeom& c, const void* M, double* out, cudaStream_t s) {
+  const long long n = (long long)c.nsites * 9 * c.n2 * c.n2;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  switch (prec) {
+    case P64: coarse_export_kernel<double2><<<nb, 256, 0, s>>>((const double2*)M, (double2*)out, c); break;
+    case P32: coarse_export_kernel<float2><<<nb, 256, 0, s>>>((const float2*)M, (double2*)out, c); break;
+    case P16: coarse_export_kernel<__half2><<<nb, 256, 0, s>>>((const __half2*)M, (double2*)out, c); break;
+    case PBF: coarse_export_kernel<__nv_bfloat162><<<nb, 256, 0, s>>>((const __nv_bfloat162*)M, (double2*)out, c); break;
+    default: return MG_ERR_ARG;
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+// Blocked FP64 vector-major -> canonical FP64 export of the level-0 vectors.
+}  // namespace sapmg

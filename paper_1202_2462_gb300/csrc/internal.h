@@ -1,0 +1,36 @@
+// Internal declarations of the SAP-multilevel library (not part of the C-ABI).
+#pragma once
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+
+#include "sapmg.h"
+#include "common.cuh"
+
+namespace sapmg {
+
+// Storage precisions of fields; equal to the public MG_FP64 ... MG_BF16.
+enum { P64 = MG_FP64, P32 = MG_FP32, P16 = MG_FP16, PBF = MG_BF16 };
+
+inline size_t complex_bytes(int prec) { return prec == P64 ? 16 : (prec == P32 ? 8 : 4); }
+
+// layout.cu
+int launch_pack_gauge(int prec, const Geom& g, const double* Uc, void* Ub, int antiperiodic_t, cudaStream_t s);
+int launch_clover_build(const Geom& g, const double* Uc, void* Ab64, double m0, double c_sw, cudaStream_t s);
+int launch_clover_export(const Geom& g, const void* Ab64, double* out, cudaStream_t s);
+int launch_convert(int from, const void* in, int to, void* out, size_t n_complex, cudaStream_t s);
+int launch_pack_spinor(int pin, const void* canon, int pout, void* blocked, const Geom& g, int nrhs, cudaStream_t s);
+int launch_unpack_spinor(int pin, const void* blocked, int pout, void* canon, const Geom& g, int nrhs, cudaStream_t s);
+int launch_draw_vectors(const Geom& g, void* out64, int nvec, unsigned long long seed, unsigned long long stream,
+                        cudaStream_t s);
+uint64_t host_splitmix64(uint64_t x);
+
+// dirac.cu
+int launch_dirac(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
+                 cudaStream_t s);
+
+// sap.cu
+int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
+                      int n_mr, int nrhs, cudaStream_t s);
+
+}  // namespace sapmg

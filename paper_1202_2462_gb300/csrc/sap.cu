@@ -1,0 +1,146 @@
+// K2: one colour pass of red-black Schwarz (Sec. 2, Algorithm 1).
+//
+// For every block i of colour c (blocks of one colour never touch, so they
+// run as independent CTAs of one launch):
+//   r = b - D z on the block's sites (full operator: halo z from the
+//       neighbouring blocks of the other colour),
+//   e ~ D_i^{-1} r by n_MR minimal-residual steps with the Dirichlet block
+//       operator D_i = I^T D I (hops leaving the block dropped),
+//   z += e.
+// One CTA per block, one thread per site.  The MR iterate rho lives in shared
+// memory for the neighbour accesses of D_i; e, rho (own site) and p live in
+// registers; the block-wide dots are warp shuffles plus one shared-memory
+// exchange.  The two colours are two launches in stream order.
+#include "internal.h"
+#include "stencil.cuh"
+
+namespace sapmg {
+
+template <class R>
+__device__ __forceinline__ void load_smem_spinor(const Cplx<R>* __restrict__ s, int loc, Cplx<R> (&p)[12]) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) p[c] = s[c * 256 + loc];
+}
+
+// Sum of the hops of D_i at loc (neighbours inside the block only, from shared memory).
+template <int MU, class R, class TG>
+__device__ __forceinline__ void block_hops_dir(const TG* __restrict__ U, const Cplx<R>* __restrict__ rs, int blk,
+                                               int loc, Cplx<R> (&acc)[12]) {
+  const int ls = 1 << (2 * MU);
+  const int c = (loc >> (2 * MU)) & 3;
+  Cplx<R> pn[12];
+  if (c < 3) {
+    load_smem_spinor(rs, loc + ls, pn);
+    hop_fwd<MU>(U, blk, loc, pn, acc);
+  }
+  if (c > 0) {
+    load_smem_spinor(rs, loc - ls, pn);
+    hop_bwd<MU>(U, blk, loc - ls, pn, acc);
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void block_reduce3(R& a, R& b, R& c, R (*red)[4]) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { red[w][0] = a; red[w][1] = b; red[w][2] = c; }
+  __syncthreads();
+  a = b = c = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) { a += red[k][0]; b += red[k][1]; c += red[k][2]; }
+}
+
+template <class R, class TS, class TG>
+__global__ void __launch_bounds__(256) sap_colour_kernel(TS* __restrict__ z, const TS* __restrict__ b,
+                                                         const TG* __restrict__ U, const TG* __restrict__ A, Geom g,
+                                                         int colour, int n_mr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<R>* rs = reinterpret_cast<Cplx<R>*>(smem_raw);                    // [12][256]
+  R (*red)[4] = reinterpret_cast<R (*)[4]>(smem_raw + sizeof(Cplx<R>) * 12 * 256);
+  const size_t off = (size_t)blockIdx.y * g.V * 12;
+  z += off;
+  b += off;
+  const int blk = colour_block(g, blockIdx.x, colour);
+  const int loc = threadIdx.x;
+
+  // residual r = b - D z (Algorithm 1: residual update before the colour's block solves)
+  Cplx<R> zz[12], r[12], acc[12];
+  load_spinor<R>(z, blk, loc, zz);
+  clover_apply<R>(A, blk, loc, zz, r);
+  hops_global<R>(g, z, U, blk, loc, acc);
+  {
+    Cplx<R> bb[12];
+    load_spinor<R>(b, blk, loc, bb);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) r[c] = bb[c] - (r[c] - (R)0.5 * acc[c]);
+  }
+
+  // n_MR minimal-residual steps on D_i e = r
+  Cplx<R> e[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) e[c] = cmk<R>(0, 0);
+  for (int it = 0; it < n_mr; ++it) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) rs[c * 256 + loc] = r[c];
+    __syncthreads();
+    Cplx<R> p[12];
+    clover_apply<R>(A, blk, loc, r, p);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = cmk<R>(0, 0);
+    block_hops_dir<0>(U, rs, blk, loc, acc);
+    block_hops_dir<1>(U, rs, blk, loc, acc);
+    block_hops_dir<2>(U, rs, blk, loc, acc);
+    block_hops_dir<3>(U, rs, blk, loc, acc);
+    R pr_re = 0, pr_im = 0, pp = 0;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      p[c] = p[c] - (R)0.5 * acc[c];
+      pr_re += p[c].re * r[c].re + p[c].im * r[c].im;
+      pr_im += p[c].re * r[c].im - p[c].im * r[c].re;
+      pp += p[c].re * p[c].re + p[c].im * p[c].im;
+    }
+    block_reduce3(pr_re, pr_im, pp, red);
+    Cplx<R> alpha = cmk<R>(0, 0);
+    if (pp > (R)0) alpha = cmk(pr_re / pp, pr_im / pp);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      e[c] = e[c] + alpha * r[c];
+      r[c] = r[c] - alpha * p[c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 12; ++c) zz[c] = zz[c] + e[c];
+  store_spinor<R>(z, blk, loc, zz);
+}
+
+template <class R, class TS, class TG>
+static int run(const Geom& g, void* z, const void* b, const void* U, const void* A, int colour, int n_mr, int nrhs,
+               cudaStream_t s) {
+  const size_t smem = sizeof(Cplx<R>) * 12 * 256 + sizeof(R) * 8 * 4;
+  static bool attr = false;
+  if (!attr) {
+    SAPMG_CUDA_TRY(cudaFuncSetAttribute(sap_colour_kernel<R, TS, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    attr = true;
+  }
+  dim3 grid(g.nblocks / 2, nrhs);
+  sap_colour_kernel<R, TS, TG><<<grid, 256, smem, s>>>((TS*)z, (const TS*)b, (const TG*)U, (const TG*)A, g, colour,
+                                                       n_mr);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
+                      int n_mr, int nrhs, cudaStream_t s) {
+  switch (prec) {
+    case P64: return run<double, double2, double2>(g, z, b, U, A, colour, n_mr, nrhs, s);
+    case P32: return run<float, float2, float2>(g, z, b, U, A, colour, n_mr, nrhs, s);
+    case P16: return run<float, float2, __half2>(g, z, b, U, A, colour, n_mr, nrhs, s);
+    case PBF: return run<float, float2, __nv_bfloat162>(g, z, b, U, A, colour, n_mr, nrhs, s);
+    default: return MG_ERR_ARG;
+  }
+}
+
+}  // namespace sapmg

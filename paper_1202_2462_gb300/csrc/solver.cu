@@ -1,0 +1,781 @@
+// Host orchestration and the C-ABI: context and set-up (Sec. 3, bootstrap part
+// 1), the multilevel cycle, the device-resident fixed-step coarse GMRES, the
+// outer flexible GMRES (Sec. 2, Sec. 4) and FP64 defect correction.
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "blas.h"
+#include "coarse.h"
+
+namespace sapmg {
+
+static thread_local std::string g_err;
+void set_last_error(const char* msg, const char* file, int line) {
+  g_err = std::string(msg) + " (" + file + ":" + std::to_string(line) + ")";
+}
+static int fail(int code, const std::string& m) {
+  g_err = m;
+  return code;
+}
+
+#define TRY(x)                  \
+  do {                          \
+    int rc__ = (x);             \
+    if (rc__ < 0) return rc__;  \
+  } while (0)
+
+enum { FAM_DIRAC = 0, FAM_SAP = 1, FAM_COARSE = 2, FAM_RESTRICT = 3, FAM_PROLONG = 4, FAM_BLAS = 5, FAM_N = 6 };
+
+struct Prof {
+  bool on = false;
+  struct Rec { int fam; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> pending;
+  long long launches[FAM_N] = {};
+  double ms[FAM_N] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain() {
+    for (auto& r : pending) {
+      float t = 0;
+      cudaEventSynchronize(r.b);
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.fam] += t;
+      launches[r.fam] += 1;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  ~Prof() {
+    for (auto& r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct ProfScope {
+  Prof& p;
+  int fam;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(Prof& p_, int f, cudaStream_t s_) : p(p_), fam(f), s(s_) {
+    if (p.on) { a = p.get(); cudaEventRecord(a, s); }
+  }
+  ~ProfScope() {
+    if (p.on) {
+      cudaEvent_t b = p.get();
+      cudaEventRecord(b, s);
+      p.pending.push_back({fam, a, b});
+      if (p.pending.size() > 4096) p.drain();
+    }
+  }
+};
+
+struct CoarseLevel {
+  CGeom cg;
+  int store = P64;           // storage precision of M
+  void* M64 = nullptr;       // FP64 operator (set-up result, export)
+  void* M = nullptr;         // operator used by the solver (== M64 in FP64)
+  // fixed-step GMRES workspace (vector type = context's cycle type)
+  void* V = nullptr;         // (kmax + 1) vectors
+  void* w = nullptr;
+  void* x = nullptr;
+  void* b = nullptr;
+  double2* H = nullptr;      // 33 x 32 column-major
+  double2* tmp = nullptr;    // 64 scratch scalars
+  double2* beta2 = nullptr;
+  double2* y = nullptr;
+  size_t n() const { return (size_t)cg.nsites * cg.n2; }
+};
+
+}  // namespace sapmg
+
+using namespace sapmg;
+
+struct mg_ctx {
+  mg_params p;
+  Geom g;
+  cudaStream_t s = nullptr;
+  int prec = P64;    // MG_FP64 or the mixed storage precision
+  int vt = P64;      // vector type of the cycle (P64 plain, P32 mixed)
+  double m0 = 0, csw = 0;
+  std::vector<void*> allocs;
+  void *U64 = nullptr, *A64 = nullptr;     // blocked FP64 links (boundary sign folded in) and clover
+  void *U32 = nullptr, *A32 = nullptr;     // FP32 copies (mixed form)
+  void *Us = nullptr, *As = nullptr;       // smoother precision (== U64/A64 or U32/A32 or half)
+  int N0 = 0;
+  void* V64 = nullptr;                     // locally orthonormal test vectors, FP64 vector-major
+  void* Pv = nullptr;                      // P in cycle storage, block-major
+  CoarseLevel c1;
+  // fine workspace
+  void* zero_f = nullptr;                  // a zero fine field (cycle type)
+  void* io_a = nullptr;                    // canonical <-> blocked staging (FP64, nrhs_max fields)
+  void* io_b = nullptr;
+  double2* partial = nullptr;
+  // Krylov workspace
+  int m = 0;
+  void *V = nullptr, *Z = nullptr, *w = nullptr;       // outer (plain: FP64; mixed: FP32 inner)
+  void *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *b64 = nullptr;
+  double2* hd = nullptr;                   // device scalars (m + 2)
+  double2* hh = nullptr;                   // pinned host mirror
+  Prof prof;
+
+  void* alloc(size_t bytes) {
+    void* ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    allocs.push_back(ptr);
+    return ptr;
+  }
+  ~mg_ctx() {
+    for (void* q : allocs) cudaFree(q);
+    if (hh) cudaFreeHost(hh);
+  }
+  size_t fine_n() const { return (size_t)g.V * 12; }
+};
+
+namespace sapmg {
+
+// ------------------------------------------------------------ helpers
+static int smoother_sweeps(mg_ctx* c, const void* b, void* z, int n_sweeps, int nrhs) {
+  for (int it = 0; it < n_sweeps; ++it)
+    for (int col = 0; col < 2; ++col) {
+      ProfScope ps(c->prof, FAM_SAP, c->s);
+      TRY(launch_sap_colour(c->prec, c->g, z, b, c->Us, c->As, col, c->p.n_mr, nrhs, c->s));
+    }
+  return MG_OK;
+}
+
+static int fine_dirac(mg_ctx* c, int prec, void* out, const void* in, int nrhs) {
+  const void* U = prec == P64 ? c->U64 : (prec == P32 ? c->U32 : c->Us);
+  const void* A = prec == P64 ? c->A64 : (prec == P32 ? c->A32 : c->As);
+  if (!U || !A) return fail(MG_ERR_STATE, "requested precision not set up in this context");
+  ProfScope ps(c->prof, FAM_DIRAC, c->s);
+  return launch_dirac(prec, c->g, out, in, U, A, nrhs, c->s);
+}
+
+static int dot_to(mg_ctx* c, int type, const void* a, const void* b, size_t n, double2* out) {
+  const void* v[1] = {a};
+  return blas_multidot(type, v, 1, b, n, out, 0, nullptr, c->partial, c->s);
+}
+
+// Fixed-step GMRES from zero on a coarse level (Sec. 4: 12 steps on the coarse grid):
+// Arnoldi with classical Gram-Schmidt applied twice, all scalars on the device.
+static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k) {
+  const size_t n = L.n();
+  const int vt = c->vt;
+  const size_t eb = complex_bytes(vt);
+  auto Vj = [&](int j) { return (void*)((char*)L.V + (size_t)j * n * eb); };
+  TRY(dot_to(c, vt, L.b, L.b, n, L.beta2));
+  TRY(blas_normalize(vt, L.b, Vj(0), L.beta2, nullptr, n, c->s));
+  std::vector<const void*> vl;
+  for (int j = 0; j < k; ++j) {
+    {
+      ProfScope ps(c->prof, FAM_COARSE, c->s);
+      TRY(launch_coarse_apply(L.store, L.cg, L.M, Vj(j), L.w, 1, c->s));
+    }
+    vl.push_back(Vj(j));
+    double2* hcol = L.H + (size_t)j * 33;
+    TRY(blas_multidot(vt, vl.data(), j + 1, L.w, n, hcol, 0, nullptr, c->partial, c->s));
+    TRY(blas_multiaxpy(vt, L.w, vl.data(), j + 1, hcol, -1.0, n, c->s));
+    TRY(blas_multidot(vt, vl.data(), j + 1, L.w, n, hcol, 1, L.tmp, c->partial, c->s));
+    TRY(blas_multiaxpy(vt, L.w, vl.data(), j + 1, L.tmp, -1.0, n, c->s));
+    TRY(dot_to(c, vt, L.w, L.w, n, L.tmp + 40));
+    TRY(blas_normalize(vt, L.w, Vj(j + 1), L.tmp + 40, hcol + j + 1, n, c->s));
+  }
+  TRY(blas_hessenberg_solve(L.H, 33, k, L.beta2, L.y, c->s));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, n * eb, c->s));
+  TRY(blas_multiaxpy(vt, L.x, vl.data(), k, L.y, 1.0, n, c->s));
+  return MG_OK;
+}
+
+static int coarse_solve(mg_ctx* c, int level) {
+  if (level != 1) return fail(MG_ERR_ARG, "coarse level out of range");
+  return coarse_gmres(c, c->c1, c->p.coarse_iters);
+}
+
+// The multilevel cycle z = M v on the fine level (cycle vector type).
+static int cycle(mg_ctx* c, const void* v, void* z) {
+  const size_t n = c->fine_n();
+  if (c->p.n_levels == 1) {
+    SAPMG_CUDA_TRY(cudaMemsetAsync(z, 0, n * complex_bytes(c->vt), c->s));
+    return smoother_sweeps(c, v, z, c->p.nu_post, 1);
+  }
+  {
+    ProfScope ps(c->prof, FAM_RESTRICT, c->s);
+    TRY(launch_transfer0(true, c->prec, c->g, v, c->c1.b, c->Pv, c->N0, 1, c->s));
+  }
+  TRY(coarse_solve(c, 1));
+  {
+    ProfScope ps(c->prof, FAM_PROLONG, c->s);
+    TRY(launch_transfer0(false, c->prec, c->g, c->c1.x, z, c->Pv, c->N0, 1, c->s));
+  }
+  return smoother_sweeps(c, v, z, c->p.nu_post, 1);
+}
+
+// One cycle of flexible GMRES(m) on A e = r from e = x (x updated in place,
+// x += Z y).  r is the current residual (type ft), rnorm its norm.  Stops when
+// the least-squares residual estimate <= abs_tol, after m steps or at iters_left.
+// Orthogonalisation: classical Gram-Schmidt with a second pass when the norm
+// drops below 1/sqrt(2) of its value (Daniel-Gragg-Kaufman-Stewart criterion).
+static int fgmres_cycle(mg_ctx* c, int ft, int aprec, const void* r, double rnorm, void* x, double abs_tol,
+                        int iters_left, int& done, double& est) {
+  const size_t n = c->fine_n();
+  const size_t eb = complex_bytes(ft);
+  const int m = std::min(c->m, std::max(1, iters_left));
+  auto Vj = [&](int j) { return (void*)((char*)c->V + (size_t)j * n * eb); };
+  auto Zj = [&](int j) { return (void*)((char*)c->Z + (size_t)j * n * eb); };
+  std::vector<std::complex<double>> H((size_t)(m + 1) * m, 0.0), g(m + 1, 0.0), sn(m, 0.0);
+  std::vector<double> cs(m, 0.0);
+  TRY(blas_axpby(ft, make_double2(1.0 / rnorm, 0), r, make_double2(0, 0), Vj(0), n, c->s));
+  g[0] = rnorm;
+  std::vector<const void*> vl;
+  int j_done = 0;
+  est = rnorm;
+  for (int j = 0; j < m; ++j) {
+    TRY(cycle(c, Vj(j), Zj(j)));
+    TRY(fine_dirac(c, aprec, c->w, Zj(j), 1));
+    vl.push_back(Vj(j));
+    // h = V^dagger w and ||w||^2 in one fused pass
+    vl.push_back(c->w);
+    TRY(blas_multidot(ft, vl.data(), j + 2, c->w, n, c->hd, 0, nullptr, c->partial, c->s));
+    vl.pop_back();
+    TRY(blas_multiaxpy(ft, c->w, vl.data(), j + 1, c->hd, -1.0, n, c->s));
+    TRY(dot_to(c, ft, c->w, c->w, n, c->hd + j + 2));
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * (j + 3), cudaMemcpyDeviceToHost, c->s));
+    SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+    for (int i = 0; i <= j; ++i) H[i + (size_t)j * (m + 1)] = std::complex<double>(c->hh[i].x, c->hh[i].y);
+    double before = c->hh[j + 1].x, after = c->hh[j + 2].x;
+    if (after < 0.5 * before) {
+      TRY(blas_multidot(ft, vl.data(), j + 1, c->w, n, c->hd, 0, nullptr, c->partial, c->s));
+      TRY(blas_multiaxpy(ft, c->w, vl.data(), j + 1, c->hd, -1.0, n, c->s));
+      TRY(dot_to(c, ft, c->w, c->w, n, c->hd + j + 2));
+      SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * (j + 3), cudaMemcpyDeviceToHost, c->s));
+      SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+      for (int i = 0; i <= j; ++i) H[i + (size_t)j * (m + 1)] += std::complex<double>(c->hh[i].x, c->hh[i].y);
+      after = c->hh[j + 2].x;
+    }
+    const double hn = std::sqrt(std::max(after, 0.0));
+    H[j + 1 + (size_t)j * (m + 1)] = hn;
+    // Givens rotations on column j
+    for (int i = 0; i < j; ++i) {
+      auto& a = H[i + (size_t)j * (m + 1)];
+      auto& b = H[i + 1 + (size_t)j * (m + 1)];
+      const std::complex<double> t = cs[i] * a + sn[i] * b;
+      b = -std::conj(sn[i]) * a + cs[i] * b;
+      a = t;
+    }
+    {
+      auto& a = H[j + (size_t)j * (m + 1)];
+      auto& b = H[j + 1 + (size_t)j * (m + 1)];
+      const double na = std::abs(a), nb = std::abs(b);
+      const double den = std::sqrt(na * na + nb * nb);
+      if (den == 0.0) { cs[j] = 1; sn[j] = 0; }
+      else if (na == 0.0) { cs[j] = 0; sn[j] = 1; }
+      else { cs[j] = na / den; sn[j] = (a / na) * std::conj(b) / den; }
+      a = cs[j] * a + sn[j] * b;
+      b = 0.0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+    }
+    j_done = j + 1;
+    est = std::abs(g[j + 1]);
+    if (est <= abs_tol || hn == 0.0 || j + 1 == m) break;
+    TRY(blas_axpby(ft, make_double2(1.0 / hn, 0), c->w, make_double2(0, 0), Vj(j + 1), n, c->s));
+  }
+  // back substitution and x += Z y
+  std::vector<std::complex<double>> y(j_done);
+  for (int i = j_done - 1; i >= 0; --i) {
+    std::complex<double> s = g[i];
+    for (int k = i + 1; k < j_done; ++k) s -= H[i + (size_t)k * (m + 1)] * y[k];
+    const auto d = H[i + (size_t)i * (m + 1)];
+    y[i] = std::abs(d) > 0 ? s / d : 0.0;
+  }
+  for (int i = 0; i < j_done; ++i) c->hh[i] = make_double2(y[i].real(), y[i].imag());
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hd, c->hh, sizeof(double2) * j_done, cudaMemcpyHostToDevice, c->s));
+  std::vector<const void*> zl;
+  for (int i = 0; i < j_done; ++i) zl.push_back(Zj(i));
+  TRY(blas_multiaxpy(ft, x, zl.data(), j_done, c->hd, 1.0, n, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));   // hh is reused by the next cycle
+  done = j_done;
+  return MG_OK;
+}
+
+static double host_norm(mg_ctx* c, int type, const void* x, size_t n, int& rc) {
+  rc = dot_to(c, type, x, x, n, c->hd + c->m + 1);
+  if (rc < 0) return 0;
+  cudaMemcpyAsync(c->hh + c->m + 1, c->hd + c->m + 1, sizeof(double2), cudaMemcpyDeviceToHost, c->s);
+  if (cudaStreamSynchronize(c->s) != cudaSuccess) { rc = fail(MG_ERR_CUDA, "synchronize failed"); return 0; }
+  return std::sqrt(std::max(c->hh[c->m + 1].x, 0.0));
+}
+
+// Solve one right-hand side: b64 (blocked FP64) -> x64 (blocked FP64).
+static int solve_one(mg_ctx* c, int& iters, int& restarts, double& relres) {
+  const size_t n = c->fine_n();
+  int rc = 0;
+  const double bn = host_norm(c, P64, c->b64, n, rc);
+  TRY(rc);
+  SAPMG_CUDA_TRY(cudaMemsetAsync(c->x64, 0, n * 16, c->s));
+  iters = 0;
+  restarts = 0;
+  if (bn == 0.0) { relres = 0; return MG_OK; }
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->r64, c->b64, n * 16, cudaMemcpyDeviceToDevice, c->s));
+  const double tol = c->p.tol * bn;
+  for (;;) {
+    const double rn = host_norm(c, P64, c->r64, n, rc);
+    TRY(rc);
+    relres = rn / bn;
+    if (c->p.verbose) std::fprintf(stderr, "[sapmg] outer %d iters %d relres %.3e\n", restarts, iters, relres);
+    if (rn <= tol) return MG_OK;
+    if (iters >= c->p.maxiter) return MG_NOT_CONVERGED;
+    int done = 0;
+    double est = 0;
+    if (c->prec == P64) {
+      TRY(fgmres_cycle(c, P64, P64, c->r64, rn, c->x64, tol, c->p.maxiter - iters, done, est));
+    } else {
+      // FP64 defect correction around an FP32 flexible GMRES cycle
+      TRY(blas_axpby2(P64, make_double2(1.0 / rn, 0), c->r64, P32, make_double2(0, 0), c->t64, n, c->s));
+      SAPMG_CUDA_TRY(cudaMemsetAsync(c->io_b, 0, n * 8, c->s));
+      const double inner = std::max(2e-6, 0.5 * tol / rn);
+      TRY(fgmres_cycle(c, P32, P32, c->t64, 1.0, c->io_b, inner, c->p.maxiter - iters, done, est));
+      TRY(blas_axpby2(P32, make_double2(rn, 0), c->io_b, P64, make_double2(1, 0), c->x64, n, c->s));
+    }
+    iters += done;
+    restarts += 1;
+    TRY(fine_dirac(c, P64, c->r64, c->x64, 1));
+    TRY(blas_axpby(P64, make_double2(1, 0), c->b64, make_double2(-1, 0), c->r64, n, c->s));
+    if (done == 0) return MG_NOT_CONVERGED;
+  }
+}
+
+// ------------------------------------------------------------ set-up
+__global__ void nonfinite_kernel(const double* __restrict__ x, size_t n, int* flag) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) *flag = 1;
+}
+
+static int check_finite(mg_ctx* c, const double* x, size_t n_doubles) {
+  int* flag = (int*)c->alloc(sizeof(int));
+  if (!flag) return fail(MG_ERR_OOM, "allocation failed");
+  SAPMG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), c->s));
+  nonfinite_kernel<<<1024, 256, 0, c->s>>>(x, n_doubles, flag);
+  int h = 0;
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  return h ? fail(MG_ERR_NONFINITE, "non-finite value in input field") : MG_OK;
+}
+
+// Global orthonormalisation of the N set-up vectors (FP64): classical
+// Gram-Schmidt against the previous vectors, applied twice, then normalise.
+static int orthonormalise(mg_ctx* c, void* V, int N) {
+  const size_t n = c->fine_n();
+  auto Vk = [&](int k) { return (void*)((char*)V + (size_t)k * n * 16); };
+  std::vector<const void*> vl;
+  for (int k = 0; k < N; ++k) {
+    for (int pass = 0; pass < 2 && k > 0; ++pass) {
+      TRY(blas_multidot(P64, vl.data(), k, Vk(k), n, c->hd, 0, nullptr, c->partial, c->s));
+      TRY(blas_multiaxpy(P64, Vk(k), vl.data(), k, c->hd, -1.0, n, c->s));
+    }
+    TRY(dot_to(c, P64, Vk(k), Vk(k), n, c->hd + 40));
+    TRY(blas_normalize(P64, Vk(k), Vk(k), c->hd + 40, nullptr, n, c->s));
+    vl.push_back(Vk(k));
+  }
+  return MG_OK;
+}
+
+static int setup_level0(mg_ctx* c) {
+  const size_t n = c->fine_n();
+  const int N = c->N0;
+  const mg_params& p = c->p;
+  c->V64 = c->alloc((size_t)N * n * 16);
+  if (!c->V64) return fail(MG_ERR_OOM, "test vectors");
+  if (p.init_vectors) {
+    TRY(launch_pack_spinor(P64, p.init_vectors, P64, c->V64, c->g, N, c->s));
+  } else {
+    TRY(launch_draw_vectors(c->g, c->V64, N, p.seed, 3ull /* test-vector stream */, c->s));
+  }
+  // bootstrap part 1: nu sweeps of the smoother's iteration matrix (SAP on D x = 0), kept orthonormal
+  for (int it = 0; it < p.setup_iters; ++it) {
+    for (int k = 0; k < N; ++k) {
+      void* vk = (char*)c->V64 + (size_t)k * n * 16;
+      if (c->vt == P64) {
+        TRY(smoother_sweeps(c, c->zero_f, vk, 1, 1));
+      } else {
+        TRY(blas_axpby2(P64, make_double2(1, 0), vk, P32, make_double2(0, 0), c->io_b, n, c->s));
+        TRY(smoother_sweeps(c, c->zero_f, c->io_b, 1, 1));
+        TRY(blas_axpby2(P32, make_double2(1, 0), c->io_b, P64, make_double2(0, 0), vk, n, c->s));
+      }
+    }
+    TRY(orthonormalise(c, c->V64, N));
+  }
+  TRY(launch_block_gs0(c->g, c->V64, N, c->s));
+  c->Pv = c->alloc((size_t)N * n * complex_bytes(c->prec));
+  if (!c->Pv) return fail(MG_ERR_OOM, "interpolation");
+  TRY(launch_store_p0(c->prec, c->g, c->V64, c->Pv, N, c->s));
+  // Galerkin coarse operator
+  CoarseLevel& L = c->c1;
+  for (int mu = 0; mu < 4; ++mu) L.cg.L[mu] = c->g.nb[mu];
+  L.cg.nsites = c->g.nblocks;
+  L.cg.n2 = 2 * N;
+  const size_t msz = (size_t)L.cg.nsites * 9 * L.cg.n2 * L.cg.n2;
+  L.M64 = c->alloc(msz * 16);
+  if (!L.M64) return fail(MG_ERR_OOM, "coarse operator");
+  TRY(launch_assemble0(c->g, c->V64, c->U64, c->A64, L.M64, N, c->s));
+  L.store = c->prec;
+  if (c->prec == P64) {
+    L.M = L.M64;
+  } else {
+    L.M = c->alloc(msz * complex_bytes(c->prec));
+    if (!L.M) return fail(MG_ERR_OOM, "coarse operator");
+    TRY(launch_convert(P64, L.M64, c->prec, L.M, msz, c->s));
+  }
+  return MG_OK;
+}
+
+static int alloc_coarse_ws(mg_ctx* c, CoarseLevel& L, int kmax) {
+  const size_t n = L.n(), eb = complex_bytes(c->vt);
+  L.V = c->alloc((size_t)(kmax + 1) * n * eb);
+  L.w = c->alloc(n * eb);
+  L.x = c->alloc(n * eb);
+  L.b = c->alloc(n * eb);
+  L.H = (double2*)c->alloc(sizeof(double2) * 33 * 33);
+  L.tmp = (double2*)c->alloc(sizeof(double2) * 64);
+  L.beta2 = (double2*)c->alloc(sizeof(double2));
+  L.y = (double2*)c->alloc(sizeof(double2) * 33);
+  if (!L.V || !L.w || !L.x || !L.b || !L.H || !L.tmp || !L.beta2 || !L.y) return fail(MG_ERR_OOM, "coarse workspace");
+  SAPMG_CUDA_TRY(cudaMemsetAsync(L.H, 0, sizeof(double2) * 33 * 33, c->s));
+  return MG_OK;
+}
+
+static int validate(const mg_params* p) {
+  for (int mu = 0; mu < 4; ++mu)
+    if (p->dims[mu] <= 0 || p->dims[mu] % 8 != 0)
+      return fail(MG_ERR_ARG, "every lattice dim must be a positive multiple of 8 (even number of 4^4 blocks)");
+  if (p->n_levels < 1 || p->n_levels > 2) return fail(MG_ERR_ARG, "n_levels must be 1 or 2");
+  if (p->n_levels >= 2 && (p->n_vec[0] < 1 || p->n_vec[0] > 32)) return fail(MG_ERR_ARG, "n_vec[0] must be in 1..32");
+  if (p->setup_iters < 0 || p->n_mr < 0 || p->nu_post < 0) return fail(MG_ERR_ARG, "negative iteration count");
+  if (p->coarse_iters < 1 || p->coarse_iters > 32) return fail(MG_ERR_ARG, "coarse_iters must be in 1..32");
+  if (p->fgmres_m < 1 || p->fgmres_m > 256) return fail(MG_ERR_ARG, "fgmres_m must be in 1..256");
+  if (!(p->tol > 0)) return fail(MG_ERR_ARG, "tol must be positive");
+  if (p->maxiter < 1) return fail(MG_ERR_ARG, "maxiter must be positive");
+  if (p->precision < MG_FP64 || p->precision > MG_BF16) return fail(MG_ERR_ARG, "unknown precision");
+  if (p->nrhs_max < 1) return fail(MG_ERR_ARG, "nrhs_max must be positive");
+  return MG_OK;
+}
+
+static int do_setup(mg_ctx* c, const double* U) {
+  const mg_params& p = c->p;
+  const size_t n = c->fine_n();
+  const size_t ulinks = (size_t)c->g.V * 4 * 9, aslots = (size_t)c->g.V * 36;
+  TRY(check_finite(c, U, ulinks * 2));
+  c->U64 = c->alloc(ulinks * 16);
+  c->A64 = c->alloc(aslots * 16);
+  if (!c->U64 || !c->A64) return fail(MG_ERR_OOM, "gauge field");
+  TRY(launch_pack_gauge(P64, c->g, U, c->U64, p.antiperiodic_t, c->s));
+  TRY(launch_clover_build(c->g, U, c->A64, c->m0, c->csw, c->s));
+  if (c->prec != P64) {
+    c->U32 = c->alloc(ulinks * 8);
+    c->A32 = c->alloc(aslots * 8);
+    if (!c->U32 || !c->A32) return fail(MG_ERR_OOM, "gauge field");
+    TRY(launch_convert(P64, c->U64, P32, c->U32, ulinks, c->s));
+    TRY(launch_convert(P64, c->A64, P32, c->A32, aslots, c->s));
+    if (c->prec == P32) {
+      c->Us = c->U32;
+      c->As = c->A32;
+    } else {
+      c->Us = c->alloc(ulinks * 4);
+      c->As = c->alloc(aslots * 4);
+      if (!c->Us || !c->As) return fail(MG_ERR_OOM, "gauge field");
+      TRY(launch_convert(P64, c->U64, c->prec, c->Us, ulinks, c->s));
+      TRY(launch_convert(P64, c->A64, c->prec, c->As, aslots, c->s));
+    }
+  } else {
+    c->Us = c->U64;
+    c->As = c->A64;
+  }
+  // workspace
+  const size_t eb = complex_bytes(c->vt);
+  c->partial = (double2*)c->alloc(sizeof(double2) * kMaxReduceCta * 8);
+  c->zero_f = c->alloc(n * eb);
+  c->io_a = c->alloc((size_t)p.nrhs_max * n * 16);
+  c->io_b = c->alloc((size_t)p.nrhs_max * n * 16);
+  c->m = p.fgmres_m;
+  const size_t ft = complex_bytes(c->vt);
+  c->V = c->alloc((size_t)(c->m + 1) * n * ft);
+  c->Z = c->alloc((size_t)c->m * n * ft);
+  c->w = c->alloc(n * ft);
+  c->x64 = c->alloc(n * 16);
+  c->r64 = c->alloc(n * 16);
+  c->t64 = c->alloc(n * 16);
+  c->b64 = c->alloc(n * 16);
+  c->hd = (double2*)c->alloc(sizeof(double2) * (c->m + 64));
+  if (!c->partial || !c->zero_f || !c->io_a || !c->io_b || !c->V || !c->Z || !c->w || !c->x64 || !c->r64 ||
+      !c->t64 || !c->b64 || !c->hd)
+    return fail(MG_ERR_OOM, "workspace");
+  if (cudaMallocHost((void**)&c->hh, sizeof(double2) * (c->m + 64)) != cudaSuccess) return fail(MG_ERR_OOM, "host");
+  SAPMG_CUDA_TRY(cudaMemsetAsync(c->zero_f, 0, n * eb, c->s));
+  if (p.n_levels >= 2) {
+    c->N0 = p.n_vec[0];
+    TRY(setup_level0(c));
+    TRY(alloc_coarse_ws(c, c->c1, p.coarse_iters));
+  }
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  return MG_OK;
+}
+
+// canonical <-> blocked staging for the component entry points
+static int stage_in(mg_ctx* c, const void* in, int prec, bool blocked, int nrhs, const void** out_ptr) {
+  if (blocked) { *out_ptr = in; return MG_OK; }
+  const int t = prec == P64 ? P64 : P32;
+  TRY(launch_pack_spinor(t, in, t, c->io_a, c->g, nrhs, c->s));
+  *out_ptr = c->io_a;
+  return MG_OK;
+}
+
+}  // namespace sapmg
+
+// ============================================================ C-ABI
+extern "C" {
+
+int mg_default_params(mg_params* p) {
+  if (!p) return fail(MG_ERR_ARG, "null params");
+  std::memset(p, 0, sizeof(*p));
+  p->n_levels = 1;
+  for (int mu = 0; mu < 4; ++mu) { p->agg2[mu] = 2; p->sap_block2[mu] = 2; }
+  p->n_vec[0] = 8;
+  p->n_vec[1] = 8;
+  p->setup_iters = 3;
+  p->n_mr = 4;
+  p->nu_post = 2;
+  p->coarse_iters = 12;
+  p->inner_iters = 8;
+  p->fgmres_m = 20;
+  p->tol = 1e-10;
+  p->maxiter = 1000;
+  p->precision = MG_FP64;
+  p->nrhs_max = 1;
+  p->seed = 1;
+  return MG_OK;
+}
+
+const char* mg_last_error(void) { return g_err.c_str(); }
+
+unsigned long mg_sizeof_params(void) { return (unsigned long)sizeof(mg_params); }
+
+int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx** out) {
+  if (!U || !p || !out) return fail(MG_ERR_ARG, "null argument");
+  *out = nullptr;
+  TRY(validate(p));
+  mg_ctx* c = new mg_ctx();
+  c->p = *p;
+  c->g = make_geom(p->dims);
+  c->s = (cudaStream_t)p->stream;
+  c->prec = p->precision;
+  c->vt = p->precision == MG_FP64 ? P64 : P32;
+  c->m0 = m0;
+  c->csw = c_sw;
+  const int rc = do_setup(c, U);
+  if (rc < 0) {
+    cudaStreamSynchronize(c->s);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+void mg_destroy(mg_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->s);
+  delete c;
+}
+
+int dirac_apply(mg_ctx* c, const void* in, void* out, int prec, int nrhs) {
+  if (!c || !in || !out || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
+  const bool blocked = (prec & MG_BLOCKED) != 0;
+  prec &= 0xff;
+  if (prec < MG_FP64 || prec > MG_BF16) return fail(MG_ERR_ARG, "unknown precision");
+  if (!blocked && nrhs > c->p.nrhs_max) return fail(MG_ERR_ARG, "nrhs exceeds nrhs_max for canonical layout");
+  const int t = prec == P64 ? P64 : P32;
+  const void* src;
+  TRY(stage_in(c, in, prec, blocked, nrhs, &src));
+  void* dst = blocked ? out : c->io_b;
+  TRY(fine_dirac(c, prec, dst, src, nrhs));
+  if (!blocked) TRY(launch_unpack_spinor(t, dst, t, out, c->g, nrhs, c->s));
+  return MG_OK;
+}
+
+int sap_smooth(mg_ctx* c, const void* b, void* z, int n_sweeps, int prec, int nrhs) {
+  if (!c || !b || !z || nrhs < 1 || n_sweeps < 0) return fail(MG_ERR_ARG, "bad argument");
+  const bool blocked = (prec & MG_BLOCKED) != 0;
+  prec &= 0xff;
+  if (prec != c->prec) return fail(MG_ERR_STATE, "sap_smooth runs in the context's smoother precision");
+  if (!blocked && nrhs > c->p.nrhs_max) return fail(MG_ERR_ARG, "nrhs exceeds nrhs_max for canonical layout");
+  const int t = prec == P64 ? P64 : P32;
+  if (blocked) return smoother_sweeps(c, b, z, n_sweeps, nrhs);
+  TRY(launch_pack_spinor(t, b, t, c->io_a, c->g, nrhs, c->s));
+  TRY(launch_pack_spinor(t, z, t, c->io_b, c->g, nrhs, c->s));
+  TRY(smoother_sweeps(c, c->io_a, c->io_b, n_sweeps, nrhs));
+  return launch_unpack_spinor(t, c->io_b, t, z, c->g, nrhs, c->s);
+}
+
+int mg_solve(mg_ctx* c, const double* b, double* z, int nrhs, mg_solve_info* info) {
+  if (!c || !b || !z || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t n = c->fine_n();
+  int status = MG_OK, it_sum = 0, rs_sum = 0;
+  double worst = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    TRY(launch_pack_spinor(P64, b + r * n * 2, P64, c->b64, c->g, 1, c->s));
+    int it = 0, rs = 0;
+    double rel = 0;
+    const int rc = solve_one(c, it, rs, rel);
+    if (rc < 0) return rc;
+    if (rc == MG_NOT_CONVERGED) status = MG_NOT_CONVERGED;
+    TRY(launch_unpack_spinor(P64, c->x64, P64, z + r * n * 2, c->g, 1, c->s));
+    it_sum += it;
+    rs_sum += rs;
+    worst = std::max(worst, rel);
+  }
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  if (info) {
+    info->iterations = it_sum;
+    info->restarts = rs_sum;
+    info->relres = worst;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->precond_seconds = 0;
+  }
+  return status;
+}
+
+int mg_pack_spinor(mg_ctx* c, const void* canonical, void* blocked, int prec, int nrhs) {
+  if (!c || !canonical || !blocked || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
+  const int t = (prec & 0xff) == P64 ? P64 : P32;
+  return launch_pack_spinor(t, canonical, t, blocked, c->g, nrhs, c->s);
+}
+
+int mg_unpack_spinor(mg_ctx* c, const void* blocked, void* canonical, int prec, int nrhs) {
+  if (!c || !canonical || !blocked || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
+  const int t = (prec & 0xff) == P64 ? P64 : P32;
+  return launch_unpack_spinor(t, blocked, t, canonical, c->g, nrhs, c->s);
+}
+
+int mg_clover_export(mg_ctx* c, double* out) {
+  if (!c || !out) return fail(MG_ERR_ARG, "bad argument");
+  return launch_clover_export(c->g, c->A64, out, c->s);
+}
+
+int mg_get_vectors(mg_ctx* c, int level, double* out) {
+  if (!c || !out) return fail(MG_ERR_ARG, "bad argument");
+  if (level != 0 || !c->V64) return fail(MG_ERR_STATE, "no test vectors on that level");
+  return launch_unpack_spinor(P64, c->V64, P64, out, c->g, c->N0, c->s);
+}
+
+int mg_get_coarse_op(mg_ctx* c, int level, double* out) {
+  if (!c || !out) return fail(MG_ERR_ARG, "bad argument");
+  if (level != 1 || !c->c1.M64) return fail(MG_ERR_STATE, "no coarse operator on that level");
+  return launch_coarse_export(P64, c->c1.cg, c->c1.M64, out, c->s);
+}
+
+int mg_restrict(mg_ctx* c, int level, const void* in, void* out, int prec) {
+  if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
+  const bool blocked = (prec & MG_BLOCKED) != 0;
+  prec &= 0xff;
+  if (level != 0 || !c->Pv) return fail(MG_ERR_STATE, "no interpolation on that level");
+  if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
+  const void* src;
+  TRY(stage_in(c, in, prec, blocked, 1, &src));
+  ProfScope ps(c->prof, FAM_RESTRICT, c->s);
+  return launch_transfer0(true, c->prec, c->g, src, out, c->Pv, c->N0, 1, c->s);
+}
+
+int mg_prolong(mg_ctx* c, int level, const void* in, void* out, int prec) {
+  if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
+  const bool blocked = (prec & MG_BLOCKED) != 0;
+  prec &= 0xff;
+  if (level != 0 || !c->Pv) return fail(MG_ERR_STATE, "no interpolation on that level");
+  if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
+  void* dst = blocked ? out : c->io_b;
+  {
+    ProfScope ps(c->prof, FAM_PROLONG, c->s);
+    TRY(launch_transfer0(false, c->prec, c->g, in, dst, c->Pv, c->N0, 1, c->s));
+  }
+  if (!blocked) {
+    const int t = prec == P64 ? P64 : P32;
+    TRY(launch_unpack_spinor(t, dst, t, out, c->g, 1, c->s));
+  }
+  return MG_OK;
+}
+
+int mg_coarse_apply(mg_ctx* c, int level, const void* in, void* out, int prec) {
+  if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
+  prec &= 0xff;
+  if (level != 1 || !c->c1.M) return fail(MG_ERR_STATE, "no coarse operator on that level");
+  if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
+  ProfScope ps(c->prof, FAM_COARSE, c->s);
+  return launch_coarse_apply(c->c1.store, c->c1.cg, c->c1.M, in, out, 1, c->s);
+}
+
+int mg_coarse_solve(mg_ctx* c, int level, const void* in, void* out, int prec) {
+  if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
+  prec &= 0xff;
+  if (level != 1 || !c->c1.M) return fail(MG_ERR_STATE, "no coarse operator on that level");
+  if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
+  const size_t bytes = c->c1.n() * complex_bytes(c->vt);
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->c1.b, in, bytes, cudaMemcpyDeviceToDevice, c->s));
+  TRY(coarse_solve(c, 1));
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(out, c->c1.x, bytes, cudaMemcpyDeviceToDevice, c->s));
+  return MG_OK;
+}
+
+int mg_precondition(mg_ctx* c, const void* v, void* z, int prec) {
+  if (!c || !v || !z) return fail(MG_ERR_ARG, "bad argument");
+  const bool blocked = (prec & MG_BLOCKED) != 0;
+  prec &= 0xff;
+  if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
+  const void* src;
+  TRY(stage_in(c, v, prec, blocked, 1, &src));
+  void* dst = blocked ? z : c->io_b;
+  TRY(cycle(c, src, dst));
+  if (!blocked) {
+    const int t = prec == P64 ? P64 : P32;
+    TRY(launch_unpack_spinor(t, dst, t, z, c->g, 1, c->s));
+  }
+  return MG_OK;
+}
+
+int mg_set_profiling(mg_ctx* c, int on) {
+  if (!c) return fail(MG_ERR_ARG, "bad argument");
+  c->prof.on = on != 0;
+  return MG_OK;
+}
+
+int mg_get_profile(mg_ctx* c, int family, long long* launches, double* ms) {
+  if (!c || family < 0 || family >= FAM_N) return fail(MG_ERR_ARG, "bad argument");
+  c->prof.drain();
+  if (launches) *launches = c->prof.launches[family];
+  if (ms) *ms = c->prof.ms[family];
+  return MG_OK;
+}
+
+int mg_reset_profile(mg_ctx* c) {
+  if (!c) return fail(MG_ERR_ARG, "bad argument");
+  c->prof.drain();
+  for (int f = 0; f < FAM_N; ++f) { c->prof.launches[f] = 0; c->prof.ms[f] = 0; }
+  return MG_OK;
+}
+
+}  // extern "C"

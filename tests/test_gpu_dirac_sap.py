@@ -1,0 +1,130 @@
+"""GPU parity of the Dirac operator (Sec. 1, Eq. 1.1) and of red-black Schwarz
+sweeps (Sec. 2, Algorithm 1) against the FP64 oracle, through the C-ABI."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.dirac import WilsonClover
+from oracle.sap import BlockDecomposition, sap_sweep
+from tests.gpu_util import torch_cuda, dev, host, rel, round_storage
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((8, 8, 8, 8), 0.5, -0.2, False), ((8, 16, 8, 24), 0.7, 0.1, True)]
+
+
+def _solver(torch, u, csw, m0, ap, **kw):
+    from paper_1202_2462_gb300 import Solver
+    return Solver(dev(torch, u), csw, m0, antiperiodic_t=int(ap), **kw)
+
+
+@pytest.mark.parametrize("dims,eps,m0,ap", CASES)
+def test_dirac_fp64_parity(dims, eps, m0, ap):
+    torch = torch_cuda()
+    u = synth.random_gauge_field(dims, eps, 11)
+    op = WilsonClover(u, m0, 1.0, antiperiodic_t=ap)
+    psi = synth.random_spinor(dims, 12, nvec=2)
+    ref = op.apply(psi)
+    s = _solver(torch, u, 1.0, m0, ap, nrhs_max=2)
+    out = host(s.dirac(dev(torch, psi)))
+    s.close()
+    assert rel(out, ref) < 1e-14
+    assert np.max(np.abs(out - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("dims,eps,m0,ap", CASES)
+def test_dirac_fp32_parity(dims, eps, m0, ap):
+    """FP32 storage and arithmetic: <= 1e-5 relative against the exact FP64 operator."""
+    torch = torch_cuda()
+    from paper_1202_2462_gb300 import MG_FP32
+    u = synth.random_gauge_field(dims, eps, 13)
+    op = WilsonClover(u, m0, 1.0, antiperiodic_t=ap)
+    psi = synth.random_spinor(dims, 14)
+    ref = op.apply(psi)
+    s = _solver(torch, u, 1.0, m0, ap, precision="fp32")
+    out = host(s.dirac(dev(torch, psi, torch.complex64), MG_FP32)).astype(np.complex128)
+    s.close()
+    assert rel(out, ref) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_dirac_half_storage_parity(prec):
+    """FP16/BF16-stored links and clover with FP32 arithmetic: compared with the
+    oracle applied to the identically rounded fields (1e-6), and with the exact
+    operator at the storage format's accuracy."""
+    torch = torch_cuda()
+    from paper_1202_2462_gb300 import PRECISIONS
+    dims = (8, 8, 8, 16)
+    u = synth.random_gauge_field(dims, 0.6, 15)
+    op = WilsonClover(u, -0.1, 1.0)
+    opr = WilsonClover(round_storage(u, prec), -0.1, 1.0)
+    opr.a = round_storage(op.a, prec)
+    psi = synth.random_spinor(dims, 16).astype(np.complex64).astype(np.complex128)
+    s = _solver(torch, u, 1.0, -0.1, False, precision=prec)
+    out = host(s.dirac(dev(torch, psi, torch.complex64), PRECISIONS[prec])).astype(np.complex128)
+    s.close()
+    assert rel(out, opr.apply(psi)) < 2e-6
+    assert rel(out, op.apply(psi)) < (2e-3 if prec == "fp16" else 1.5e-2)
+
+
+def test_dirac_zero_field():
+    torch = torch_cuda()
+    dims = (8, 8, 8, 8)
+    u = synth.random_gauge_field(dims, 0.5, 17)
+    s = _solver(torch, u, 1.0, 0.0, False)
+    out = host(s.dirac(torch.zeros((1, 8, 8, 8, 8, 4, 3), dtype=torch.complex128, device="cuda")))
+    s.close()
+    assert np.all(out == 0)
+
+
+@pytest.mark.parametrize("dims,eps,m0,ap", CASES)
+def test_sap_sweep_fp64_parity(dims, eps, m0, ap):
+    torch = torch_cuda()
+    u = synth.random_gauge_field(dims, eps, 21)
+    op = WilsonClover(u, m0, 1.0, antiperiodic_t=ap)
+    bl = BlockDecomposition(dims, (4, 4, 4, 4))
+    b = synth.random_spinor(dims, 22)
+    z0 = synth.random_spinor(dims, 23)
+    ref = sap_sweep(op, bl, b, sap_sweep(op, bl, b, z0, 4), 4)
+    s = _solver(torch, u, 1.0, m0, ap, n_mr=4)
+    z = dev(torch, z0)
+    s.smooth(dev(torch, b), z, 2)
+    out = host(z)
+    s.close()
+    assert rel(out, ref) < 1e-13
+
+
+@pytest.mark.parametrize("n_mr", [0, 1, 5])
+def test_sap_sweep_fp32_parity(n_mr):
+    torch = torch_cuda()
+    dims = (8, 8, 16, 8)
+    u = synth.random_gauge_field(dims, 0.5, 24)
+    op = WilsonClover(u, 0.0, 1.0)
+    bl = BlockDecomposition(dims, (4, 4, 4, 4))
+    b = synth.random_spinor(dims, 25)
+    z0 = np.zeros_like(b)
+    ref = sap_sweep(op, bl, b, z0, n_mr)
+    s = _solver(torch, u, 1.0, 0.0, False, n_mr=n_mr, precision="fp32")
+    z = dev(torch, z0, torch.complex64)
+    s.smooth(dev(torch, b, torch.complex64), z, 1)
+    out = host(z).astype(np.complex128)
+    s.close()
+    if n_mr == 0:
+        assert np.all(out == 0)
+    else:
+        assert rel(out, ref) < 2e-6
+
+
+def test_sap_zero_rhs_block_stays_finite():
+    """A block whose residual is exactly zero: MR takes alpha = 0 (no 0/0)."""
+    torch = torch_cuda()
+    dims = (8, 8, 8, 8)
+    u = synth.random_gauge_field(dims, 0.5, 26)
+    s = _solver(torch, u, 1.0, 0.0, False)
+    b = torch.zeros((1, 8, 8, 8, 8, 4, 3), dtype=torch.complex128, device="cuda")
+    z = torch.zeros_like(b)
+    s.smooth(b, z, 3)
+    out = host(z)
+    s.close()
+    assert np.all(out == 0)
