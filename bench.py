@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the SAP-multilevel solver on one GB300 (or N replicas).
+
+One step = one call of mg_solve on the workload's right-hand sides, to a
+relative residual of 1e-10 (verified in FP64 by the library), with the set-up
+done once before the timed region and reported separately (as the paper's
+tables do).  The default workload is the 32^3 x 64 lattice with the 12
+spin-colour point sources, solved by the mixed-precision form (FP32
+arithmetic, BF16-stored links, clover, test vectors and coarse operators; FP64
+defect correction).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
+FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (nominal)
+
+
+def flops_dirac_site():
+    return 1848.0
+
+
+def flops_sap_site(n_mr):
+    # residual (D + subtraction) + n_MR x (block operator (6 hops on average) + dots + updates) + update
+    return 1896.0 + 1854.0 * n_mr
+
+
+def bytes_sap_site(prec):
+    spinor = 4 * 12 * (16 if prec == "fp64" else 8)          # b, z, halo z read; z written
+    store = {"fp64": 16, "fp32": 8, "fp16": 4, "bf16": 4}[prec]
+    return spinor + 2 * 36 * store                              # links (4 x 9 complex) + clover (36 slots)
+
+
+def bytes_dirac_site(prec):
+    spinor = 2 * 12 * (16 if prec == "fp64" else 8)
+    store = {"fp64": 16, "fp32": 8, "fp16": 4, "bf16": 4}[prec]
+    return spinor + 2 * 36 * store
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.lines = []
+        self.proc = None
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def make_rhs(wl, dims):
+    if wl["rhs"] == "point12":
+        return synth.point_sources(dims)
+    if wl["rhs"] == "z2":
+        return synth.z2_spinor(dims, wl["rhs_seed"])[None]
+    return synth.random_spinor(dims, wl["rhs_seed"])[None]
+
+
+def solver_kwargs(wl, precision, nrhs):
+    return dict(n_levels=wl["n_levels"], n_vec=tuple(wl["n_vec"]), setup_iters=wl["setup_iters"],
+                n_mr=wl["n_mr"], nu_post=wl["nu_post"], coarse_iters=wl["coarse_iters"],
+                fgmres_m=wl["fgmres_m"], tol=wl["tol"], maxiter=wl.get("maxiter", 500),
+                precision=precision, nrhs_max=nrhs, seed=wl.get("vec_seed", 1))
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(wl, steps=1):
+    """Time one multilevel-preconditioned FGMRES iteration of the oracle on a
+    sub-lattice of 1/128 of the workload's volume (same method parameters, a
+    hierarchy from the initial random vectors); returns seconds per iteration
+    at the sub-volume and the sub-lattice dims."""
+    from oracle.dirac import WilsonClover
+    from oracle.mg import Multigrid
+    dims = tuple(wl["dims"])
+    sub = (dims[0] // 2, dims[1] // 2, dims[2] // 4, dims[3] // 8)
+    u = synth.random_gauge_field(sub, wl["eps"], wl["gauge_seed"])
+    op = WilsonClover(u, wl["m0"], wl["c_sw"])
+    n = wl["n_vec"][0]
+    mg = Multigrid(op, dict(n_levels=2, n_vec=(n,), setup_iters=0, n_mr=wl["n_mr"], nu_post=wl["nu_post"],
+                            coarse_iters=wl["coarse_iters"], sap_block=((4, 4, 4, 4),), agg=((4, 4, 4, 4),)),
+                   synth.test_vector_draw(sub, n, 1))
+    v = synth.random_spinor(sub, 7)
+    v = v / np.linalg.norm(v)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        z = mg.cycle(0, v)
+        w = op.apply(z)
+        h = np.vdot(v, w)                 # one orthogonalisation step of the Arnoldi process
+        w = w - h * v
+        times.append(time.perf_counter() - t0)
+    return times, sub
+
+
+def run_reference(a, wl):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    dims = tuple(wl["dims"])
+    scale = int(np.prod(dims))
+    t_all, sub = oracle_sample(wl, a.warmup + a.steps)
+    t = t_all[a.warmup:]
+    per_iter = statistics.mean(t) * (scale / int(np.prod(sub)))
+    iters = wl["ref_iterations"]
+    nrhs = 12 if wl["rhs"] == "point12" else 1
+    value = per_iter * iters * nrhs
+    line = {
+        "impl": "reference", "metric": wl["metric"], "value": value, "unit": "s", "n_gpus": 0,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(t) * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": wl_config(wl, a.workload, "fp64"),
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"one oracle FGMRES iteration (two-level cycle + D + one Gram-Schmidt step) "
+                                   f"on {sub[0]}x{sub[1]}x{sub[2]}x{sub[3]} = 1/{scale // int(np.prod(sub))} "
+                                   f"of the volume, scaled by volume, x{iters} iterations per RHS "
+                                   f"(documented estimate) x{nrhs} RHS"},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def wl_config(wl, name, precision):
+    d = wl["dims"]
+    return {"workload": f"{d[0]}^3x{d[3]}" if d[0] == d[1] == d[2] else name,
+            "lattice": list(d), "eps": wl["eps"], "c_sw": wl["c_sw"], "m0": wl["m0"],
+            "rhs": wl["rhs"], "levels": wl["n_levels"], "n_vec": list(wl["n_vec"]), "n_mr": wl["n_mr"],
+            "nu_post": wl["nu_post"], "coarse_iters": wl["coarse_iters"], "fgmres_m": wl["fgmres_m"],
+            "tol": wl["tol"], "storage": precision, "parallelism": "replicas",
+            "l2": "inputs larger than L2 (fields of several GB)"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(a, wl):
+    import torch
+    import paper_1202_2462_gb300 as G
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dims = tuple(wl["dims"])
+    prec = a.precision or wl["precision"]
+    t0 = time.perf_counter()
+    u_h = synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"])
+    rhs_h = make_rhs(wl, dims)
+    gen_s = time.perf_counter() - t0
+    nrhs = rhs_h.shape[0]
+    u = torch.from_numpy(u_h).cuda()
+    b = torch.from_numpy(rhs_h).cuda()
+    b_pinned = torch.from_numpy(rhs_h).pin_memory()
+    z_pinned = torch.empty_like(b_pinned).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = G.Solver(u, wl["c_sw"], wl["m0"], **solver_kwargs(wl, prec, nrhs))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    del u
+
+    # warm-up steps, profiled per kernel family to find the dominant one
+    G.mg_set_profiling(s.ctx, 1)
+    infos = []
+    for _ in range(a.warmup):
+        z, info, code = s.solve(b)
+        infos.append((info.iterations, info.relres, code))
+    fam_ms = {f: G.mg_get_profile(s.ctx, i)[1] for f, i in G.PROFILE_FAMILIES.items()}
+    dominant = max(fam_ms, key=fam_ms.get)
+    G.mg_reset_profile(s.ctx)
+    G.mg_set_profiling(s.ctx, G.profile_mask(dominant))
+
+    # timed region: K steps, barrier + synchronize on both sides, CUDA events on the stream
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_id)
+    l0 = G.mg_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    codes = []
+    for _ in range(a.steps):
+        z, info, code = s.solve(b)
+        codes.append((info.iterations, info.relres, code, info.restarts))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = G.mg_launch_count() - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    n_prof, ms_prof = G.mg_get_profile(s.ctx, G.PROFILE_FAMILIES[dominant])
+    G.mg_set_profiling(s.ctx, 0)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+
+    # end to end through the public API with host buffers
+    e2e_steps = max(1, min(a.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bd = b_pinned.to("cuda", non_blocking=True)
+        zd, _, _ = s.solve(bd)
+        z_pinned.copy_(zd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    # Dirac-apply GB/s (storage precision of the smoother, blocked layout)
+    v = dims[0] * dims[1] * dims[2] * dims[3]
+    x = torch.randn((v * 12,), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    pd = G.PRECISIONS[prec] | G.MG_BLOCKED
+    for _ in range(3):
+        G.dirac_apply(s.ctx, x, y, pd, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        G.dirac_apply(s.ctx, x, y, pd, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dirac_s = e0.elapsed_time(e1) / reps / 1e3
+    dirac_gbs = bytes_dirac_site(prec) * v / dirac_s / 1e9
+    s.close()
+
+    hbm, peak_kind = load_peaks()
+    if dominant == "sap":
+        per_launch_units = v // 2 * nrhs_per_launch(nrhs)
+        avg_s = ms_prof / max(n_prof, 1) / 1e3
+        tflops = flops_sap_site(wl["n_mr"]) * (v // 2) / avg_s / 1e12 if n_prof else None
+        roof = {"kernel": "sap_colour_kernel", "bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS if tflops else None, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "hbm_gbs": bytes_sap_site(prec) * (v // 2) / avg_s / 1e9 if n_prof else None,
+                "hbm_frac": (bytes_sap_site(prec) * (v // 2) / avg_s / 1e9) / hbm if n_prof else None,
+                "launches": n_prof, "avg_launch_ms": avg_s * 1e3, "units_per_launch": per_launch_units}
+    else:
+        avg_s = ms_prof / max(n_prof, 1) / 1e3
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None, "launches": n_prof, "avg_launch_ms": avg_s * 1e3}
+
+    iters = [c[0] for c in codes]
+    line = {
+        "metric": wl["metric"], "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": wl_config(wl, a.workload, prec),
+        "iterations_per_step": iters, "restarts_per_step": [c[3] for c in codes],
+        "relres": max(c[1] for c in codes), "status": [c[2] for c in codes], "rhs_per_step": nrhs * world,
+        "setup_s": setup_s, "input_generation_s": gen_s,
+        "dirac_apply": {"storage": prec, "gbs": dirac_gbs, "frac_of_measured_hbm": dirac_gbs / hbm,
+                        "frac_of_8tbs": dirac_gbs / 8000.0, "us": dirac_s * 1e6},
+        "family_ms_warmup": fam_ms, "roofline": roof, "peak_hbm_gbs": hbm, "peak_kind": peak_kind,
+        "clocks": clk, "gpu_launches": launches,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(b_pinned.numel() * 16),
+                "d2h_bytes_per_step": int(z_pinned.numel() * 16)},
+    }
+    if a.fp64_form and rank == 0:
+        line["fp64_form"] = fp64_form(a, wl, u_h, rhs_h)
+    if rank == 0 and world == 1 and not a.no_cpu:
+        t, sub = oracle_sample(wl, 2)
+        per_iter = t[-1] * (v / int(np.prod(sub)))
+        it_rhs = statistics.mean(iters) / nrhs
+        line["cpu_baseline"] = {
+            "value": per_iter * it_rhs * nrhs, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"one oracle FGMRES iteration (two-level cycle + D + one Gram-Schmidt step) on "
+                      f"{sub[0]}x{sub[1]}x{sub[2]}x{sub[3]} ({t[-1]:.2f} s), scaled by volume x{v // int(np.prod(sub))}"
+                      f" and by this run's {it_rhs:.1f} iterations per RHS x{nrhs} RHS"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def nrhs_per_launch(nrhs):
+    return 1
+
+
+def fp64_form(a, wl, u_h, rhs_h):
+    """Time-to-solution of the plain FP64 form (same method, FP64 everywhere) on
+    the first right-hand side; the 12-RHS figure is that time x nrhs."""
+    import torch
+    import paper_1202_2462_gb300 as G
+    u = torch.from_numpy(u_h).cuda()
+    kw = solver_kwargs(wl, "fp64", 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = G.Solver(u, wl["c_sw"], wl["m0"], **kw)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    del u
+    b = torch.from_numpy(rhs_h[:1]).cuda()
+    t0 = time.perf_counter()
+    z, info, code = s.solve(b)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter() - t0
+    s.close()
+    return {"setup_s": setup, "s_per_rhs": t1, "s_all_rhs": t1 * rhs_h.shape[0], "iterations": info.iterations,
+            "relres": info.relres, "status": code, "rhs_measured": 1}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="32^3x64")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--fp64-form", dest="fp64_form", action="store_true", default=True)
+    ap.add_argument("--no-fp64-form", dest="fp64_form", action="store_false")
+    ap.add_argument("--no-cpu", action="store_true")
+    a = ap.parse_args()
+    wl = synth.workload(a.workload)
+    if a.impl == "reference":
+        return run_reference(a, wl)
+    return run_ours(a, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -178,13 +178,18 @@ int mg_coarse_solve(mg_ctx* ctx, int level, const void* in, void* out, int prec)
  * MG_FP32 for a mixed one.  Asynchronous. */
 int mg_precondition(mg_ctx* ctx, const void* v, void* z, int prec);
 
-/* Per-kernel device timing with CUDA events around every launch of the
- * selected kernel families (0 = off).  mg_get_profile returns, for each
- * family (0 dirac, 1 Schwarz colour pass, 2 coarse apply, 3 restrict,
- * 4 prolong, 5 BLAS), the launch count and the summed milliseconds. */
-int mg_set_profiling(mg_ctx* ctx, int on);
+/* Per-kernel device timing with CUDA events recorded on the context's stream
+ * around every launch of the selected kernel families.  mask: 0 = off, 1 = all
+ * families, otherwise bit (f + 1) selects family f (0 dirac, 1 Schwarz colour
+ * pass, 2 coarse apply, 3 restrict, 4 prolong, 5 BLAS).  mg_get_profile
+ * returns a family's timed launch count and summed milliseconds (it
+ * synchronises on the pending events). */
+int mg_set_profiling(mg_ctx* ctx, int mask);
 int mg_get_profile(mg_ctx* ctx, int family, long long* launches, double* ms);
 int mg_reset_profile(mg_ctx* ctx);
+
+/* Number of kernel launches the library has issued in this process. */
+long long mg_launch_count(void);
 
 #ifdef __cplusplus
 }

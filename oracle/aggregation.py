@@ -96,7 +96,7 @@ class Aggregation:
     def restrict(self, r):
         """(P^dagger r)[a, chi*N + k] = sum over aggregate a, chirality chi of conj(v_k) r."""
         ra = self.to_aggregates(r)                                   # (..., S, 2, L)
-        c = np.einsum("ksxl,...sxl->...sxk", np.conj(self.q), ra)    # (..., S, 2, N)
+        c = np.einsum("ksxl,...sxl->...sxk", np.conj(self.q), ra, optimize=True)    # (..., S, 2, N)
         lead = c.shape[:-3]
         return c.reshape(lead + self.clat + (2 * self.nvec,))
 
@@ -104,7 +104,7 @@ class Aggregation:
         """(P e)(x) = sum_k v_k(x)|_chi e[a(x), chi*N + k]."""
         lead = e.shape[:-5]
         ec = e.reshape(lead + (-1, 2, self.nvec))                    # (..., S, 2, N)
-        fa = np.einsum("ksxl,...sxk->...sxl", self.q, ec)
+        fa = np.einsum("ksxl,...sxk->...sxl", self.q, ec, optimize=True)
         return self.from_aggregates(fa)
 
     def dense(self):

@@ -39,19 +39,19 @@ class CoarseOperator:
         fine_tail = len(agg.dof_shape)
         faces = {(mu, s): agg.face_mask(mu, s).reshape(agg.lat + (1,) * fine_tail)
                  for mu in range(4) for s in (1, -1)}
-        for chi in (0, 1):
-            proj = agg.chirality_projector(chi)
-            for k in range(n):
-                u = cols[k] * proj                   # sum over aggregates of P e_(a, chi, k)
-                j = chi * n + k
-                self.self_[..., :, j] += agg.restrict(fine_op.local(u))
-                for mu in range(4):
-                    for s in (1, -1):
-                        h = fine_op.hop(u, mu, s)
-                        f = faces[(mu, s)]
-                        self.self_[..., :, j] += agg.restrict(h * (1.0 - f))
-                        tgt = self.fwd if s > 0 else self.bwd
-                        tgt[mu][..., :, j] += agg.restrict(h * f)
+        # all 2N columns at once: column j = chi*N + k is v_k restricted to chirality chi
+        proj = np.stack([agg.chirality_projector(chi) for chi in (0, 1)])          # (2, *dof)
+        proj = proj.reshape((2, 1, 1, 1, 1, 1) + agg.dof_shape)
+        u = (proj * cols[None]).reshape((n2,) + cols.shape[1:])                    # (2N, lat, dof)
+        to_cols = lambda r: np.moveaxis(r, 0, -1)                                   # (2N, clat, 2N_i) -> (clat, i, j)
+        self.self_ += to_cols(agg.restrict(fine_op.local(u)))
+        for mu in range(4):
+            for s in (1, -1):
+                h = fine_op.hop(u, mu, s)
+                f = faces[(mu, s)]
+                self.self_ += to_cols(agg.restrict(h * (1.0 - f)))
+                tgt = self.fwd if s > 0 else self.bwd
+                tgt[mu] += to_cols(agg.restrict(h * f))
 
     def local(self, x):
         return np.einsum("...ij,...j->...i", self.self_, x)

@@ -130,8 +130,8 @@ class WilsonClover:
     def local(self, psi):
         """The site-diagonal part A(x) psi(x)."""
         sh = psi.shape
-        p = psi.reshape(sh[:-2] + (12,))
-        return np.einsum("...ij,...j->...i", self.a, p).reshape(sh)
+        p = psi.reshape(sh[:-2] + (12, 1))
+        return np.matmul(self.a, p).reshape(sh)
 
     def hop(self, psi, mu, step):
         """One hopping term of D.
@@ -142,14 +142,14 @@ class WilsonClover:
         umu = self.u[..., mu, :, :]
         if step > 0:
             nb = self._bc(shift(psi, mu, 1, 2), mu, 1)
-            c = np.einsum("...ab,...sb->...sa", umu, nb)
+            c = np.matmul(nb, np.swapaxes(umu, -1, -2))            # c[s, a] = sum_b U[a, b] psi[s, b]
             spin = ONE4 - GAMMA[mu]
         else:
             nb = self._bc(shift(psi, mu, -1, 2), mu, -1)
             ub = shift(umu, mu, -1, 2)
-            c = np.einsum("...ba,...sb->...sa", np.conj(ub), nb)
+            c = np.matmul(nb, np.conj(ub))                         # c[s, a] = sum_b conj(U[b, a]) psi[s, b]
             spin = ONE4 + GAMMA[mu]
-        return -0.5 * np.einsum("st,...tb->...sb", spin, c)
+        return -0.5 * np.matmul(spin, c)
 
     def apply(self, psi):
         """D psi."""

@@ -89,6 +89,7 @@ _SIGNATURES = {
     "mg_set_profiling": (_I, [_VP, _I]),
     "mg_get_profile": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     "mg_reset_profile": (_I, [_VP]),
+    "mg_launch_count": (ctypes.c_longlong, []),
 }
 
 _lib = None
@@ -218,6 +219,18 @@ def mg_get_profile(ctx, family):
 
 def mg_reset_profile(ctx):
     return _check(lib().mg_reset_profile(ctx), "mg_reset_profile")
+
+
+def mg_launch_count():
+    return lib().mg_launch_count()
+
+
+def profile_mask(*families):
+    """mg_set_profiling mask selecting the named families."""
+    m = 0
+    for f in families:
+        m |= 1 << (PROFILE_FAMILIES[f] + 1)
+    return m
 
 
 PROFILE_FAMILIES = {"dirac": 0, "sap": 1, "coarse": 2, "restrict": 3, "prolong": 4, "blas": 5}

@@ -85,7 +85,7 @@ static int grid_for(size_t n) {
 
 template <class T2, int K>
 static void md_launch(int ncta, const Ptrs8<T2>& p, const T2* w, size_t n, double2* part, cudaStream_t s) {
-  multidot_partial<T2, K><<<ncta, 256, 0, s>>>(p, w, n, part);
+  multidot_partial<T2, K><<<ncta, 256, 0, s>>>(p, w, n, part); count_launches(1);
 }
 
 template <class T2>
@@ -107,7 +107,7 @@ static int multidot_t(const void* const* v, int k, const void* w, size_t n, doub
       default: md_launch<T2, 8>(ncta, p, (const T2*)w, n, partial, s); break;
     }
     multidot_finalize<<<1, 256, 0, s>>>(partial, ncta, kk, out ? out + j0 : nullptr, mode,
-                                        out2 ? out2 + j0 : nullptr);
+                                        out2 ? out2 + j0 : nullptr); count_launches(1);
   }
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) multiaxpy_kernel(T2* __restrict__ w, Ptrs
 template <class T2, int K>
 static void ma_launch(T2* w, const Ptrs8<T2>& p, const double2* c, double sign, size_t n, cudaStream_t s) {
   const int ncta = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 8));
-  multiaxpy_kernel<T2, K><<<ncta, 256, 0, s>>>(w, p, c, sign, n);
+  multiaxpy_kernel<T2, K><<<ncta, 256, 0, s>>>(w, p, c, sign, n); count_launches(1);
 }
 
 template <class T2>
@@ -207,10 +207,10 @@ int blas_axpby2(int tx, double2 a, const void* x, int ty, double2 b, void* y, si
   if (n == 0) return MG_OK;
   const int ncta = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 8));
   const int z = (b.x == 0.0 && b.y == 0.0) ? 1 : 0;
-  if (tx == P64 && ty == P64) axpby_kernel<double2, double2><<<ncta, 256, 0, s>>>(a.x, a.y, (const double2*)x, b.x, b.y, (double2*)y, n, z);
-  else if (tx == P32 && ty == P32) axpby_kernel<float2, float2><<<ncta, 256, 0, s>>>(a.x, a.y, (const float2*)x, b.x, b.y, (float2*)y, n, z);
-  else if (tx == P32 && ty == P64) axpby_kernel<float2, double2><<<ncta, 256, 0, s>>>(a.x, a.y, (const float2*)x, b.x, b.y, (double2*)y, n, z);
-  else if (tx == P64 && ty == P32) axpby_kernel<double2, float2><<<ncta, 256, 0, s>>>(a.x, a.y, (const double2*)x, b.x, b.y, (float2*)y, n, z);
+  if (tx == P64 && ty == P64) { axpby_kernel<double2, double2><<<ncta, 256, 0, s>>>(a.x, a.y, (const double2*)x, b.x, b.y, (double2*)y, n, z); count_launches(1); }
+  else if (tx == P32 && ty == P32) { axpby_kernel<float2, float2><<<ncta, 256, 0, s>>>(a.x, a.y, (const float2*)x, b.x, b.y, (float2*)y, n, z); count_launches(1); }
+  else if (tx == P32 && ty == P64) { axpby_kernel<float2, double2><<<ncta, 256, 0, s>>>(a.x, a.y, (const float2*)x, b.x, b.y, (double2*)y, n, z); count_launches(1); }
+  else if (tx == P64 && ty == P32) { axpby_kernel<double2, float2><<<ncta, 256, 0, s>>>(a.x, a.y, (const double2*)x, b.x, b.y, (float2*)y, n, z); count_launches(1); }
   else return MG_ERR_ARG;
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
@@ -240,8 +240,8 @@ __global__ void normalize_kernel(const T2* __restrict__ x, T2* __restrict__ out,
 int blas_normalize(int type, const void* x, void* out, const double2* nrm2, double2* store, size_t n,
                    cudaStream_t s) {
   const int ncta = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 8));
-  if (type == P64) normalize_kernel<double2><<<ncta, 256, 0, s>>>((const double2*)x, (double2*)out, nrm2, store, n);
-  else if (type == P32) normalize_kernel<float2><<<ncta, 256, 0, s>>>((const float2*)x, (float2*)out, nrm2, store, n);
+  if (type == P64) { normalize_kernel<double2><<<ncta, 256, 0, s>>>((const double2*)x, (double2*)out, nrm2, store, n); count_launches(1); }
+  else if (type == P32) { normalize_kernel<float2><<<ncta, 256, 0, s>>>((const float2*)x, (float2*)out, nrm2, store, n); count_launches(1); }
   else return MG_ERR_ARG;
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
@@ -314,7 +314,7 @@ __global__ void hessenberg_solve_kernel(const double2* __restrict__ Hin, int ldh
 
 int blas_hessenberg_solve(const double2* H, int ldh, int m, const double2* beta2, double2* y, cudaStream_t s) {
   if (m > 32) return MG_ERR_ARG;
-  hessenberg_solve_kernel<<<1, 32, 0, s>>>(H, ldh, m, beta2, y);
+  hessenberg_solve_kernel<<<1, 32, 0, s>>>(H, ldh, m, beta2, y); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }

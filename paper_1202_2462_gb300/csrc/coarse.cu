@@ -80,10 +80,10 @@ static int transfer0_run(bool restrict_, const Geom& g, const void* in, void* ou
   dim3 grid(g.nblocks, nrhs);
   if (restrict_) {
     const size_t smem = sizeof(R) * 4 * 8 * N;
-    restrict0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TS*)in, (TC*)out, (const TV*)Pv, N);
+    restrict0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TS*)in, (TC*)out, (const TV*)Pv, N); count_launches(1);
   } else {
     const size_t smem = sizeof(Cplx<R>) * 2 * N;
-    prolong0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TC*)in, (TS*)out, (const TV*)Pv, N);
+    prolong0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TC*)in, (TS*)out, (const TV*)Pv, N); count_launches(1);
   }
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) block_gs0_kernel(double2* __restrict__ V,
 
 int launch_block_gs0(const Geom& g, void* V64, int N, cudaStream_t s) {
   dim3 grid(g.nblocks, 2);
-  block_gs0_kernel<<<grid, 256, 0, s>>>((double2*)V64, N, (long long)g.V * 12);
+  block_gs0_kernel<<<grid, 256, 0, s>>>((double2*)V64, N, (long long)g.V * 12); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }
@@ -162,10 +162,10 @@ int launch_store_p0(int prec, const Geom& g, const void* V64, void* Pv, int N, c
   dim3 grid(g.nblocks, N);
   const long long fs = (long long)g.V * 12;
   switch (prec) {
-    case P64: store_p0_kernel<double2><<<grid, 256, 0, s>>>((const double2*)V64, (double2*)Pv, N, fs); break;
-    case P32: store_p0_kernel<float2><<<grid, 256, 0, s>>>((const double2*)V64, (float2*)Pv, N, fs); break;
-    case P16: store_p0_kernel<__half2><<<grid, 256, 0, s>>>((const double2*)V64, (__half2*)Pv, N, fs); break;
-    case PBF: store_p0_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>((const double2*)V64, (__nv_bfloat162*)Pv, N, fs); break;
+    case P64: store_p0_kernel<double2><<<grid, 256, 0, s>>>((const double2*)V64, (double2*)Pv, N, fs); count_launches(1); break;
+    case P32: store_p0_kernel<float2><<<grid, 256, 0, s>>>((const double2*)V64, (float2*)Pv, N, fs); count_launches(1); break;
+    case P16: store_p0_kernel<__half2><<<grid, 256, 0, s>>>((const double2*)V64, (__half2*)Pv, N, fs); count_launches(1); break;
+    case PBF: store_p0_kernel<__nv_bfloat162><<<grid, 256, 0, s>>>((const double2*)V64, (__nv_bfloat162*)Pv, N, fs); count_launches(1); break;
     default: return MG_ERR_ARG;
   }
   SAPMG_CUDA_TRY(cudaGetLastError());
@@ -264,7 +264,7 @@ int launch_assemble0(const Geom& g, const void* V64, const void* U64, const void
   dim3 grid(g.nblocks, 2 * N);
   const size_t smem = sizeof(double) * 4 * 8 * N;
   assemble0_kernel<<<grid, 256, smem, s>>>((const double2*)V64, (const double2*)U64, (const double2*)A64,
-                                           (double2*)M64, g, N);
+                                           (double2*)M64, g, N); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }
@@ -312,10 +312,10 @@ int launch_coarse_apply(int prec, const CGeom& c, const void* M, const void* x, 
   const long long n = (long long)c.nsites * c.n2;
   dim3 grid((unsigned)((n + 255) / 256), nrhs);
   switch (prec) {
-    case P64: coarse_apply_kernel<double, double2, double2><<<grid, 256, 0, s>>>((const double2*)M, (const double2*)x, (double2*)out, c); break;
-    case P32: coarse_apply_kernel<float, float2, float2><<<grid, 256, 0, s>>>((const float2*)M, (const float2*)x, (float2*)out, c); break;
-    case P16: coarse_apply_kernel<float, __half2, float2><<<grid, 256, 0, s>>>((const __half2*)M, (const float2*)x, (float2*)out, c); break;
-    case PBF: coarse_apply_kernel<float, __nv_bfloat162, float2><<<grid, 256, 0, s>>>((const __nv_bfloat162*)M, (const float2*)x, (float2*)out, c); break;
+    case P64: coarse_apply_kernel<double, double2, double2><<<grid, 256, 0, s>>>((const double2*)M, (const double2*)x, (double2*)out, c); count_launches(1); break;
+    case P32: coarse_apply_kernel<float, float2, float2><<<grid, 256, 0, s>>>((const float2*)M, (const float2*)x, (float2*)out, c); count_launches(1); break;
+    case P16: coarse_apply_kernel<float, __half2, float2><<<grid, 256, 0, s>>>((const __half2*)M, (const float2*)x, (float2*)out, c); count_launches(1); break;
+    case PBF: coarse_apply_kernel<float, __nv_bfloat162, float2><<<grid, 256, 0, s>>>((const __nv_bfloat162*)M, (const float2*)x, (float2*)out, c); count_launches(1); break;
     default: return MG_ERR_ARG;
   }
   SAPMG_CUDA_TRY(cudaGetLastError());
@@ -338,10 +338,10 @@ int launch_coarse_export(int prec, const CGeom& c, const void* M, double* out, c
   const long long n = (long long)c.nsites * 9 * c.n2 * c.n2;
   const unsigned nb = (unsigned)((n + 255) / 256);
   switch (prec) {
-    case P64: coarse_export_kernel<double2><<<nb, 256, 0, s>>>((const double2*)M, (double2*)out, c); break;
-    case P32: coarse_export_kernel<float2><<<nb, 256, 0, s>>>((const float2*)M, (double2*)out, c); break;
-    case P16: coarse_export_kernel<__half2><<<nb, 256, 0, s>>>((const __half2*)M, (double2*)out, c); break;
-    case PBF: coarse_export_kernel<__nv_bfloat162><<<nb, 256, 0, s>>>((const __nv_bfloat162*)M, (double2*)out, c); break;
+    case P64: coarse_export_kernel<double2><<<nb, 256, 0, s>>>((const double2*)M, (double2*)out, c); count_launches(1); break;
+    case P32: coarse_export_kernel<float2><<<nb, 256, 0, s>>>((const float2*)M, (double2*)out, c); count_launches(1); break;
+    case P16: coarse_export_kernel<__half2><<<nb, 256, 0, s>>>((const __half2*)M, (double2*)out, c); count_launches(1); break;
+    case PBF: coarse_export_kernel<__nv_bfloat162><<<nb, 256, 0, s>>>((const __nv_bfloat162*)M, (double2*)out, c); count_launches(1); break;
     default: return MG_ERR_ARG;
   }
   SAPMG_CUDA_TRY(cudaGetLastError());

@@ -164,4 +164,6 @@ template <class R> __device__ __forceinline__ R warp_sum(R v) {
 
 namespace sapmg {
 void set_last_error(const char* msg, const char* file, int line);
+// Count of kernel launches issued by the library (diagnostics).
+void count_launches(int n);
 }

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) dirac_kernel(TS* __restrict__ out, const 
 template <class R, class TS, class TG>
 static void run(const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs, cudaStream_t s) {
   dim3 grid(g.nblocks, nrhs);
-  dirac_kernel<R, TS, TG><<<grid, 256, 0, s>>>((TS*)out, (const TS*)in, (const TG*)U, (const TG*)A, g);
+  dirac_kernel<R, TS, TG><<<grid, 256, 0, s>>>((TS*)out, (const TS*)in, (const TG*)U, (const TG*)A, g); count_launches(1);
 }
 
 int launch_dirac(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,

@@ -56,10 +56,10 @@ int launch_pack_gauge(int prec, const Geom& g, const double* Uc, void* Ub, int a
   const unsigned nb = (unsigned)((n + th - 1) / th);
   const double2* u = (const double2*)Uc;
   switch (prec) {
-    case P64: pack_gauge_kernel<double2><<<nb, th, 0, s>>>(u, (double2*)Ub, g, antiperiodic_t); break;
-    case P32: pack_gauge_kernel<float2><<<nb, th, 0, s>>>(u, (float2*)Ub, g, antiperiodic_t); break;
-    case P16: pack_gauge_kernel<__half2><<<nb, th, 0, s>>>(u, (__half2*)Ub, g, antiperiodic_t); break;
-    case PBF: pack_gauge_kernel<__nv_bfloat162><<<nb, th, 0, s>>>(u, (__nv_bfloat162*)Ub, g, antiperiodic_t); break;
+    case P64: pack_gauge_kernel<double2><<<nb, th, 0, s>>>(u, (double2*)Ub, g, antiperiodic_t); count_launches(1); break;
+    case P32: pack_gauge_kernel<float2><<<nb, th, 0, s>>>(u, (float2*)Ub, g, antiperiodic_t); count_launches(1); break;
+    case P16: pack_gauge_kernel<__half2><<<nb, th, 0, s>>>(u, (__half2*)Ub, g, antiperiodic_t); count_launches(1); break;
+    case PBF: pack_gauge_kernel<__nv_bfloat162><<<nb, th, 0, s>>>(u, (__nv_bfloat162*)Ub, g, antiperiodic_t); count_launches(1); break;
     default: return MG_ERR_ARG;
   }
   SAPMG_CUDA_TRY(cudaGetLastError());
@@ -167,7 +167,7 @@ __global__ void clover_build_kernel(const double2* __restrict__ Uc, double2* __r
 int launch_clover_build(const Geom& g, const double* Uc, void* Ab64, double m0, double c_sw, cudaStream_t s) {
   const int th = 128;
   clover_build_kernel<<<(unsigned)((g.V + th - 1) / th), th, 0, s>>>((const double2*)Uc, (double2*)Ab64, g,
-                                                                     4.0 + m0, c_sw);
+                                                                     4.0 + m0, c_sw); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }
@@ -199,7 +199,7 @@ __global__ void clover_export_kernel(const double2* __restrict__ Ab, double2* __
 
 int launch_clover_export(const Geom& g, const void* Ab64, double* out, cudaStream_t s) {
   const int th = 128;
-  clover_export_kernel<<<(unsigned)((g.V + th - 1) / th), th, 0, s>>>((const double2*)Ab64, (double2*)out, g);
+  clover_export_kernel<<<(unsigned)((g.V + th - 1) / th), th, 0, s>>>((const double2*)Ab64, (double2*)out, g); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }
@@ -216,10 +216,10 @@ static int convert_from(const TI* in, int to, void* out, size_t n, cudaStream_t 
   const int th = 256;
   const unsigned nb = (unsigned)std::min<size_t>((n + th - 1) / th, 152 * 64);
   switch (to) {
-    case P64: convert_kernel<TI, double2><<<nb, th, 0, s>>>(in, (double2*)out, n); break;
-    case P32: convert_kernel<TI, float2><<<nb, th, 0, s>>>(in, (float2*)out, n); break;
-    case P16: convert_kernel<TI, __half2><<<nb, th, 0, s>>>(in, (__half2*)out, n); break;
-    case PBF: convert_kernel<TI, __nv_bfloat162><<<nb, th, 0, s>>>(in, (__nv_bfloat162*)out, n); break;
+    case P64: convert_kernel<TI, double2><<<nb, th, 0, s>>>(in, (double2*)out, n); count_launches(1); break;
+    case P32: convert_kernel<TI, float2><<<nb, th, 0, s>>>(in, (float2*)out, n); count_launches(1); break;
+    case P16: convert_kernel<TI, __half2><<<nb, th, 0, s>>>(in, (__half2*)out, n); count_launches(1); break;
+    case PBF: convert_kernel<TI, __nv_bfloat162><<<nb, th, 0, s>>>(in, (__nv_bfloat162*)out, n); count_launches(1); break;
     default: return MG_ERR_ARG;
   }
   return MG_OK;
@@ -271,8 +271,8 @@ __global__ void unpack_spinor_kernel(const TI* __restrict__ in, TO* __restrict__
 template <class TI, class TO>
 static void layout_launch(bool pack, unsigned nb, int th, const void* in, void* out, const Geom& g, int nrhs,
                           cudaStream_t s) {
-  if (pack) pack_spinor_kernel<TI, TO><<<nb, th, 0, s>>>((const TI*)in, (TO*)out, g, nrhs);
-  else unpack_spinor_kernel<TI, TO><<<nb, th, 0, s>>>((const TI*)in, (TO*)out, g, nrhs);
+  if (pack) { pack_spinor_kernel<TI, TO><<<nb, th, 0, s>>>((const TI*)in, (TO*)out, g, nrhs); count_launches(1); }
+  else { unpack_spinor_kernel<TI, TO><<<nb, th, 0, s>>>((const TI*)in, (TO*)out, g, nrhs); count_launches(1); }
 }
 
 static int layout_dispatch(bool pack, int pin, const void* in, int pout, void* out, const Geom& g, int nrhs,
@@ -338,7 +338,7 @@ int launch_draw_vectors(const Geom& g, void* out64, int nvec, unsigned long long
   const uint64_t key = host_splitmix64(host_splitmix64(seed) + stream);
   const long long n = g.V * nvec;
   const int th = 128;
-  draw_vectors_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>((double2*)out64, g, nvec, key);
+  draw_vectors_kernel<<<(unsigned)((n + th - 1) / th), th, 0, s>>>((double2*)out64, g, nvec, key); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }

@@ -127,7 +127,7 @@ static int run(const Geom& g, void* z, const void* b, const void* U, const void*
   }
   dim3 grid(g.nblocks / 2, nrhs);
   sap_colour_kernel<R, TS, TG><<<grid, 256, smem, s>>>((TS*)z, (const TS*)b, (const TG*)U, (const TG*)A, g, colour,
-                                                       n_mr);
+                                                       n_mr); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <atomic>
 
 #include "internal.h"
 #include "blas.h"
@@ -16,6 +17,8 @@
 namespace sapmg {
 
 static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void set_last_error(const char* msg, const char* file, int line) {
   g_err = std::string(msg) + " (" + file + ":" + std::to_string(line) + ")";
 }
@@ -34,6 +37,7 @@ enum { FAM_DIRAC = 0, FAM_SAP = 1, FAM_COARSE = 2, FAM_RESTRICT = 3, FAM_PROLONG
 
 struct Prof {
   bool on = false;
+  unsigned mask = 0;   // families timed (bit f = family f)
   struct Rec { int fam; cudaEvent_t a, b; };
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> pending;
@@ -68,11 +72,12 @@ struct ProfScope {
   int fam;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
-  ProfScope(Prof& p_, int f, cudaStream_t s_) : p(p_), fam(f), s(s_) {
-    if (p.on) { a = p.get(); cudaEventRecord(a, s); }
+  bool act;
+  ProfScope(Prof& p_, int f, cudaStream_t s_) : p(p_), fam(f), s(s_), act(p_.on && ((p_.mask >> f) & 1u)) {
+    if (act) { a = p.get(); cudaEventRecord(a, s); }
   }
   ~ProfScope() {
-    if (p.on) {
+    if (act) {
       cudaEvent_t b = p.get();
       cudaEventRecord(b, s);
       p.pending.push_back({fam, a, b});
@@ -371,7 +376,7 @@ static int check_finite(mg_ctx* c, const double* x, size_t n_doubles) {
   int* flag = (int*)c->alloc(sizeof(int));
   if (!flag) return fail(MG_ERR_OOM, "allocation failed");
   SAPMG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), c->s));
-  nonfinite_kernel<<<1024, 256, 0, c->s>>>(x, n_doubles, flag);
+  nonfinite_kernel<<<1024, 256, 0, c->s>>>(x, n_doubles, flag); count_launches(1);
   int h = 0;
   SAPMG_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
@@ -757,11 +762,14 @@ int mg_precondition(mg_ctx* c, const void* v, void* z, int prec) {
   return MG_OK;
 }
 
-int mg_set_profiling(mg_ctx* c, int on) {
+int mg_set_profiling(mg_ctx* c, int mask) {
   if (!c) return fail(MG_ERR_ARG, "bad argument");
-  c->prof.on = on != 0;
+  c->prof.on = mask != 0;
+  c->prof.mask = (mask == 1) ? 0xffffffffu : (unsigned)mask >> 1;
   return MG_OK;
 }
+
+long long mg_launch_count(void) { return g_launches.load(); }
 
 int mg_get_profile(mg_ctx* c, int family, long long* launches, double* ms) {
   if (!c || family < 0 || family >= FAM_N) return fail(MG_ERR_ARG, "bad argument");

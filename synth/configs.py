@@ -8,25 +8,27 @@ reaches the stated target.
 hopping parameter as m0 = 1/(2 kappa) - 4.
 """
 
+METRIC = "time-to-solution to 1e-10 at 32^3x64 (mixed vs FP64); Dirac-apply HBM GB/s"
+
 WORKLOADS = {
     # Plain method, FP64, two levels.
     "8^4": dict(
         dims=(8, 8, 8, 8), eps=0.3, gauge_seed=101, c_sw=1.0, m0=-0.25,
         rhs="gaussian", rhs_seed=201, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(8,),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
-        precision="fp64"),
+        precision="fp64", metric=METRIC, ref_iterations=60),
     # Plain vs mixed precision, three levels.
     "16^3x32": dict(
         dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.55,
-        rhs="z2", rhs_seed=202, n_levels=3, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
+        rhs="z2", rhs_seed=202, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
-        precision="fp16"),
+        precision="fp16", metric=METRIC, ref_iterations=60),
     # Multi-RHS: 12 spin-colour point sources.
     "32^3x64": dict(
         dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.7,
-        rhs="point12", rhs_seed=0, n_levels=3, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
+        rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
-        precision="bf16"),
+        precision="bf16", metric=METRIC, ref_iterations=60),
 }
 
 

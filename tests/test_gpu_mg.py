@@ -1,0 +1,222 @@
+"""GPU parity of the aggregation and coarse-grid components (Sec. 3), the
+multilevel cycle and the outer solve (Sec. 4) against the FP64 oracle, through
+the C-ABI entry points."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.dirac import WilsonClover
+from oracle.aggregation import Aggregation
+from oracle.coarse import CoarseOperator
+from oracle.krylov import gmres_fixed
+from oracle.mg import Multigrid
+from tests.gpu_util import torch_cuda, dev, host, rel, round_storage
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (8, 8, 8, 8)
+M0, CSW = -0.2, 1.0
+
+
+@pytest.fixture(scope="module")
+def field():
+    u = synth.random_gauge_field(DIMS, 0.4, 31)
+    return u, WilsonClover(u, M0, CSW)
+
+
+def _solver(torch, u, **kw):
+    import paper_1202_2462_gb300 as G
+    return G.Solver(dev(torch, u), CSW, M0, **kw)
+
+
+def _vectors(torch, s, n):
+    import paper_1202_2462_gb300 as G
+    v = torch.zeros((n,) + s.lat + (4, 3), dtype=torch.complex128, device="cuda")
+    G.mg_get_vectors(s.ctx, 0, v)
+    return host(v)
+
+
+def test_clover_export_parity(field):
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u, op = field
+    s = _solver(torch, u)
+    a = torch.zeros(DIMS[::-1] + (2, 6, 6), dtype=torch.complex128, device="cuda")
+    G.mg_clover_export(s.ctx, a)
+    s.close()
+    a = host(a)
+    assert np.max(np.abs(a[..., 0, :, :] - op.a[..., :6, :6])) < 1e-14
+    assert np.max(np.abs(a[..., 1, :, :] - op.a[..., 6:, 6:])) < 1e-14
+
+
+def test_drawn_test_vectors_match_counter_generator():
+    """With no set-up sweeps P is the local QR of the drawn vectors: the device
+    draw (SplitMix64 counters) must equal the host draw bit for bit, so P agrees
+    with the oracle's local orthonormalisation to rounding."""
+    torch = torch_cuda()
+    u = synth.random_gauge_field(DIMS, 0.4, 32)
+    s = _solver(torch, u, n_levels=2, n_vec=(5,), setup_iters=0, seed=12345)
+    v = _vectors(torch, s, 5)
+    s.close()
+    ref = Aggregation(DIMS, (4, 4, 4, 4), (4, 3)).build(synth.test_vector_draw(DIMS, 5, 12345)).columns()
+    assert np.max(np.abs(v - ref)) < 1e-14
+
+
+def test_bootstrap_setup_parity(field):
+    """Bootstrap part 1 with identical initial vectors (FP64): P agrees."""
+    torch = torch_cuda()
+    u, op = field
+    iv = synth.test_vector_draw(DIMS, 6, 33)
+    s = _solver(torch, u, n_levels=2, n_vec=(6,), setup_iters=2, init_vectors=dev(torch, iv))
+    v = _vectors(torch, s, 6)
+    s.close()
+    mg = Multigrid(op, dict(n_levels=2, n_vec=(6,), setup_iters=2, sap_block=((4, 4, 4, 4),),
+                            agg=((4, 4, 4, 4),)), iv)
+    assert np.max(np.abs(v - mg.levels[0].agg.columns())) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def fp64_ctx(field):
+    torch = torch_cuda()
+    u, op = field
+    iv = synth.test_vector_draw(DIMS, 6, 34)
+    s = _solver(torch, u, n_levels=2, n_vec=(6,), setup_iters=0, init_vectors=dev(torch, iv))
+    agg = Aggregation(DIMS, (4, 4, 4, 4), (4, 3)).build(iv)
+    yield s, agg, CoarseOperator(op, agg)
+    s.close()
+
+
+def test_coarse_operator_parity(fp64_ctx):
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    s, agg, c = fp64_ctx
+    m = torch.zeros((16, 9, 12, 12), dtype=torch.complex128, device="cuda")
+    G.mg_get_coarse_op(s.ctx, 1, m)
+    m = host(m)
+    scale = np.max(np.abs(c.self_))
+    assert np.max(np.abs(m[:, 0] - c.self_.reshape(16, 12, 12))) < 1e-14 * scale
+    for mu in range(4):
+        assert np.max(np.abs(m[:, 1 + 2 * mu] - c.fwd[mu].reshape(16, 12, 12))) < 1e-14 * scale
+        assert np.max(np.abs(m[:, 2 + 2 * mu] - c.bwd[mu].reshape(16, 12, 12))) < 1e-14 * scale
+
+
+def test_restrict_prolong_apply_parity(fp64_ctx):
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    s, agg, c = fp64_ctx
+    r = synth.random_spinor(DIMS, 35)
+    rc = torch.zeros((16, 12), dtype=torch.complex128, device="cuda")
+    G.mg_restrict(s.ctx, 0, dev(torch, r), rc, G.MG_FP64)
+    assert rel(host(rc), agg.restrict(r).reshape(16, 12)) < 1e-14
+    ec = synth.random_spinor((2, 2, 2, 2), 36).reshape(16, 12)
+    f = torch.zeros(DIMS[::-1] + (4, 3), dtype=torch.complex128, device="cuda")
+    G.mg_prolong(s.ctx, 0, dev(torch, ec), f, G.MG_FP64)
+    assert rel(host(f), agg.prolong(ec.reshape(2, 2, 2, 2, 12))) < 1e-14
+    out = torch.zeros_like(rc)
+    G.mg_coarse_apply(s.ctx, 1, dev(torch, ec), out, G.MG_FP64)
+    assert rel(host(out), c.apply(ec.reshape(2, 2, 2, 2, 12)).reshape(16, 12)) < 1e-14
+
+
+def test_coarse_gmres_parity(fp64_ctx):
+    """Fixed-step GMRES (12 steps) from zero: the Krylov minimiser is unique."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    s, agg, c = fp64_ctx
+    bc = synth.random_spinor((2, 2, 2, 2), 37).reshape(16, 12)
+    out = torch.zeros((16, 12), dtype=torch.complex128, device="cuda")
+    G.mg_coarse_solve(s.ctx, 1, dev(torch, bc), out, G.MG_FP64)
+    ref = gmres_fixed(c.apply, bc.reshape(2, 2, 2, 2, 12), 12).reshape(16, 12)
+    assert rel(host(out), ref) < 1e-11
+
+
+def test_cycle_parity(field, fp64_ctx):
+    """One multilevel cycle z = M v with the same P (FP64)."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u, op = field
+    s, agg, c = fp64_ctx
+    iv = synth.test_vector_draw(DIMS, 6, 34)
+    mg = Multigrid(op, dict(n_levels=2, n_vec=(6,), setup_iters=0, sap_block=((4, 4, 4, 4),),
+                            agg=((4, 4, 4, 4),)), iv)
+    v = synth.random_spinor(DIMS, 38)
+    z = torch.zeros(DIMS[::-1] + (4, 3), dtype=torch.complex128, device="cuda")
+    G.mg_precondition(s.ctx, dev(torch, v), z, G.MG_FP64)
+    assert rel(host(z), mg.cycle(0, v)) < 1e-11
+
+
+def test_mixed_transfer_parity():
+    """FP16-stored P with FP32 arithmetic against the oracle with the same rounded P."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u = synth.random_gauge_field(DIMS, 0.4, 39)
+    iv = synth.test_vector_draw(DIMS, 4, 40)
+    s = _solver(torch, u, n_levels=2, n_vec=(4,), setup_iters=0, precision="fp16", init_vectors=dev(torch, iv))
+    agg = Aggregation(DIMS, (4, 4, 4, 4), (4, 3)).build(iv)
+    agg.q = round_storage(agg.q, "fp16")
+    r = synth.random_spinor(DIMS, 41).astype(np.complex64)
+    rc = torch.zeros((16, 8), dtype=torch.complex64, device="cuda")
+    G.mg_restrict(s.ctx, 0, dev(torch, r), rc, G.MG_FP16)
+    s.close()
+    assert rel(host(rc), agg.restrict(r.astype(np.complex128)).reshape(16, 8)) < 2e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_solve_reaches_tolerance(field, prec):
+    """Outer solve: the oracle's own D confirms ||b - D z|| <= 1e-10 ||b||."""
+    torch = torch_cuda()
+    u, op = field
+    b = synth.random_spinor(DIMS, 42, nvec=2)
+    s = _solver(torch, u, n_levels=2, n_vec=(8,), precision=prec, nrhs_max=2, seed=3)
+    z, info, code = s.solve(dev(torch, b))
+    s.close()
+    assert code == 0
+    z = host(z)
+    for k in range(2):
+        assert np.linalg.norm(b[k] - op.apply(z[k])) <= 1e-10 * np.linalg.norm(b[k])
+    assert info.relres <= 1e-10
+
+
+def test_fp64_and_mixed_solutions_agree(field):
+    torch = torch_cuda()
+    u, op = field
+    b = synth.z2_spinor(DIMS, 43)
+    s1 = _solver(torch, u, n_levels=2, n_vec=(8,), precision="fp64", seed=4)
+    z1 = host(s1.solve(dev(torch, b))[0])
+    s1.close()
+    s2 = _solver(torch, u, n_levels=2, n_vec=(8,), precision="bf16", seed=4)
+    z2 = host(s2.solve(dev(torch, b))[0])
+    s2.close()
+    assert rel(z2, z1) < 1e-7
+
+
+def test_solve_zero_rhs(field):
+    torch = torch_cuda()
+    u, op = field
+    s = _solver(torch, u, n_levels=2, n_vec=(4,))
+    z, info, code = s.solve(torch.zeros(DIMS[::-1] + (4, 3), dtype=torch.complex128, device="cuda"))
+    s.close()
+    assert code == 0 and np.all(host(z) == 0) and info.relres == 0
+
+
+def test_iteration_cap_reports_not_converged(field):
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u, op = field
+    b = synth.random_spinor(DIMS, 44)
+    s = _solver(torch, u, n_levels=1, maxiter=3, fgmres_m=3)
+    z, info, code = s.solve(dev(torch, b))
+    s.close()
+    assert code == G.MG_NOT_CONVERGED
+    assert 1e-10 < info.relres < 1.0
+    assert np.linalg.norm(b - op.apply(host(z))) < np.linalg.norm(b)
+
+
+def test_nonfinite_gauge_field_rejected():
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u = synth.random_gauge_field(DIMS, 0.4, 45)
+    u[1, 2, 3, 4, 2, 1, 1] = np.nan
+    with pytest.raises(G.MgError) as e:
+        _solver(torch, u)
+    assert e.value.code == G.MG_ERR_NONFINITE
