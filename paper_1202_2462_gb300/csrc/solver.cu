@@ -111,8 +111,10 @@ struct mg_ctx {
   mg_params p;
   Geom g;
   cudaStream_t s = nullptr;
-  int prec = P64;    // MG_FP64 or the mixed storage precision
+  int prec = P64;    // MG_FP64 or the mixed storage precision of links and clover
   int vt = P64;      // vector type of the cycle (P64 plain, P32 mixed)
+  int pv_prec = P64; // storage of the interpolation P (FP16 for both half modes)
+  int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
   double m0 = 0, csw = 0;
   std::vector<void*> allocs;
   void *U64 = nullptr, *A64 = nullptr;     // blocked FP64 links (boundary sign folded in) and clover
@@ -221,12 +223,12 @@ static int cycle(mg_ctx* c, const void* v, void* z) {
   }
   {
     ProfScope ps(c->prof, FAM_RESTRICT, c->s);
-    TRY(launch_transfer0(true, c->prec, c->g, v, c->c1.b, c->Pv, c->N0, 1, c->s));
+    TRY(launch_transfer0(true, c->pv_prec, c->g, v, c->c1.b, c->Pv, c->N0, 1, c->s));
   }
   TRY(coarse_solve(c, 1));
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
-    TRY(launch_transfer0(false, c->prec, c->g, c->c1.x, z, c->Pv, c->N0, 1, c->s));
+    TRY(launch_transfer0(false, c->pv_prec, c->g, c->c1.x, z, c->Pv, c->N0, 1, c->s));
   }
   return smoother_sweeps(c, v, z, c->p.nu_post, 1);
 }
@@ -427,9 +429,9 @@ static int setup_level0(mg_ctx* c) {
     TRY(orthonormalise(c, c->V64, N));
   }
   TRY(launch_block_gs0(c->g, c->V64, N, c->s));
-  c->Pv = c->alloc((size_t)N * n * complex_bytes(c->prec));
+  c->Pv = c->alloc((size_t)N * n * complex_bytes(c->pv_prec));
   if (!c->Pv) return fail(MG_ERR_OOM, "interpolation");
-  TRY(launch_store_p0(c->prec, c->g, c->V64, c->Pv, N, c->s));
+  TRY(launch_store_p0(c->pv_prec, c->g, c->V64, c->Pv, N, c->s));
   // Galerkin coarse operator
   CoarseLevel& L = c->c1;
   for (int mu = 0; mu < 4; ++mu) L.cg.L[mu] = c->g.nb[mu];
@@ -439,13 +441,13 @@ static int setup_level0(mg_ctx* c) {
   L.M64 = c->alloc(msz * 16);
   if (!L.M64) return fail(MG_ERR_OOM, "coarse operator");
   TRY(launch_assemble0(c->g, c->V64, c->U64, c->A64, L.M64, N, c->s));
-  L.store = c->prec;
-  if (c->prec == P64) {
+  L.store = c->dc_prec;
+  if (c->dc_prec == P64) {
     L.M = L.M64;
   } else {
-    L.M = c->alloc(msz * complex_bytes(c->prec));
+    L.M = c->alloc(msz * complex_bytes(c->dc_prec));
     if (!L.M) return fail(MG_ERR_OOM, "coarse operator");
-    TRY(launch_convert(P64, L.M64, c->prec, L.M, msz, c->s));
+    TRY(launch_convert(P64, L.M64, c->dc_prec, L.M, msz, c->s));
   }
   return MG_OK;
 }
@@ -590,6 +592,8 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   c->s = (cudaStream_t)p->stream;
   c->prec = p->precision;
   c->vt = p->precision == MG_FP64 ? P64 : P32;
+  c->pv_prec = p->precision == MG_BF16 ? P16 : p->precision;
+  c->dc_prec = p->precision == MG_FP64 ? P64 : P32;
   c->m0 = m0;
   c->csw = c_sw;
   const int rc = do_setup(c, U);
@@ -704,7 +708,7 @@ int mg_restrict(mg_ctx* c, int level, const void* in, void* out, int prec) {
   const void* src;
   TRY(stage_in(c, in, prec, blocked, 1, &src));
   ProfScope ps(c->prof, FAM_RESTRICT, c->s);
-  return launch_transfer0(true, c->prec, c->g, src, out, c->Pv, c->N0, 1, c->s);
+  return launch_transfer0(true, c->pv_prec, c->g, src, out, c->Pv, c->N0, 1, c->s);
 }
 
 int mg_prolong(mg_ctx* c, int level, const void* in, void* out, int prec) {
@@ -716,7 +720,7 @@ int mg_prolong(mg_ctx* c, int level, const void* in, void* out, int prec) {
   void* dst = blocked ? out : c->io_b;
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
-    TRY(launch_transfer0(false, c->prec, c->g, in, dst, c->Pv, c->N0, 1, c->s));
+    TRY(launch_transfer0(false, c->pv_prec, c->g, in, dst, c->Pv, c->N0, 1, c->s));
   }
   if (!blocked) {
     const int t = prec == P64 ? P64 : P32;

@@ -2,7 +2,11 @@
 parameters).  The paper's ensembles (Tables 1 and 2) are unavailable; these
 seeded fields stand in for them at c_sw = 1.0 (the value of Table 2), with the
 bare mass m0 chosen near the point where the smallest singular value of D
-reaches the stated target.
+reaches the stated target (measured by inverse iteration with this library,
+``python -m paper_1202_2462_gb300.tune``): 8^4 at m0 = -0.19 has
+sigma_min(D) = 1.0e-2; on the 32^3 x 64 field sigma_min(D) falls from 0.11
+(m0 = -0.6) to 0.064 (m0 = -0.8) and rises again beyond (0.16 at -0.9), so
+-0.8 is the closest to critical the scan reached.
 
 ``m0`` is the bare mass in D = 4 + m0 - (hopping)/2 + clover; it maps to the
 hopping parameter as m0 = 1/(2 kappa) - 4.
@@ -13,7 +17,7 @@ METRIC = "time-to-solution to 1e-10 at 32^3x64 (mixed vs FP64); Dirac-apply HBM 
 WORKLOADS = {
     # Plain method, FP64, two levels.
     "8^4": dict(
-        dims=(8, 8, 8, 8), eps=0.3, gauge_seed=101, c_sw=1.0, m0=-0.25,
+        dims=(8, 8, 8, 8), eps=0.3, gauge_seed=101, c_sw=1.0, m0=-0.19,
         rhs="gaussian", rhs_seed=201, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(8,),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
         precision="fp64", metric=METRIC, ref_iterations=60),
@@ -25,9 +29,9 @@ WORKLOADS = {
         precision="fp16", metric=METRIC, ref_iterations=60),
     # Multi-RHS: 12 spin-colour point sources.
     "32^3x64": dict(
-        dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.7,
+        dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.8,
         rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
-        n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
+        n_mr=4, nu_post=2, setup_iters=8, coarse_iters=24, fgmres_m=20, tol=1e-10,
         precision="bf16", metric=METRIC, ref_iterations=60),
 }
 
