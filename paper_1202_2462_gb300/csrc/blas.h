@@ -1,25 +1,40 @@
-// Vector kernels of the Krylov solvers (internal).
+// Vector kernels of the Krylov solvers, batched over right-hand sides (internal).
 #pragma once
 #include "internal.h"
 
 namespace sapmg {
 
-// Upper bound on the CTAs of a reduction; partial buffers hold kMaxReduceCta * 8 double2.
-constexpr int kMaxReduceCta = 1024;
+// Upper bound on the CTAs of one reduction over all right-hand sides; the
+// partial buffer holds kMaxReduceCta * 8 double2.
+constexpr int kMaxReduceCta = 4096;
 
-// out[j] = <v_j, w> = sum conj(v_j) w for j < k (out2[j] too if non-null); mode 1 adds into out.
-int blas_multidot(int type, const void* const* v, int k, const void* w, size_t n, double2* out, int mode,
-                  double2* out2, double2* partial, cudaStream_t s);
-// w += sign * sum_j coeff[j] v_j with device coefficients.
-int blas_multiaxpy(int type, void* w, const void* const* v, int k, const double2* coeff, double sign, size_t n,
-                   cudaStream_t s);
-// y = a x + b y (b = 0: y is not read).
-int blas_axpby(int type, double2 a, const void* x, double2 b, void* y, size_t n, cudaStream_t s);
-// The same with element types tx of x and ty of y (P64 / P32 each).
-int blas_axpby2(int tx, double2 a, const void* x, int ty, double2 b, void* y, size_t n, cudaStream_t s);
-// out = x / sqrt(*nrm2); *store = sqrt(*nrm2).
-int blas_normalize(int type, const void* x, void* out, const double2* nrm2, double2* store, size_t n, cudaStream_t s);
-// y = argmin || sqrt(*beta2) e1 - H y || for the (m+1) x m Hessenberg H (column-major, ldh), m <= 32.
-int blas_hessenberg_solve(const double2* H, int ldh, int m, const double2* beta2, double2* y, cudaStream_t s);
+// Geometry of a batched vector operation: R systems, n elements each; the
+// vector v_j of system r is at v_j + r*vstride, w of system r at w + r*wstride.
+struct BVec {
+  size_t n;
+  int R;
+  size_t vstride;
+  size_t wstride;
+};
+inline BVec bvec(size_t n, int R, size_t stride) { return BVec{n, R, stride, stride}; }
+
+// Per-system complex scalars passed by value (R <= 32).
+struct Scal32 { double2 v[32]; };
+
+// out[r*ldo + j] = <v_j[r], w[r]> = sum conj(v_j) w (out2 too if non-null); mode 1 adds into out.
+int blas_multidot(int type, const BVec& b, const void* const* v, int k, const void* w, double2* out, int ldo,
+                  int mode, double2* out2, double2* partial, cudaStream_t s);
+// w[r] += sign * sum_j coeff[r*ldc + j] v_j[r] with device coefficients.
+int blas_multiaxpy(int type, const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc,
+                   double sign, cudaStream_t s);
+// y[r] = a_r x[r] + b_r y[r]; element types tx, ty (P64 / P32); b_r = 0: y not read.
+int blas_axpby2(int tx, const Scal32& a, const void* x, size_t xs, int ty, const Scal32& b, void* y, size_t ys,
+                size_t n, int R, cudaStream_t s);
+// out[r] = x[r] / sqrt(nrm2[r*ldn]); store[r*lds] = sqrt(nrm2[r*ldn]) if store != nullptr.
+int blas_normalize(int type, const BVec& b, const void* x, void* out, const double2* nrm2, int ldn, double2* store,
+                   int lds, cudaStream_t s);
+// y[r] = argmin || sqrt(beta2[r]) e1 - H_r y || for (m+1) x m Hessenberg H_r (column-major, ldh; H_r at H + r*ldr).
+int blas_hessenberg_solve(const double2* H, int ldh, int ldr, int m, const double2* beta2, double2* y, int ldy,
+                          int R, cudaStream_t s);
 
 }  // namespace sapmg

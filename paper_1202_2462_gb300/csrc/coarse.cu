@@ -20,12 +20,12 @@ namespace sapmg {
 // K3: rc[blk][chi*N + k] = sum over the block's sites and chirality chi of conj(v_k) r
 template <class R, class TS, class TV, class TC>
 __global__ void __launch_bounds__(256) restrict0_kernel(const TS* __restrict__ in, TC* __restrict__ out,
-                                                        const TV* __restrict__ Pv, int N) {
+                                                        const TV* __restrict__ Pv, int N, int nrhs, int nblocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R (*red)[4] = reinterpret_cast<R (*)[4]>(smem_raw);        // [8 * N][4]
-  const int blk = blockIdx.x, loc = threadIdx.x;
+  const int blk = blockIdx.x / nrhs, rhs = blockIdx.x % nrhs, loc = threadIdx.x;
   const int wid = loc >> 5, lane = loc & 31;
-  const size_t off = (size_t)blockIdx.y * gridDim.x * 12 * 256;   // rhs stride (one field)
+  const size_t off = (size_t)rhs * nblocks * 12 * 256;       // rhs stride (one field)
   Cplx<R> r[12];
   load_spinor<R>(in + off, blk, loc, r);
   for (int k = 0; k < N; ++k) {
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) restrict0_kernel(const TS* __restrict__ i
   }
   __syncthreads();
   const int n2 = 2 * N;
-  TC* o = out + (size_t)blockIdx.y * gridDim.x * n2 + (size_t)blk * n2;
+  TC* o = out + (size_t)rhs * nblocks * n2 + (size_t)blk * n2;
   for (int t = loc; t < n2; t += 256) {
     const int chi = t / N, k = t % N;
     R sr = 0, si = 0;
@@ -52,12 +52,12 @@ __global__ void __launch_bounds__(256) restrict0_kernel(const TS* __restrict__ i
 // K4: out(x) = sum_k v_k(x)|_chi e[blk][chi*N + k]   (overwrites out)
 template <class R, class TS, class TV, class TC>
 __global__ void __launch_bounds__(256) prolong0_kernel(const TC* __restrict__ in, TS* __restrict__ out,
-                                                       const TV* __restrict__ Pv, int N) {
+                                                       const TV* __restrict__ Pv, int N, int nrhs, int nblocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<R>* e = reinterpret_cast<Cplx<R>*>(smem_raw);             // [2N]
-  const int blk = blockIdx.x, loc = threadIdx.x;
+  const int blk = blockIdx.x / nrhs, rhs = blockIdx.x % nrhs, loc = threadIdx.x;
   const int n2 = 2 * N;
-  const TC* ein = in + (size_t)blockIdx.y * gridDim.x * n2 + (size_t)blk * n2;
+  const TC* ein = in + (size_t)rhs * nblocks * n2 + (size_t)blk * n2;
   for (int t = loc; t < n2; t += 256) e[t] = Io<R, TC>::ldc(ein + t);
   __syncthreads();
   Cplx<R> o[12];
@@ -71,19 +71,21 @@ __global__ void __launch_bounds__(256) prolong0_kernel(const TC* __restrict__ in
 #pragma unroll
     for (int c = 6; c < 12; ++c) cfma(o[c], Io<R, TV>::ld(v + c * 256), e1);
   }
-  store_spinor<R>(out + (size_t)blockIdx.y * gridDim.x * 12 * 256, blk, loc, o);
+  store_spinor<R>(out + (size_t)rhs * nblocks * 12 * 256, blk, loc, o);
 }
 
 template <class R, class TS, class TV, class TC>
 static int transfer0_run(bool restrict_, const Geom& g, const void* in, void* out, const void* Pv, int N, int nrhs,
                          cudaStream_t s) {
-  dim3 grid(g.nblocks, nrhs);
+  const unsigned grid = (unsigned)(g.nblocks * nrhs);   // right-hand side fastest: P shared through L2
   if (restrict_) {
     const size_t smem = sizeof(R) * 4 * 8 * N;
-    restrict0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TS*)in, (TC*)out, (const TV*)Pv, N); count_launches(1);
+    restrict0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TS*)in, (TC*)out, (const TV*)Pv, N, nrhs,
+                                                            g.nblocks); count_launches(1);
   } else {
     const size_t smem = sizeof(Cplx<R>) * 2 * N;
-    prolong0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TC*)in, (TS*)out, (const TV*)Pv, N); count_launches(1);
+    prolong0_kernel<R, TS, TV, TC><<<grid, 256, smem, s>>>((const TC*)in, (TS*)out, (const TV*)Pv, N, nrhs,
+                                                           g.nblocks); count_launches(1);
   }
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
@@ -288,34 +290,58 @@ __device__ __forceinline__ int cg_neighbour(const CGeom& c, int site, int d) {
   return site + (nx - x) * stride;
 }
 
-// K5: out[site][i] = sum_d sum_j M[site][d][j][i] x[nb_d(site)][j]
-template <class R, class TM, class TX>
+// K5: out_r[site][i] = sum_d sum_j M[site][d][j][i] x_r[nb_d(site)][j] for RB
+// right-hand sides at once: every matrix entry is loaded once and applied to
+// all RB vectors (the operator dominates the traffic; the vectors stay in L2).
+template <class R, class TM, class TX, int RB>
 __global__ void __launch_bounds__(256) coarse_apply_kernel(const TM* __restrict__ M, const TX* __restrict__ x,
-                                                           TX* __restrict__ out, CGeom c) {
+                                                           TX* __restrict__ out, CGeom c, int r0) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int n2 = c.n2;
   if (t >= (long long)c.nsites * n2) return;
   const int site = (int)(t / n2), i = (int)(t % n2);
-  const size_t roff = (size_t)blockIdx.y * c.nsites * n2;
-  const TX* xr = x + roff;
-  Cplx<R> acc = cmk<R>(0, 0);
+  const size_t fs = (size_t)c.nsites * n2;
+  const TX* xr = x + (size_t)r0 * fs;
+  Cplx<R> acc[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) acc[r] = cmk<R>(0, 0);
   for (int d = 0; d < 9; ++d) {
     const int nb = cg_neighbour(c, site, d);
     const TM* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
     const TX* xn = xr + (size_t)nb * n2;
-    for (int j = 0; j < n2; ++j) cfma(acc, Io<R, TM>::ld(m + (size_t)j * n2), Io<R, TX>::ld(xn + j));
+#pragma unroll 4
+    for (int j = 0; j < n2; ++j) {
+      const Cplx<R> mv = Io<R, TM>::ld(m + (size_t)j * n2);
+#pragma unroll
+      for (int r = 0; r < RB; ++r) cfma(acc[r], mv, Io<R, TX>::ld(xn + r * fs + j));
+    }
   }
-  Io<R, TX>::st(out + roff + t, acc);
+#pragma unroll
+  for (int r = 0; r < RB; ++r) Io<R, TX>::st(out + (size_t)(r0 + r) * fs + t, acc[r]);
+}
+
+template <class R, class TM, class TX>
+static void coarse_apply_t(const CGeom& c, const void* M, const void* x, void* out, int nrhs, cudaStream_t s) {
+  const long long n = (long long)c.nsites * c.n2;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int left = nrhs - r0;
+    const TM* m = (const TM*)M;
+    const TX* xi = (const TX*)x;
+    TX* o = (TX*)out;
+    if (left >= 12) { coarse_apply_kernel<R, TM, TX, 12><<<grid, 256, 0, s>>>(m, xi, o, c, r0); count_launches(1); r0 += 12; }
+    else if (left >= 4) { coarse_apply_kernel<R, TM, TX, 4><<<grid, 256, 0, s>>>(m, xi, o, c, r0); count_launches(1); r0 += 4; }
+    else if (left >= 2) { coarse_apply_kernel<R, TM, TX, 2><<<grid, 256, 0, s>>>(m, xi, o, c, r0); count_launches(1); r0 += 2; }
+    else { coarse_apply_kernel<R, TM, TX, 1><<<grid, 256, 0, s>>>(m, xi, o, c, r0); count_launches(1); r0 += 1; }
+  }
 }
 
 int launch_coarse_apply(int prec, const CGeom& c, const void* M, const void* x, void* out, int nrhs, cudaStream_t s) {
-  const long long n = (long long)c.nsites * c.n2;
-  dim3 grid((unsigned)((n + 255) / 256), nrhs);
   switch (prec) {
-    case P64: coarse_apply_kernel<double, double2, double2><<<grid, 256, 0, s>>>((const double2*)M, (const double2*)x, (double2*)out, c); count_launches(1); break;
-    case P32: coarse_apply_kernel<float, float2, float2><<<grid, 256, 0, s>>>((const float2*)M, (const float2*)x, (float2*)out, c); count_launches(1); break;
-    case P16: coarse_apply_kernel<float, __half2, float2><<<grid, 256, 0, s>>>((const __half2*)M, (const float2*)x, (float2*)out, c); count_launches(1); break;
-    case PBF: coarse_apply_kernel<float, __nv_bfloat162, float2><<<grid, 256, 0, s>>>((const __nv_bfloat162*)M, (const float2*)x, (float2*)out, c); count_launches(1); break;
+    case P64: coarse_apply_t<double, double2, double2>(c, M, x, out, nrhs, s); break;
+    case P32: coarse_apply_t<float, float2, float2>(c, M, x, out, nrhs, s); break;
+    case P16: coarse_apply_t<float, __half2, float2>(c, M, x, out, nrhs, s); break;
+    case PBF: coarse_apply_t<float, __nv_bfloat162, float2>(c, M, x, out, nrhs, s); break;
     default: return MG_ERR_ARG;
   }
   SAPMG_CUDA_TRY(cudaGetLastError());

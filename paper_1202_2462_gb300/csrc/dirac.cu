@@ -12,10 +12,13 @@ namespace sapmg {
 
 template <class R, class TS, class TG>
 __global__ void __launch_bounds__(256) dirac_kernel(TS* __restrict__ out, const TS* __restrict__ in,
-                                                    const TG* __restrict__ U, const TG* __restrict__ A, Geom g) {
-  const int blk = blockIdx.x;
+                                                    const TG* __restrict__ U, const TG* __restrict__ A, Geom g,
+                                                    int nrhs) {
+  // right-hand side fastest in the grid: the CTAs of one block run back to
+  // back and share its links and clover through L2
+  const int blk = blockIdx.x / nrhs;
   const int loc = threadIdx.x;
-  const size_t off = (size_t)blockIdx.y * g.V * 12;
+  const size_t off = (size_t)(blockIdx.x % nrhs) * g.V * 12;
   in += off;
   out += off;
   Cplx<R> p[12], o[12], acc[12];
@@ -29,8 +32,8 @@ __global__ void __launch_bounds__(256) dirac_kernel(TS* __restrict__ out, const 
 
 template <class R, class TS, class TG>
 static void run(const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs, cudaStream_t s) {
-  dim3 grid(g.nblocks, nrhs);
-  dirac_kernel<R, TS, TG><<<grid, 256, 0, s>>>((TS*)out, (const TS*)in, (const TG*)U, (const TG*)A, g); count_launches(1);
+  dirac_kernel<R, TS, TG><<<(unsigned)(g.nblocks * nrhs), 256, 0, s>>>((TS*)out, (const TS*)in, (const TG*)U,
+                                                                      (const TG*)A, g, nrhs); count_launches(1);
 }
 
 int launch_dirac(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,

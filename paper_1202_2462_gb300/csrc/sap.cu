@@ -55,14 +55,15 @@ __device__ __forceinline__ void block_reduce3(R& a, R& b, R& c, R (*red)[4]) {
 template <class R, class TS, class TG>
 __global__ void __launch_bounds__(256) sap_colour_kernel(TS* __restrict__ z, const TS* __restrict__ b,
                                                          const TG* __restrict__ U, const TG* __restrict__ A, Geom g,
-                                                         int colour, int n_mr) {
+                                                         int colour, int n_mr, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<R>* rs = reinterpret_cast<Cplx<R>*>(smem_raw);                    // [12][256]
   R (*red)[4] = reinterpret_cast<R (*)[4]>(smem_raw + sizeof(Cplx<R>) * 12 * 256);
-  const size_t off = (size_t)blockIdx.y * g.V * 12;
+  // right-hand side fastest in the grid (links and clover of a block shared through L2)
+  const size_t off = (size_t)(blockIdx.x % nrhs) * g.V * 12;
   z += off;
   b += off;
-  const int blk = colour_block(g, blockIdx.x, colour);
+  const int blk = colour_block(g, blockIdx.x / nrhs, colour);
   const int loc = threadIdx.x;
 
   // residual r = b - D z (Algorithm 1: residual update before the colour's block solves)
@@ -125,9 +126,8 @@ static int run(const Geom& g, void* z, const void* b, const void* U, const void*
                                         (int)smem));
     attr = true;
   }
-  dim3 grid(g.nblocks / 2, nrhs);
-  sap_colour_kernel<R, TS, TG><<<grid, 256, smem, s>>>((TS*)z, (const TS*)b, (const TG*)U, (const TG*)A, g, colour,
-                                                       n_mr); count_launches(1);
+  sap_colour_kernel<R, TS, TG><<<(unsigned)(g.nblocks / 2 * nrhs), 256, smem, s>>>(
+      (TS*)z, (const TS*)b, (const TG*)U, (const TG*)A, g, colour, n_mr, nrhs); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }

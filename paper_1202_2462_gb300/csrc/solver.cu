@@ -91,15 +91,15 @@ struct CoarseLevel {
   int store = P64;           // storage precision of M
   void* M64 = nullptr;       // FP64 operator (set-up result, export)
   void* M = nullptr;         // operator used by the solver (== M64 in FP64)
-  // fixed-step GMRES workspace (vector type = context's cycle type)
-  void* V = nullptr;         // (kmax + 1) vectors
-  void* w = nullptr;
+  // fixed-step GMRES workspace for R right-hand sides (vector type = the cycle's)
+  void* V = nullptr;         // (kmax + 1) batched vectors, vector j at V + j*R*n
+  void* w = nullptr;         // batched [R][n]
   void* x = nullptr;
   void* b = nullptr;
-  double2* H = nullptr;      // 33 x 32 column-major
-  double2* tmp = nullptr;    // 64 scratch scalars
-  double2* beta2 = nullptr;
-  double2* y = nullptr;
+  double2* H = nullptr;      // [R][33 x 33] column-major
+  double2* tmp = nullptr;    // [R][64] scratch scalars
+  double2* beta2 = nullptr;  // [R]
+  double2* y = nullptr;      // [R][33]
   size_t n() const { return (size_t)cg.nsites * cg.n2; }
 };
 
@@ -132,8 +132,10 @@ struct mg_ctx {
   // Krylov workspace
   int m = 0;
   void *V = nullptr, *Z = nullptr, *w = nullptr;       // outer (plain: FP64; mixed: FP32 inner)
-  void *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *b64 = nullptr;
-  double2* hd = nullptr;                   // device scalars (m + 2)
+  void *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *b64 = nullptr;   // [nrhs_max] fine fields
+  void* e32 = nullptr;                                                    // inner correction (mixed form)
+  int ldh = 0;                             // per-RHS stride of the scalar buffers
+  double2* hd = nullptr;                   // device scalars [nrhs_max][ldh]
   double2* hh = nullptr;                   // pinned host mirror
   Prof prof;
 
@@ -174,197 +176,257 @@ static int fine_dirac(mg_ctx* c, int prec, void* out, const void* in, int nrhs) 
   return launch_dirac(prec, c->g, out, in, U, A, nrhs, c->s);
 }
 
-static int dot_to(mg_ctx* c, int type, const void* a, const void* b, size_t n, double2* out) {
-  const void* v[1] = {a};
-  return blas_multidot(type, v, 1, b, n, out, 0, nullptr, c->partial, c->s);
+static int dot_to(mg_ctx* c, int type, const BVec& b, const void* x, const void* y, double2* out, int ldo) {
+  const void* v[1] = {x};
+  return blas_multidot(type, b, v, 1, y, out, ldo, 0, nullptr, c->partial, c->s);
 }
 
-// Fixed-step GMRES from zero on a coarse level (Sec. 4: 12 steps on the coarse grid):
-// Arnoldi with classical Gram-Schmidt applied twice, all scalars on the device.
-static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k) {
+static Scal32 scal_all(double re, int R) {
+  Scal32 s;
+  for (int r = 0; r < 32; ++r) s.v[r] = make_double2(r < R ? re : 0.0, 0.0);
+  return s;
+}
+
+// Fixed-step GMRES from zero on a coarse level for R right-hand sides at once
+// (Sec. 4: 12 steps on the coarse grid): Arnoldi with classical Gram-Schmidt
+// applied twice, all scalars on the device, one operator application per step
+// serving every right-hand side.
+static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k, int R) {
   const size_t n = L.n();
   const int vt = c->vt;
   const size_t eb = complex_bytes(vt);
-  auto Vj = [&](int j) { return (void*)((char*)L.V + (size_t)j * n * eb); };
-  TRY(dot_to(c, vt, L.b, L.b, n, L.beta2));
-  TRY(blas_normalize(vt, L.b, Vj(0), L.beta2, nullptr, n, c->s));
+  const BVec bv = bvec(n, R, n);
+  auto Vj = [&](int j) { return (void*)((char*)L.V + (size_t)j * R * n * eb); };
+  TRY(dot_to(c, vt, bv, L.b, L.b, L.beta2, 1));
+  TRY(blas_normalize(vt, bv, L.b, Vj(0), L.beta2, 1, nullptr, 0, c->s));
   std::vector<const void*> vl;
   for (int j = 0; j < k; ++j) {
     {
       ProfScope ps(c->prof, FAM_COARSE, c->s);
-      TRY(launch_coarse_apply(L.store, L.cg, L.M, Vj(j), L.w, 1, c->s));
+      TRY(launch_coarse_apply(L.store, L.cg, L.M, Vj(j), L.w, R, c->s));
     }
     vl.push_back(Vj(j));
     double2* hcol = L.H + (size_t)j * 33;
-    TRY(blas_multidot(vt, vl.data(), j + 1, L.w, n, hcol, 0, nullptr, c->partial, c->s));
-    TRY(blas_multiaxpy(vt, L.w, vl.data(), j + 1, hcol, -1.0, n, c->s));
-    TRY(blas_multidot(vt, vl.data(), j + 1, L.w, n, hcol, 1, L.tmp, c->partial, c->s));
-    TRY(blas_multiaxpy(vt, L.w, vl.data(), j + 1, L.tmp, -1.0, n, c->s));
-    TRY(dot_to(c, vt, L.w, L.w, n, L.tmp + 40));
-    TRY(blas_normalize(vt, L.w, Vj(j + 1), L.tmp + 40, hcol + j + 1, n, c->s));
+    TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
+    TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
+    TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 1, L.tmp, c->partial, c->s));
+    TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, c->s));
+    TRY(dot_to(c, vt, bv, L.w, L.w, L.tmp + 40, 33 * 33));
+    TRY(blas_normalize(vt, bv, L.w, Vj(j + 1), L.tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
   }
-  TRY(blas_hessenberg_solve(L.H, 33, k, L.beta2, L.y, c->s));
-  SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, n * eb, c->s));
-  TRY(blas_multiaxpy(vt, L.x, vl.data(), k, L.y, 1.0, n, c->s));
+  TRY(blas_hessenberg_solve(L.H, 33, 33 * 33, k, L.beta2, L.y, 33, R, c->s));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, (size_t)R * n * eb, c->s));
+  TRY(blas_multiaxpy(vt, bv, L.x, vl.data(), k, L.y, 33, 1.0, c->s));
   return MG_OK;
 }
 
-static int coarse_solve(mg_ctx* c, int level) {
+static int coarse_solve(mg_ctx* c, int level, int R) {
   if (level != 1) return fail(MG_ERR_ARG, "coarse level out of range");
-  return coarse_gmres(c, c->c1, c->p.coarse_iters);
+  return coarse_gmres(c, c->c1, c->p.coarse_iters, R);
 }
 
-// The multilevel cycle z = M v on the fine level (cycle vector type).
-static int cycle(mg_ctx* c, const void* v, void* z) {
+// The multilevel cycle z = M v on the fine level for R right-hand sides (cycle vector type).
+static int cycle(mg_ctx* c, const void* v, void* z, int R) {
   const size_t n = c->fine_n();
   if (c->p.n_levels == 1) {
-    SAPMG_CUDA_TRY(cudaMemsetAsync(z, 0, n * complex_bytes(c->vt), c->s));
-    return smoother_sweeps(c, v, z, c->p.nu_post, 1);
+    SAPMG_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)R * n * complex_bytes(c->vt), c->s));
+    return smoother_sweeps(c, v, z, c->p.nu_post, R);
   }
   {
     ProfScope ps(c->prof, FAM_RESTRICT, c->s);
-    TRY(launch_transfer0(true, c->pv_prec, c->g, v, c->c1.b, c->Pv, c->N0, 1, c->s));
+    TRY(launch_transfer0(true, c->pv_prec, c->g, v, c->c1.b, c->Pv, c->N0, R, c->s));
   }
-  TRY(coarse_solve(c, 1));
+  TRY(coarse_solve(c, 1, R));
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
-    TRY(launch_transfer0(false, c->pv_prec, c->g, c->c1.x, z, c->Pv, c->N0, 1, c->s));
+    TRY(launch_transfer0(false, c->pv_prec, c->g, c->c1.x, z, c->Pv, c->N0, R, c->s));
   }
-  return smoother_sweeps(c, v, z, c->p.nu_post, 1);
+  return smoother_sweeps(c, v, z, c->p.nu_post, R);
 }
 
-// One cycle of flexible GMRES(m) on A e = r from e = x (x updated in place,
-// x += Z y).  r is the current residual (type ft), rnorm its norm.  Stops when
-// the least-squares residual estimate <= abs_tol, after m steps or at iters_left.
-// Orthogonalisation: classical Gram-Schmidt with a second pass when the norm
-// drops below 1/sqrt(2) of its value (Daniel-Gragg-Kaufman-Stewart criterion).
-static int fgmres_cycle(mg_ctx* c, int ft, int aprec, const void* r, double rnorm, void* x, double abs_tol,
-                        int iters_left, int& done, double& est) {
+// One cycle of flexible GMRES(m) for R systems in lockstep, A e = r from e = x
+// (x updated in place, x += Z y).  r: current residuals (type ft); rnorm[r]
+// their norms (0 = system inactive).  System r stops when its least-squares
+// residual estimate <= abs_tol[r]; the cycle ends when every system has stopped,
+// after m steps or at iters_left.  Orthogonalisation: classical Gram-Schmidt
+// with a second pass when a norm drops below 1/sqrt(2) of its value (the
+// Daniel-Gragg-Kaufman-Stewart criterion).  done[r] = steps taken by system r.
+static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, const std::vector<double>& rnorm,
+                        void* x, const std::vector<double>& abs_tol, int iters_left, std::vector<int>& done,
+                        std::vector<double>& est) {
+  typedef std::complex<double> cd;
   const size_t n = c->fine_n();
   const size_t eb = complex_bytes(ft);
   const int m = std::min(c->m, std::max(1, iters_left));
-  auto Vj = [&](int j) { return (void*)((char*)c->V + (size_t)j * n * eb); };
-  auto Zj = [&](int j) { return (void*)((char*)c->Z + (size_t)j * n * eb); };
-  std::vector<std::complex<double>> H((size_t)(m + 1) * m, 0.0), g(m + 1, 0.0), sn(m, 0.0);
-  std::vector<double> cs(m, 0.0);
-  TRY(blas_axpby(ft, make_double2(1.0 / rnorm, 0), r, make_double2(0, 0), Vj(0), n, c->s));
-  g[0] = rnorm;
+  const int ld = c->ldh;
+  const BVec bv = bvec(n, R, n);
+  auto Vj = [&](int j) { return (void*)((char*)c->V + (size_t)j * R * n * eb); };
+  auto Zj = [&](int j) { return (void*)((char*)c->Z + (size_t)j * R * n * eb); };
+  std::vector<cd> H((size_t)R * (m + 1) * m, 0.0), g((size_t)R * (m + 1), 0.0), sn((size_t)R * m, 0.0);
+  std::vector<double> cs((size_t)R * m, 0.0), hn(R, 0.0);
+  std::vector<char> active(R, 0);
+  done.assign(R, 0);
+  est.assign(R, 0.0);
+  Scal32 a = scal_all(0, R), zero = scal_all(0, R);
+  int n_active = 0;
+  for (int q = 0; q < R; ++q) {
+    est[q] = rnorm[q];
+    if (rnorm[q] > 0 && rnorm[q] > abs_tol[q]) { active[q] = 1; ++n_active; a.v[q].x = 1.0 / rnorm[q]; }
+    g[(size_t)q * (m + 1)] = rnorm[q];
+  }
+  if (n_active == 0) return MG_OK;
+  TRY(blas_axpby2(ft, a, r, n, ft, zero, Vj(0), n, n, R, c->s));
+  auto Hq = [&](int q, int i, int j) -> cd& { return H[(size_t)q * (m + 1) * m + i + (size_t)j * (m + 1)]; };
   std::vector<const void*> vl;
-  int j_done = 0;
-  est = rnorm;
   for (int j = 0; j < m; ++j) {
-    TRY(cycle(c, Vj(j), Zj(j)));
-    TRY(fine_dirac(c, aprec, c->w, Zj(j), 1));
+    TRY(cycle(c, Vj(j), Zj(j), R));
+    TRY(fine_dirac(c, aprec, c->w, Zj(j), R));
     vl.push_back(Vj(j));
-    // h = V^dagger w and ||w||^2 in one fused pass
-    vl.push_back(c->w);
-    TRY(blas_multidot(ft, vl.data(), j + 2, c->w, n, c->hd, 0, nullptr, c->partial, c->s));
+    vl.push_back(c->w);                  // h = V^dagger w and ||w||^2 in one pass
+    TRY(blas_multidot(ft, bv, vl.data(), j + 2, c->w, c->hd, ld, 0, nullptr, c->partial, c->s));
     vl.pop_back();
-    TRY(blas_multiaxpy(ft, c->w, vl.data(), j + 1, c->hd, -1.0, n, c->s));
-    TRY(dot_to(c, ft, c->w, c->w, n, c->hd + j + 2));
-    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * (j + 3), cudaMemcpyDeviceToHost, c->s));
+    TRY(blas_multiaxpy(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->s));
+    TRY(dot_to(c, ft, bv, c->w, c->w, c->hd + j + 2, ld));
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * R * ld, cudaMemcpyDeviceToHost, c->s));
     SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
-    for (int i = 0; i <= j; ++i) H[i + (size_t)j * (m + 1)] = std::complex<double>(c->hh[i].x, c->hh[i].y);
-    double before = c->hh[j + 1].x, after = c->hh[j + 2].x;
-    if (after < 0.5 * before) {
-      TRY(blas_multidot(ft, vl.data(), j + 1, c->w, n, c->hd, 0, nullptr, c->partial, c->s));
-      TRY(blas_multiaxpy(ft, c->w, vl.data(), j + 1, c->hd, -1.0, n, c->s));
-      TRY(dot_to(c, ft, c->w, c->w, n, c->hd + j + 2));
-      SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * (j + 3), cudaMemcpyDeviceToHost, c->s));
+    bool again = false;
+    for (int q = 0; q < R; ++q) {
+      const double2* h = c->hh + (size_t)q * ld;
+      for (int i = 0; i <= j; ++i) Hq(q, i, j) = cd(h[i].x, h[i].y);
+      hn[q] = h[j + 2].x;
+      if (active[q] && h[j + 2].x < 0.5 * h[j + 1].x) again = true;
+    }
+    if (again) {
+      TRY(blas_multidot(ft, bv, vl.data(), j + 1, c->w, c->hd, ld, 0, nullptr, c->partial, c->s));
+      TRY(blas_multiaxpy(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->s));
+      TRY(dot_to(c, ft, bv, c->w, c->w, c->hd + j + 2, ld));
+      SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * R * ld, cudaMemcpyDeviceToHost, c->s));
       SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
-      for (int i = 0; i <= j; ++i) H[i + (size_t)j * (m + 1)] += std::complex<double>(c->hh[i].x, c->hh[i].y);
-      after = c->hh[j + 2].x;
+      for (int q = 0; q < R; ++q) {
+        const double2* h = c->hh + (size_t)q * ld;
+        for (int i = 0; i <= j; ++i) Hq(q, i, j) += cd(h[i].x, h[i].y);
+        hn[q] = h[j + 2].x;
+      }
     }
-    const double hn = std::sqrt(std::max(after, 0.0));
-    H[j + 1 + (size_t)j * (m + 1)] = hn;
-    // Givens rotations on column j
-    for (int i = 0; i < j; ++i) {
-      auto& a = H[i + (size_t)j * (m + 1)];
-      auto& b = H[i + 1 + (size_t)j * (m + 1)];
-      const std::complex<double> t = cs[i] * a + sn[i] * b;
-      b = -std::conj(sn[i]) * a + cs[i] * b;
-      a = t;
+    n_active = 0;
+    for (int q = 0; q < R; ++q) {
+      a.v[q] = make_double2(0, 0);
+      if (!active[q]) continue;
+      const double hq = std::sqrt(std::max(hn[q], 0.0));
+      Hq(q, j + 1, j) = hq;
+      double* csq = &cs[(size_t)q * m];
+      cd* snq = &sn[(size_t)q * m];
+      cd* gq = &g[(size_t)q * (m + 1)];
+      for (int i = 0; i < j; ++i) {
+        cd& u = Hq(q, i, j);
+        cd& v = Hq(q, i + 1, j);
+        const cd t = csq[i] * u + snq[i] * v;
+        v = -std::conj(snq[i]) * u + csq[i] * v;
+        u = t;
+      }
+      cd& u = Hq(q, j, j);
+      cd& v = Hq(q, j + 1, j);
+      const double na = std::abs(u), nb = std::abs(v), den = std::sqrt(na * na + nb * nb);
+      if (den == 0.0) { csq[j] = 1; snq[j] = 0; }
+      else if (na == 0.0) { csq[j] = 0; snq[j] = 1; }
+      else { csq[j] = na / den; snq[j] = (u / na) * std::conj(v) / den; }
+      u = csq[j] * u + snq[j] * v;
+      v = 0.0;
+      gq[j + 1] = -std::conj(snq[j]) * gq[j];
+      gq[j] = csq[j] * gq[j];
+      done[q] = j + 1;
+      est[q] = std::abs(gq[j + 1]);
+      if (est[q] <= abs_tol[q] || hq == 0.0) { active[q] = 0; continue; }
+      a.v[q].x = 1.0 / hq;
+      ++n_active;
     }
-    {
-      auto& a = H[j + (size_t)j * (m + 1)];
-      auto& b = H[j + 1 + (size_t)j * (m + 1)];
-      const double na = std::abs(a), nb = std::abs(b);
-      const double den = std::sqrt(na * na + nb * nb);
-      if (den == 0.0) { cs[j] = 1; sn[j] = 0; }
-      else if (na == 0.0) { cs[j] = 0; sn[j] = 1; }
-      else { cs[j] = na / den; sn[j] = (a / na) * std::conj(b) / den; }
-      a = cs[j] * a + sn[j] * b;
-      b = 0.0;
-      g[j + 1] = -std::conj(sn[j]) * g[j];
-      g[j] = cs[j] * g[j];
-    }
-    j_done = j + 1;
-    est = std::abs(g[j + 1]);
-    if (est <= abs_tol || hn == 0.0 || j + 1 == m) break;
-    TRY(blas_axpby(ft, make_double2(1.0 / hn, 0), c->w, make_double2(0, 0), Vj(j + 1), n, c->s));
+    if (n_active == 0 || j + 1 == m) break;
+    TRY(blas_axpby2(ft, a, c->w, n, ft, zero, Vj(j + 1), n, n, R, c->s));
   }
-  // back substitution and x += Z y
-  std::vector<std::complex<double>> y(j_done);
-  for (int i = j_done - 1; i >= 0; --i) {
-    std::complex<double> s = g[i];
-    for (int k = i + 1; k < j_done; ++k) s -= H[i + (size_t)k * (m + 1)] * y[k];
-    const auto d = H[i + (size_t)i * (m + 1)];
-    y[i] = std::abs(d) > 0 ? s / d : 0.0;
+  // back substitution per system and x += Z y
+  int jmax = 0;
+  for (int q = 0; q < R; ++q) {
+    jmax = std::max(jmax, done[q]);
+    std::vector<cd> y(done[q]);
+    const cd* gq = &g[(size_t)q * (m + 1)];
+    for (int i = done[q] - 1; i >= 0; --i) {
+      cd acc = gq[i];
+      for (int k = i + 1; k < done[q]; ++k) acc -= Hq(q, i, k) * y[k];
+      const cd d = Hq(q, i, i);
+      y[i] = std::abs(d) > 0 ? acc / d : 0.0;
+    }
+    double2* hq = c->hh + (size_t)q * ld;
+    for (int i = 0; i < ld; ++i) hq[i] = i < done[q] ? make_double2(y[i].real(), y[i].imag()) : make_double2(0, 0);
   }
-  for (int i = 0; i < j_done; ++i) c->hh[i] = make_double2(y[i].real(), y[i].imag());
-  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hd, c->hh, sizeof(double2) * j_done, cudaMemcpyHostToDevice, c->s));
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hd, c->hh, sizeof(double2) * R * ld, cudaMemcpyHostToDevice, c->s));
   std::vector<const void*> zl;
-  for (int i = 0; i < j_done; ++i) zl.push_back(Zj(i));
-  TRY(blas_multiaxpy(ft, x, zl.data(), j_done, c->hd, 1.0, n, c->s));
+  for (int i = 0; i < jmax; ++i) zl.push_back(Zj(i));
+  TRY(blas_multiaxpy(ft, bv, x, zl.data(), jmax, c->hd, ld, 1.0, c->s));
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));   // hh is reused by the next cycle
-  done = j_done;
   return MG_OK;
 }
 
-static double host_norm(mg_ctx* c, int type, const void* x, size_t n, int& rc) {
-  rc = dot_to(c, type, x, x, n, c->hd + c->m + 1);
-  if (rc < 0) return 0;
-  cudaMemcpyAsync(c->hh + c->m + 1, c->hd + c->m + 1, sizeof(double2), cudaMemcpyDeviceToHost, c->s);
-  if (cudaStreamSynchronize(c->s) != cudaSuccess) { rc = fail(MG_ERR_CUDA, "synchronize failed"); return 0; }
-  return std::sqrt(std::max(c->hh[c->m + 1].x, 0.0));
+static int host_norms(mg_ctx* c, int type, const void* x, int R, std::vector<double>& out) {
+  const size_t n = c->fine_n();
+  TRY(dot_to(c, type, bvec(n, R, n), x, x, c->hd, c->ldh));
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * R * c->ldh, cudaMemcpyDeviceToHost, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  out.resize(R);
+  for (int q = 0; q < R; ++q) out[q] = std::sqrt(std::max(c->hh[(size_t)q * c->ldh].x, 0.0));
+  return MG_OK;
 }
 
-// Solve one right-hand side: b64 (blocked FP64) -> x64 (blocked FP64).
-static int solve_one(mg_ctx* c, int& iters, int& restarts, double& relres) {
+// Solve R right-hand sides together: b64 (batched blocked FP64) -> x64.
+static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relres) {
   const size_t n = c->fine_n();
-  int rc = 0;
-  const double bn = host_norm(c, P64, c->b64, n, rc);
-  TRY(rc);
-  SAPMG_CUDA_TRY(cudaMemsetAsync(c->x64, 0, n * 16, c->s));
+  std::vector<double> bn, rn, tol(R), ones(R, 1.0), inner(R), est;
+  std::vector<int> done;
+  TRY(host_norms(c, P64, c->b64, R, bn));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(c->x64, 0, (size_t)R * n * 16, c->s));
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->r64, c->b64, (size_t)R * n * 16, cudaMemcpyDeviceToDevice, c->s));
+  for (int q = 0; q < R; ++q) tol[q] = c->p.tol * bn[q];
   iters = 0;
   restarts = 0;
-  if (bn == 0.0) { relres = 0; return MG_OK; }
-  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->r64, c->b64, n * 16, cudaMemcpyDeviceToDevice, c->s));
-  const double tol = c->p.tol * bn;
+  const Scal32 one = scal_all(1.0, R), zero = scal_all(0.0, R), minus = scal_all(-1.0, R);
   for (;;) {
-    const double rn = host_norm(c, P64, c->r64, n, rc);
-    TRY(rc);
-    relres = rn / bn;
-    if (c->p.verbose) std::fprintf(stderr, "[sapmg] outer %d iters %d relres %.3e\n", restarts, iters, relres);
-    if (rn <= tol) return MG_OK;
-    if (iters >= c->p.maxiter) return MG_NOT_CONVERGED;
-    int done = 0;
-    double est = 0;
-    if (c->prec == P64) {
-      TRY(fgmres_cycle(c, P64, P64, c->r64, rn, c->x64, tol, c->p.maxiter - iters, done, est));
-    } else {
-      // FP64 defect correction around an FP32 flexible GMRES cycle
-      TRY(blas_axpby2(P64, make_double2(1.0 / rn, 0), c->r64, P32, make_double2(0, 0), c->t64, n, c->s));
-      SAPMG_CUDA_TRY(cudaMemsetAsync(c->io_b, 0, n * 8, c->s));
-      const double inner = std::max(2e-6, 0.5 * tol / rn);
-      TRY(fgmres_cycle(c, P32, P32, c->t64, 1.0, c->io_b, inner, c->p.maxiter - iters, done, est));
-      TRY(blas_axpby2(P32, make_double2(rn, 0), c->io_b, P64, make_double2(1, 0), c->x64, n, c->s));
+    TRY(host_norms(c, P64, c->r64, R, rn));
+    relres = 0;
+    bool all = true;
+    for (int q = 0; q < R; ++q) {
+      const double rel = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
+      relres = std::max(relres, rel);
+      if (rn[q] > tol[q]) all = false;
     }
-    iters += done;
+    if (c->p.verbose) std::fprintf(stderr, "[sapmg] outer %d iters %d max relres %.3e\n", restarts, iters, relres);
+    if (all) return MG_OK;
+    if (iters >= c->p.maxiter) return MG_NOT_CONVERGED;
+    std::vector<double> act(R);
+    for (int q = 0; q < R; ++q) act[q] = rn[q] > tol[q] ? rn[q] : 0.0;
+    if (c->prec == P64) {
+      TRY(fgmres_cycle(c, P64, P64, R, c->r64, act, c->x64, tol, c->p.maxiter - iters, done, est));
+    } else {
+      // FP64 defect correction around an FP32 flexible GMRES cycle on the normalised residual
+      Scal32 a = zero, unit = zero;
+      for (int q = 0; q < R; ++q) {
+        if (act[q] > 0) { a.v[q].x = 1.0 / act[q]; unit.v[q].x = 1.0; }
+        inner[q] = act[q] > 0 ? std::max(2e-6, 0.5 * tol[q] / act[q]) : 1.0;
+      }
+      std::vector<double> unorm(R);
+      for (int q = 0; q < R; ++q) unorm[q] = act[q] > 0 ? 1.0 : 0.0;
+      TRY(blas_axpby2(P64, a, c->r64, n, P32, zero, c->t64, n, n, R, c->s));
+      SAPMG_CUDA_TRY(cudaMemsetAsync(c->e32, 0, (size_t)R * n * 8, c->s));
+      TRY(fgmres_cycle(c, P32, P32, R, c->t64, unorm, c->e32, inner, c->p.maxiter - iters, done, est));
+      Scal32 sc = zero;
+      for (int q = 0; q < R; ++q) sc.v[q].x = act[q];
+      TRY(blas_axpby2(P32, sc, c->e32, n, P64, one, c->x64, n, n, R, c->s));
+    }
+    int step = 0;
+    for (int q = 0; q < R; ++q) step = std::max(step, done[q]);
+    iters += step;
     restarts += 1;
-    TRY(fine_dirac(c, P64, c->r64, c->x64, 1));
-    TRY(blas_axpby(P64, make_double2(1, 0), c->b64, make_double2(-1, 0), c->r64, n, c->s));
-    if (done == 0) return MG_NOT_CONVERGED;
+    TRY(fine_dirac(c, P64, c->r64, c->x64, R));
+    TRY(blas_axpby2(P64, one, c->b64, n, P64, minus, c->r64, n, n, R, c->s));
+    if (step == 0) return MG_NOT_CONVERGED;
   }
 }
 
@@ -389,15 +451,16 @@ static int check_finite(mg_ctx* c, const double* x, size_t n_doubles) {
 // Gram-Schmidt against the previous vectors, applied twice, then normalise.
 static int orthonormalise(mg_ctx* c, void* V, int N) {
   const size_t n = c->fine_n();
+  const BVec one = bvec(n, 1, n);
   auto Vk = [&](int k) { return (void*)((char*)V + (size_t)k * n * 16); };
   std::vector<const void*> vl;
   for (int k = 0; k < N; ++k) {
     for (int pass = 0; pass < 2 && k > 0; ++pass) {
-      TRY(blas_multidot(P64, vl.data(), k, Vk(k), n, c->hd, 0, nullptr, c->partial, c->s));
-      TRY(blas_multiaxpy(P64, Vk(k), vl.data(), k, c->hd, -1.0, n, c->s));
+      TRY(blas_multidot(P64, one, vl.data(), k, Vk(k), c->hd, c->ldh, 0, nullptr, c->partial, c->s));
+      TRY(blas_multiaxpy(P64, one, Vk(k), vl.data(), k, c->hd, c->ldh, -1.0, c->s));
     }
-    TRY(dot_to(c, P64, Vk(k), Vk(k), n, c->hd + 40));
-    TRY(blas_normalize(P64, Vk(k), Vk(k), c->hd + 40, nullptr, n, c->s));
+    TRY(dot_to(c, P64, one, Vk(k), Vk(k), c->hd + c->ldh - 1, 1));
+    TRY(blas_normalize(P64, one, Vk(k), Vk(k), c->hd + c->ldh - 1, 1, nullptr, 0, c->s));
     vl.push_back(Vk(k));
   }
   return MG_OK;
@@ -421,9 +484,10 @@ static int setup_level0(mg_ctx* c) {
       if (c->vt == P64) {
         TRY(smoother_sweeps(c, c->zero_f, vk, 1, 1));
       } else {
-        TRY(blas_axpby2(P64, make_double2(1, 0), vk, P32, make_double2(0, 0), c->io_b, n, c->s));
+        const Scal32 one = scal_all(1.0, 1), zero = scal_all(0.0, 1);
+        TRY(blas_axpby2(P64, one, vk, n, P32, zero, c->io_b, n, n, 1, c->s));
         TRY(smoother_sweeps(c, c->zero_f, c->io_b, 1, 1));
-        TRY(blas_axpby2(P32, make_double2(1, 0), c->io_b, P64, make_double2(0, 0), vk, n, c->s));
+        TRY(blas_axpby2(P32, one, c->io_b, n, P64, zero, vk, n, n, 1, c->s));
       }
     }
     TRY(orthonormalise(c, c->V64, N));
@@ -452,18 +516,18 @@ static int setup_level0(mg_ctx* c) {
   return MG_OK;
 }
 
-static int alloc_coarse_ws(mg_ctx* c, CoarseLevel& L, int kmax) {
+static int alloc_coarse_ws(mg_ctx* c, CoarseLevel& L, int kmax, int R) {
   const size_t n = L.n(), eb = complex_bytes(c->vt);
-  L.V = c->alloc((size_t)(kmax + 1) * n * eb);
-  L.w = c->alloc(n * eb);
-  L.x = c->alloc(n * eb);
-  L.b = c->alloc(n * eb);
-  L.H = (double2*)c->alloc(sizeof(double2) * 33 * 33);
-  L.tmp = (double2*)c->alloc(sizeof(double2) * 64);
-  L.beta2 = (double2*)c->alloc(sizeof(double2));
-  L.y = (double2*)c->alloc(sizeof(double2) * 33);
+  L.V = c->alloc((size_t)(kmax + 1) * R * n * eb);
+  L.w = c->alloc((size_t)R * n * eb);
+  L.x = c->alloc((size_t)R * n * eb);
+  L.b = c->alloc((size_t)R * n * eb);
+  L.H = (double2*)c->alloc(sizeof(double2) * 33 * 33 * R);
+  L.tmp = (double2*)c->alloc(sizeof(double2) * 33 * 33 * R);
+  L.beta2 = (double2*)c->alloc(sizeof(double2) * R);
+  L.y = (double2*)c->alloc(sizeof(double2) * 33 * R);
   if (!L.V || !L.w || !L.x || !L.b || !L.H || !L.tmp || !L.beta2 || !L.y) return fail(MG_ERR_OOM, "coarse workspace");
-  SAPMG_CUDA_TRY(cudaMemsetAsync(L.H, 0, sizeof(double2) * 33 * 33, c->s));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(L.H, 0, sizeof(double2) * 33 * 33 * R, c->s));
   return MG_OK;
 }
 
@@ -479,7 +543,7 @@ static int validate(const mg_params* p) {
   if (!(p->tol > 0)) return fail(MG_ERR_ARG, "tol must be positive");
   if (p->maxiter < 1) return fail(MG_ERR_ARG, "maxiter must be positive");
   if (p->precision < MG_FP64 || p->precision > MG_BF16) return fail(MG_ERR_ARG, "unknown precision");
-  if (p->nrhs_max < 1) return fail(MG_ERR_ARG, "nrhs_max must be positive");
+  if (p->nrhs_max < 1 || p->nrhs_max > 32) return fail(MG_ERR_ARG, "nrhs_max must be in 1..32");
   return MG_OK;
 }
 
@@ -515,29 +579,32 @@ static int do_setup(mg_ctx* c, const double* U) {
   }
   // workspace
   const size_t eb = complex_bytes(c->vt);
+  const int R = p.nrhs_max;
   c->partial = (double2*)c->alloc(sizeof(double2) * kMaxReduceCta * 8);
   c->zero_f = c->alloc(n * eb);
-  c->io_a = c->alloc((size_t)p.nrhs_max * n * 16);
-  c->io_b = c->alloc((size_t)p.nrhs_max * n * 16);
+  c->io_a = c->alloc((size_t)R * n * 16);
+  c->io_b = c->alloc((size_t)R * n * 16);
   c->m = p.fgmres_m;
+  c->ldh = std::max(c->m, 32) + 8;
   const size_t ft = complex_bytes(c->vt);
-  c->V = c->alloc((size_t)(c->m + 1) * n * ft);
-  c->Z = c->alloc((size_t)c->m * n * ft);
-  c->w = c->alloc(n * ft);
-  c->x64 = c->alloc(n * 16);
-  c->r64 = c->alloc(n * 16);
-  c->t64 = c->alloc(n * 16);
-  c->b64 = c->alloc(n * 16);
-  c->hd = (double2*)c->alloc(sizeof(double2) * (c->m + 64));
+  c->V = c->alloc((size_t)(c->m + 1) * R * n * ft);
+  c->Z = c->alloc((size_t)c->m * R * n * ft);
+  c->w = c->alloc((size_t)R * n * ft);
+  c->x64 = c->alloc((size_t)R * n * 16);
+  c->r64 = c->alloc((size_t)R * n * 16);
+  c->t64 = c->alloc((size_t)R * n * 16);
+  c->b64 = c->alloc((size_t)R * n * 16);
+  c->e32 = c->vt == P64 ? c->t64 : c->alloc((size_t)R * n * 8);
+  c->hd = (double2*)c->alloc(sizeof(double2) * R * c->ldh);
   if (!c->partial || !c->zero_f || !c->io_a || !c->io_b || !c->V || !c->Z || !c->w || !c->x64 || !c->r64 ||
-      !c->t64 || !c->b64 || !c->hd)
+      !c->t64 || !c->b64 || !c->hd || !c->e32)
     return fail(MG_ERR_OOM, "workspace");
-  if (cudaMallocHost((void**)&c->hh, sizeof(double2) * (c->m + 64)) != cudaSuccess) return fail(MG_ERR_OOM, "host");
+  if (cudaMallocHost((void**)&c->hh, sizeof(double2) * R * c->ldh) != cudaSuccess) return fail(MG_ERR_OOM, "host");
   SAPMG_CUDA_TRY(cudaMemsetAsync(c->zero_f, 0, n * eb, c->s));
   if (p.n_levels >= 2) {
     c->N0 = p.n_vec[0];
     TRY(setup_level0(c));
-    TRY(alloc_coarse_ws(c, c->c1, p.coarse_iters));
+    TRY(alloc_coarse_ws(c, c->c1, p.coarse_iters, R));
   }
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
   return MG_OK;
@@ -647,15 +714,16 @@ int mg_solve(mg_ctx* c, const double* b, double* z, int nrhs, mg_solve_info* inf
   const size_t n = c->fine_n();
   int status = MG_OK, it_sum = 0, rs_sum = 0;
   double worst = 0;
-  for (int r = 0; r < nrhs; ++r) {
-    TRY(launch_pack_spinor(P64, b + r * n * 2, P64, c->b64, c->g, 1, c->s));
+  for (int r0 = 0; r0 < nrhs; r0 += c->p.nrhs_max) {
+    const int R = std::min(c->p.nrhs_max, nrhs - r0);
+    TRY(launch_pack_spinor(P64, b + (size_t)r0 * n * 2, P64, c->b64, c->g, R, c->s));
     int it = 0, rs = 0;
     double rel = 0;
-    const int rc = solve_one(c, it, rs, rel);
+    const int rc = solve_batch(c, R, it, rs, rel);
     if (rc < 0) return rc;
     if (rc == MG_NOT_CONVERGED) status = MG_NOT_CONVERGED;
-    TRY(launch_unpack_spinor(P64, c->x64, P64, z + r * n * 2, c->g, 1, c->s));
-    it_sum += it;
+    TRY(launch_unpack_spinor(P64, c->x64, P64, z + (size_t)r0 * n * 2, c->g, R, c->s));
+    it_sum += it * R;
     rs_sum += rs;
     worst = std::max(worst, rel);
   }
@@ -745,7 +813,7 @@ int mg_coarse_solve(mg_ctx* c, int level, const void* in, void* out, int prec) {
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
   const size_t bytes = c->c1.n() * complex_bytes(c->vt);
   SAPMG_CUDA_TRY(cudaMemcpyAsync(c->c1.b, in, bytes, cudaMemcpyDeviceToDevice, c->s));
-  TRY(coarse_solve(c, 1));
+  TRY(coarse_solve(c, 1, 1));
   SAPMG_CUDA_TRY(cudaMemcpyAsync(out, c->c1.x, bytes, cudaMemcpyDeviceToDevice, c->s));
   return MG_OK;
 }
@@ -758,7 +826,7 @@ int mg_precondition(mg_ctx* c, const void* v, void* z, int prec) {
   const void* src;
   TRY(stage_in(c, v, prec, blocked, 1, &src));
   void* dst = blocked ? z : c->io_b;
-  TRY(cycle(c, src, dst));
+  TRY(cycle(c, src, dst, 1));
   if (!blocked) {
     const int t = prec == P64 ? P64 : P32;
     TRY(launch_unpack_spinor(t, dst, t, z, c->g, 1, c->s));
