@@ -41,10 +41,17 @@ def flops_sap_site(n_mr):
     return 1896.0 + 1854.0 * n_mr
 
 
-def bytes_sap_site(prec):
-    spinor = 4 * 12 * (16 if prec == "fp64" else 8)          # b, z, halo z read; z written
+def bytes_sap_spinor(prec):
+    return 4 * 12 * (16 if prec == "fp64" else 8)             # b, z, halo z read; z written (per RHS)
+
+
+def bytes_sap_fields(prec):
     store = {"fp64": 16, "fp32": 8, "fp16": 4, "bf16": 4}[prec]
-    return spinor + 2 * 36 * store                              # links (4 x 9 complex) + clover (36 slots)
+    return 2 * 36 * store                                       # links (4 x 9 complex) + clover (36 slots)
+
+
+def bytes_sap_site(prec):
+    return bytes_sap_spinor(prec) + bytes_sap_fields(prec)
 
 
 def bytes_dirac_site(prec):
@@ -303,15 +310,18 @@ def run_ours(a, wl):
 
     hbm, peak_kind = load_peaks()
     if dominant == "sap":
-        per_launch_units = v // 2 * nrhs_per_launch(nrhs)
+        # one launch = one colour pass over V/2 sites for every right-hand side
+        units = (v // 2) * nrhs
         avg_s = ms_prof / max(n_prof, 1) / 1e3
-        tflops = flops_sap_site(wl["n_mr"]) * (v // 2) / avg_s / 1e12 if n_prof else None
+        tflops = flops_sap_site(wl["n_mr"]) * units / avg_s / 1e12 if n_prof else None
+        alg_bytes = (v // 2) * (nrhs * bytes_sap_spinor(prec) + bytes_sap_fields(prec))
         roof = {"kernel": "sap_colour_kernel", "bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS if tflops else None, "traffic": None,
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "hbm_gbs": bytes_sap_site(prec) * (v // 2) / avg_s / 1e9 if n_prof else None,
-                "hbm_frac": (bytes_sap_site(prec) * (v // 2) / avg_s / 1e9) / hbm if n_prof else None,
-                "launches": n_prof, "avg_launch_ms": avg_s * 1e3, "units_per_launch": per_launch_units}
+                "hbm_gbs": alg_bytes / avg_s / 1e9 if n_prof else None,
+                "hbm_frac": alg_bytes / avg_s / 1e9 / hbm if n_prof else None,
+                "launches": n_prof, "avg_launch_ms": avg_s * 1e3, "sites_x_rhs_per_launch": units,
+                "flop_per_site": flops_sap_site(wl["n_mr"]), "alg_bytes_per_launch": alg_bytes}
     else:
         avg_s = ms_prof / max(n_prof, 1) / 1e3
         roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,

@@ -33,6 +33,12 @@ WORKLOADS = {
         rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=2, setup_iters=8, coarse_iters=24, fgmres_m=20, tol=1e-10,
         precision="bf16", metric=METRIC, ref_iterations=60),
+    # Mid-size case for Nsight Compute captures: fields larger than L2, a few GB on the device.
+    "32^3x32": dict(
+        dims=(32, 32, 32, 32), eps=0.6, gauge_seed=104, c_sw=1.0, m0=-0.8,
+        rhs="gaussian", rhs_seed=204, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(12,),
+        n_mr=4, nu_post=2, setup_iters=2, coarse_iters=12, fgmres_m=10, tol=1e-10, maxiter=30,
+        precision="bf16", metric=METRIC, ref_iterations=60),
 }
 
 
