@@ -167,6 +167,9 @@ int mg_get_coarse_op(mg_ctx* ctx, int level, double* out);
 int mg_restrict(mg_ctx* ctx, int level, const void* in, void* out, int prec);
 int mg_prolong(mg_ctx* ctx, int level, const void* in, void* out, int prec);
 int mg_coarse_apply(mg_ctx* ctx, int level, const void* in, void* out, int prec);
+/* The same for nrhs coarse vectors stored back to back ([nrhs][sites][2N]);
+ * synchronises (it checks the device error flag of the bounded waits). */
+int mg_coarse_apply_batch(mg_ctx* ctx, int level, const void* in, void* out, int prec, int nrhs);
 
 /* Approximate solve on coarse level `level` >= 1 exactly as the cycle does it
  * (fixed-step GMRES on the coarsest level, fixed-step flexible GMRES with the

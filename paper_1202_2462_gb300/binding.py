@@ -84,6 +84,7 @@ _SIGNATURES = {
     "mg_restrict": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_prolong": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_coarse_apply": (_I, [_VP, _I, _VP, _VP, _I]),
+    "mg_coarse_apply_batch": (_I, [_VP, _I, _VP, _VP, _I, _I]),
     "mg_coarse_solve": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_precondition": (_I, [_VP, _VP, _VP, _I]),
     "mg_set_profiling": (_I, [_VP, _I]),
@@ -196,6 +197,10 @@ def mg_prolong(ctx, level, inp, out, prec):
 
 def mg_coarse_apply(ctx, level, inp, out, prec):
     return _check(lib().mg_coarse_apply(ctx, level, _ptr(inp), _ptr(out), prec), "mg_coarse_apply")
+
+
+def mg_coarse_apply_batch(ctx, level, inp, out, prec, nrhs):
+    return _check(lib().mg_coarse_apply_batch(ctx, level, _ptr(inp), _ptr(out), prec, nrhs), "mg_coarse_apply_batch")
 
 
 def mg_coarse_solve(ctx, level, inp, out, prec):

@@ -4,8 +4,8 @@
 //
 // A batched vector is R fields stored back to back (field r at base + r*stride).
 // Reductions are deterministic: every CTA writes its partial sums, one CTA per
-// right-hand side adds them in a fixed order.  Per-thread partial sums use the
-// vector's own precision; CTA-level and final sums use FP64.
+// right-hand side adds them in a fixed order.  Per-thread and per-warp partial
+// sums use the vector's own precision; CTA-level and final sums use FP64.
 #include "internal.h"
 #include "blas.h"
 
@@ -17,9 +17,11 @@ template <> struct RealOf<float2> { typedef float R; };
 
 template <class T2> struct Ptrs8 { const T2* p[8]; };
 
+// CTAs per right-hand side of a reduction: at least 8 elements per thread, and
+// R * CTAs within the partial buffer.
 static int reduce_ctas(size_t n, int R) {
   const size_t per = std::max<size_t>(1, (size_t)kMaxReduceCta / (size_t)std::max(R, 1));
-  return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, per));
+  return (int)std::max<size_t>(1, std::min<size_t>((n + 2047) / 2048, per));
 }
 
 template <class T2, int K>
@@ -43,11 +45,12 @@ __global__ void __launch_bounds__(256) multidot_partial(Ptrs8<T2> v, const T2* _
   }
   __shared__ double red[8][2 * K];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // warp trees in the vector's precision (FP64 arithmetic is scarce), CTA sum in FP64
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    double s = warp_sum((double)are[j]);
-    double m = warp_sum((double)aim[j]);
-    if (lane == 0) { red[wid][2 * j] = s; red[wid][2 * j + 1] = m; }
+    const R s = warp_sum(are[j]);
+    const R m = warp_sum(aim[j]);
+    if (lane == 0) { red[wid][2 * j] = (double)s; red[wid][2 * j + 1] = (double)m; }
   }
   __syncthreads();
   if (threadIdx.x < K) {
@@ -156,9 +159,10 @@ __global__ void __launch_bounds__(256) multiaxpy_kernel(T2* __restrict__ w, Ptrs
   }
 }
 
+// Streaming kernels: about 8 CTAs of 256 threads per SM over all right-hand sides.
 static dim3 stream_grid(size_t n, int R) {
   const size_t per = std::max<size_t>(16, (size_t)152 * 8 / (size_t)std::max(R, 1));
-  return dim3((unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, per)), R);
+  return dim3((unsigned)std::max<size_t>(1, std::min<size_t>((n + 1023) / 1024, per)), R);
 }
 
 template <class T2, int K>

@@ -22,5 +22,9 @@ int launch_assemble0(const Geom& g, const void* V64, const void* U64, const void
 // Coarse levels.
 int launch_coarse_apply(int prec, const CGeom& c, const void* M, const void* x, void* out, int nrhs, cudaStream_t s);
 int launch_coarse_export(int prec, const CGeom& c, const void* M, double* out, cudaStream_t s);
+// FP32 operator, FP32 vectors: the stencil fed by bulk asynchronous copies (n2 even, <= 64).
+// err: device flag raised when a bounded wait gives up.
+int launch_coarse_apply_tma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
+                            cudaStream_t s);
 
 }  // namespace sapmg

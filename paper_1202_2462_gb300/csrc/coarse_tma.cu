@@ -1,0 +1,208 @@
+// K5 (FP32 operator): the coarse stencil (D_c x)(a) = sum_d M_d(a) x(a + offset_d)
+// (Sec. 3: D_c couples nearest-neighbour aggregates only) for up to 12
+// right-hand sides, with every 2N x 2N block M_d(a) streamed from HBM once.
+//
+// Each CTA walks its sites and, per site, the 9 blocks (self, +-mu).  One
+// elected thread copies block k+1 into shared memory with a bulk asynchronous
+// copy (cp.async.bulk, completion counted on an mbarrier) while all threads
+// compute with block k (double buffering).  The right-hand sides' neighbour
+// vectors are staged in shared memory; thread (group gq, row i) owns APT
+// accumulators out_r[i] for r = gq*APT .. gq*APT+APT-1.  Every wait on an
+// mbarrier is bounded: when it gives up the kernel raises an error flag that
+// the host turns into MG_ERR_TIMEOUT.
+#include "internal.h"
+#include "coarse.h"
+
+namespace sapmg {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false after kMaxSpins tries.
+constexpr int kMaxSpins = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kMaxSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+}  // namespace
+
+template <int RB, int APT>
+__global__ void __launch_bounds__(256) coarse_apply_tma_kernel(const float2* __restrict__ M,
+                                                               const float2* __restrict__ x,
+                                                               float2* __restrict__ out, CGeom c, int r0,
+                                                               int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int n2 = c.n2;
+  const int tile = n2 * n2;                                   // complex entries per block
+  const uint32_t tile_bytes = (uint32_t)tile * sizeof(float2);
+  float2* buf0 = reinterpret_cast<float2*>(smem);
+  float2* buf1 = buf0 + tile;
+  float2* xs = buf1 + tile;                                   // [RB][n2]
+  const int tid = threadIdx.x;
+  const int gq = tid / n2, i = tid % n2;
+  const bool active = (gq * APT < RB) && (tid < ((RB + APT - 1) / APT) * n2);
+  const size_t fs = (size_t)c.nsites * n2;
+  const float2* xr = x + (size_t)r0 * fs;
+
+  const int nsite_cta = (c.nsites - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int T = 9 * nsite_cta;
+  if (T <= 0) return;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto tile_src = [&](int t) {
+    const int site = (int)blockIdx.x + (t / 9) * (int)gridDim.x;
+    return M + ((size_t)site * 9 + (t % 9)) * tile;
+  };
+  if (tid == 0) {
+    mbar_expect_tx(&bar[0], tile_bytes);
+    bulk_copy_g2s(buf0, tile_src(0), tile_bytes, &bar[0]);
+  }
+  float acc_re[APT], acc_im[APT];
+  int tfail = -1;
+  for (int t = 0; t < T; ++t) {
+    const int d = t % 9;
+    const int site = (int)blockIdx.x + (t / 9) * (int)gridDim.x;
+    if (d == 0) {
+#pragma unroll
+      for (int a = 0; a < APT; ++a) acc_re[a] = acc_im[a] = 0.f;
+    }
+    // prefetch block t+1 into the other buffer (its last readers finished at the
+    // barrier that closed step t-1)
+    if (tid == 0 && t + 1 < T) {
+      uint64_t* b = &bar[(t + 1) & 1];
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(b, tile_bytes);
+      bulk_copy_g2s(((t + 1) & 1) ? buf1 : buf0, tile_src(t + 1), tile_bytes, b);
+    }
+    // stage the neighbour vectors of every right-hand side
+    {
+      int nb = site;
+      if (d > 0) {
+        const int mu = (d - 1) >> 1, step = (d & 1) ? 1 : -1;
+        int stride = 1;
+        for (int m = 0; m < mu; ++m) stride *= c.L[m];
+        const int xc = (site / stride) % c.L[mu];
+        nb = site + (((xc + step + c.L[mu]) % c.L[mu]) - xc) * stride;
+      }
+      for (int e = tid; e < RB * n2; e += blockDim.x) xs[e] = xr[(size_t)(e / n2) * fs + (size_t)nb * n2 + e % n2];
+    }
+    const bool waited = mbar_wait(&bar[t & 1], (uint32_t)((t >> 1) & 1));
+    if (__syncthreads_or(!waited)) {          // uniform decision: every thread leaves together
+      tfail = t;
+      break;
+    }
+    const float2* mt = (t & 1) ? buf1 : buf0;
+    if (active) {
+#pragma unroll 4
+      for (int j = 0; j < n2; ++j) {
+        const float2 mv = mt[j * n2 + i];
+#pragma unroll
+        for (int a = 0; a < APT; ++a) {
+          const int r = gq * APT + a;
+          if (r < RB) {
+            const float2 xv = xs[r * n2 + j];
+            acc_re[a] = fmaf(mv.x, xv.x, fmaf(-mv.y, xv.y, acc_re[a]));
+            acc_im[a] = fmaf(mv.x, xv.y, fmaf(mv.y, xv.x, acc_im[a]));
+          }
+        }
+      }
+    }
+    if (d == 8 && active) {
+#pragma unroll
+      for (int a = 0; a < APT; ++a) {
+        const int r = gq * APT + a;
+        if (r < RB) out[(size_t)(r0 + r) * fs + (size_t)site * n2 + i] = make_float2(acc_re[a], acc_im[a]);
+      }
+    }
+    __syncthreads();
+  }
+  if (tfail >= 0) {
+    // let the copies still in flight (blocks tfail and tfail + 1) land before
+    // the CTA exits; these waits are bounded as well
+    if (tid == 0) {
+      atomicExch(err, 1);
+      mbar_wait(&bar[tfail & 1], (uint32_t)((tfail >> 1) & 1));
+      if (tfail + 1 < T) mbar_wait(&bar[(tfail + 1) & 1], (uint32_t)(((tfail + 1) >> 1) & 1));
+    }
+    __syncthreads();
+  }
+}
+
+template <int RB, int APT>
+static void launch_tma(const CGeom& c, const float2* M, const float2* x, float2* out, int r0, int* err,
+                       cudaStream_t s) {
+  const size_t smem = (size_t)(2 * c.n2 * c.n2 + RB * c.n2) * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(coarse_apply_tma_kernel<RB, APT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (220 * 1024) / (smem + 1024)));
+  const int grid = std::min(c.nsites, 152 * per_sm);
+  coarse_apply_tma_kernel<RB, APT><<<grid, 256, smem, s>>>(M, x, out, c, r0, err); count_launches(1);
+}
+
+// Requires 16-byte aligned blocks (n2 even) and n2 <= 64; the caller routes
+// other shapes to the generic kernel.
+int launch_coarse_apply_tma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
+                            cudaStream_t s) {
+  if (c.n2 % 2 != 0 || c.n2 > 64) return MG_ERR_ARG;
+  const float2* m = (const float2*)M;
+  const float2* xi = (const float2*)x;
+  float2* o = (float2*)out;
+  for (int r0 = 0; r0 < nrhs;) {
+    const int left = nrhs - r0;
+    if (left >= 12) {
+      if (c.n2 <= 42) launch_tma<12, 2>(c, m, xi, o, r0, err, s);
+      else launch_tma<12, 3>(c, m, xi, o, r0, err, s);
+      r0 += 12;
+    } else if (left >= 4) {
+      launch_tma<4, 1>(c, m, xi, o, r0, err, s);
+      r0 += 4;
+    } else {
+      launch_tma<1, 1>(c, m, xi, o, r0, err, s);
+      r0 += 1;
+    }
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+}  // namespace sapmg

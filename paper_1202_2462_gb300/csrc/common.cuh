@@ -64,13 +64,29 @@ template <class R> struct Io<R, float2> {
   static __device__ __forceinline__ Cplx<R> ldc(const float2* p) { float2 v = *p; return cmk<R>((R)v.x, (R)v.y); }
   static __device__ __forceinline__ void st(float2* p, Cplx<R> c) { *p = make_float2((float)c.re, (float)c.im); }
 };
+// Half-precision loads go through 32-bit integer loads and value conversions
+// (no address-taken temporaries, which would end up in local memory under
+// register pressure).
+__device__ __forceinline__ float2 half2_bits_to_float2(unsigned int u) {
+  return make_float2(__half2float(__ushort_as_half((unsigned short)(u & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(u >> 16))));
+}
+__device__ __forceinline__ float2 bf162_bits_to_float2(unsigned int u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
 template <class R> struct Io<R, __half2> {
-  static __device__ __forceinline__ Cplx<R> ld(const __half2* p) { float2 v = __half22float2(__ldg(p)); return cmk<R>((R)v.x, (R)v.y); }
+  static __device__ __forceinline__ Cplx<R> ld(const __half2* p) {
+    float2 v = half2_bits_to_float2(__ldg(reinterpret_cast<const unsigned int*>(p)));
+    return cmk<R>((R)v.x, (R)v.y);
+  }
   static __device__ __forceinline__ Cplx<R> ldc(const __half2* p) { float2 v = __half22float2(*p); return cmk<R>((R)v.x, (R)v.y); }
   static __device__ __forceinline__ void st(__half2* p, Cplx<R> c) { *p = __floats2half2_rn((float)c.re, (float)c.im); }
 };
 template <class R> struct Io<R, __nv_bfloat162> {
-  static __device__ __forceinline__ Cplx<R> ld(const __nv_bfloat162* p) { float2 v = __bfloat1622float2(__ldg(p)); return cmk<R>((R)v.x, (R)v.y); }
+  static __device__ __forceinline__ Cplx<R> ld(const __nv_bfloat162* p) {
+    float2 v = bf162_bits_to_float2(__ldg(reinterpret_cast<const unsigned int*>(p)));
+    return cmk<R>((R)v.x, (R)v.y);
+  }
   static __device__ __forceinline__ Cplx<R> ldc(const __nv_bfloat162* p) { float2 v = __bfloat1622float2(*p); return cmk<R>((R)v.x, (R)v.y); }
   static __device__ __forceinline__ void st(__nv_bfloat162* p, Cplx<R> c) { *p = __floats2bfloat162_rn((float)c.re, (float)c.im); }
 };

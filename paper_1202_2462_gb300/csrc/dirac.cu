@@ -11,7 +11,7 @@
 namespace sapmg {
 
 template <class R, class TS, class TG>
-__global__ void __launch_bounds__(256) dirac_kernel(TS* __restrict__ out, const TS* __restrict__ in,
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 3 : 1)) dirac_kernel(TS* __restrict__ out, const TS* __restrict__ in,
                                                     const TG* __restrict__ U, const TG* __restrict__ A, Geom g,
                                                     int nrhs) {
   // right-hand side fastest in the grid: the CTAs of one block run back to
@@ -21,13 +21,22 @@ __global__ void __launch_bounds__(256) dirac_kernel(TS* __restrict__ out, const 
   const size_t off = (size_t)(blockIdx.x % nrhs) * g.V * 12;
   in += off;
   out += off;
-  Cplx<R> p[12], o[12], acc[12];
-  load_spinor<R>(in, blk, loc, p);
-  clover_apply<R>(A, blk, loc, p, o);
-  hops_global<R>(g, in, U, blk, loc, acc);
+  // acc = -2 A psi + sum of hops, so D psi = -acc / 2
+  Cplx<R> acc[12];
+  {
+    Cplx<R> p[12];
+    load_spinor<R>(in, blk, loc, p);
+    clover_apply<R>(A, blk, loc, p, acc);
+  }
 #pragma unroll
-  for (int c = 0; c < 12; ++c) o[c] = o[c] - (R)0.5 * acc[c];
-  store_spinor<R>(out, blk, loc, o);
+  for (int c = 0; c < 12; ++c) acc[c] = (R)(-2) * acc[c];
+  hops_global_dir<0>(g, in, U, blk, loc, acc);
+  hops_global_dir<1>(g, in, U, blk, loc, acc);
+  hops_global_dir<2>(g, in, U, blk, loc, acc);
+  hops_global_dir<3>(g, in, U, blk, loc, acc);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = (R)(-0.5) * acc[c];
+  store_spinor<R>(out, blk, loc, acc);
 }
 
 template <class R, class TS, class TG>

@@ -6,6 +6,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <string>
 #include <vector>
 #include <atomic>
@@ -114,6 +115,8 @@ struct mg_ctx {
   int prec = P64;    // MG_FP64 or the mixed storage precision of links and clover
   int vt = P64;      // vector type of the cycle (P64 plain, P32 mixed)
   int pv_prec = P64; // storage of the interpolation P (FP16 for both half modes)
+  int coarse_reorth = 0;  // second Gram-Schmidt pass in the coarse GMRES (SAPMG_COARSE_REORTH=1)
+  int generic_coarse = 0; // use the generic coarse stencil kernel (SAPMG_GENERIC_COARSE=1)
   int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
   double m0 = 0, csw = 0;
   std::vector<void*> allocs;
@@ -129,6 +132,7 @@ struct mg_ctx {
   void* io_a = nullptr;                    // canonical <-> blocked staging (FP64, nrhs_max fields)
   void* io_b = nullptr;
   double2* partial = nullptr;
+  int* dev_err = nullptr;                  // raised by kernels whose bounded waits gave up
   // Krylov workspace
   int m = 0;
   void *V = nullptr, *Z = nullptr, *w = nullptr;       // outer (plain: FP64; mixed: FP32 inner)
@@ -181,6 +185,25 @@ static int dot_to(mg_ctx* c, int type, const BVec& b, const void* x, const void*
   return blas_multidot(type, b, v, 1, y, out, ldo, 0, nullptr, c->partial, c->s);
 }
 
+// D_c x on a coarse level: the bulk-copy kernel for an FP32 operator, else the generic one.
+static int coarse_apply(mg_ctx* c, CoarseLevel& L, const void* x, void* out, int R) {
+  ProfScope ps(c->prof, FAM_COARSE, c->s);
+  if (L.store == P32 && c->vt == P32 && L.cg.n2 % 2 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
+    return launch_coarse_apply_tma(L.cg, L.M, x, out, R, c->dev_err, c->s);
+  return launch_coarse_apply(L.store, L.cg, L.M, x, out, R, c->s);
+}
+
+static int check_device_error(mg_ctx* c) {
+  int h = 0;
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  if (h) {
+    SAPMG_CUDA_TRY(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->s));
+    return fail(MG_ERR_TIMEOUT, "a bounded device wait gave up");
+  }
+  return MG_OK;
+}
+
 static Scal32 scal_all(double re, int R) {
   Scal32 s;
   for (int r = 0; r < 32; ++r) s.v[r] = make_double2(r < R ? re : 0.0, 0.0);
@@ -189,8 +212,8 @@ static Scal32 scal_all(double re, int R) {
 
 // Fixed-step GMRES from zero on a coarse level for R right-hand sides at once
 // (Sec. 4: 12 steps on the coarse grid): Arnoldi with classical Gram-Schmidt
-// applied twice, all scalars on the device, one operator application per step
-// serving every right-hand side.
+// (a second pass when coarse_reorth is set), all scalars on the device, one
+// operator application per step serving every right-hand side.
 static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k, int R) {
   const size_t n = L.n();
   const int vt = c->vt;
@@ -201,16 +224,15 @@ static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k, int R) {
   TRY(blas_normalize(vt, bv, L.b, Vj(0), L.beta2, 1, nullptr, 0, c->s));
   std::vector<const void*> vl;
   for (int j = 0; j < k; ++j) {
-    {
-      ProfScope ps(c->prof, FAM_COARSE, c->s);
-      TRY(launch_coarse_apply(L.store, L.cg, L.M, Vj(j), L.w, R, c->s));
-    }
+    TRY(coarse_apply(c, L, Vj(j), L.w, R));
     vl.push_back(Vj(j));
     double2* hcol = L.H + (size_t)j * 33;
     TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
     TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
-    TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 1, L.tmp, c->partial, c->s));
-    TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, c->s));
+    if (c->coarse_reorth) {
+      TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 1, L.tmp, c->partial, c->s));
+      TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, c->s));
+    }
     TRY(dot_to(c, vt, bv, L.w, L.w, L.tmp + 40, 33 * 33));
     TRY(blas_normalize(vt, bv, L.w, Vj(j + 1), L.tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
   }
@@ -408,7 +430,7 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
       // FP64 defect correction around an FP32 flexible GMRES cycle on the normalised residual
       Scal32 a = zero, unit = zero;
       for (int q = 0; q < R; ++q) {
-        if (act[q] > 0) { a.v[q].x = 1.0 / act[q]; unit.v[q].x = 1.0; }
+        if (act[q] > 0) a.v[q].x = 1.0 / act[q];
         inner[q] = act[q] > 0 ? std::max(2e-6, 0.5 * tol[q] / act[q]) : 1.0;
       }
       std::vector<double> unorm(R);
@@ -581,6 +603,9 @@ static int do_setup(mg_ctx* c, const double* U) {
   const size_t eb = complex_bytes(c->vt);
   const int R = p.nrhs_max;
   c->partial = (double2*)c->alloc(sizeof(double2) * kMaxReduceCta * 8);
+  c->dev_err = (int*)c->alloc(sizeof(int));
+  if (!c->dev_err) return fail(MG_ERR_OOM, "workspace");
+  SAPMG_CUDA_TRY(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->s));
   c->zero_f = c->alloc(n * eb);
   c->io_a = c->alloc((size_t)R * n * 16);
   c->io_b = c->alloc((size_t)R * n * 16);
@@ -661,6 +686,8 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   c->vt = p->precision == MG_FP64 ? P64 : P32;
   c->pv_prec = p->precision == MG_BF16 ? P16 : p->precision;
   c->dc_prec = p->precision == MG_FP64 ? P64 : P32;
+  c->coarse_reorth = std::getenv("SAPMG_COARSE_REORTH") ? std::atoi(std::getenv("SAPMG_COARSE_REORTH")) : 0;
+  c->generic_coarse = std::getenv("SAPMG_GENERIC_COARSE") ? std::atoi(std::getenv("SAPMG_GENERIC_COARSE")) : 0;
   c->m0 = m0;
   c->csw = c_sw;
   const int rc = do_setup(c, U);
@@ -727,7 +754,7 @@ int mg_solve(mg_ctx* c, const double* b, double* z, int nrhs, mg_solve_info* inf
     rs_sum += rs;
     worst = std::max(worst, rel);
   }
-  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  TRY(check_device_error(c));
   if (info) {
     info->iterations = it_sum;
     info->restarts = rs_sum;
@@ -798,12 +825,16 @@ int mg_prolong(mg_ctx* c, int level, const void* in, void* out, int prec) {
 }
 
 int mg_coarse_apply(mg_ctx* c, int level, const void* in, void* out, int prec) {
-  if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
+  return mg_coarse_apply_batch(c, level, in, out, prec, 1);
+}
+
+int mg_coarse_apply_batch(mg_ctx* c, int level, const void* in, void* out, int prec, int nrhs) {
+  if (!c || !in || !out || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
   prec &= 0xff;
   if (level != 1 || !c->c1.M) return fail(MG_ERR_STATE, "no coarse operator on that level");
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
-  ProfScope ps(c->prof, FAM_COARSE, c->s);
-  return launch_coarse_apply(c->c1.store, c->c1.cg, c->c1.M, in, out, 1, c->s);
+  TRY(coarse_apply(c, c->c1, in, out, nrhs));
+  return check_device_error(c);
 }
 
 int mg_coarse_solve(mg_ctx* c, int level, const void* in, void* out, int prec) {

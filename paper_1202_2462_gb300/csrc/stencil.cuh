@@ -27,6 +27,24 @@ __device__ __forceinline__ void spin_project(const Cplx<R> (&p)[12], Cplx<R> (&h
   }
 }
 
+// The same projection reading the four-spinor component by component from a
+// loader (global or shared memory), so that only the half spinor is live.
+template <int MU, int S, class R, class LD>
+__device__ __forceinline__ void spin_project_ld(LD ld, Cplx<R> (&h)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cplx<R> l0 = ld(6 + c), l1 = ld(9 + c);
+    Cplx<R> x0, x1;
+    if (MU == 0) { x0 = mul_mi(l1); x1 = mul_mi(l0); }
+    else if (MU == 1) { x0 = cmk(-l1.re, -l1.im); x1 = l0; }
+    else if (MU == 2) { x0 = mul_mi(l0); x1 = mul_i(l1); }
+    else { x0 = l0; x1 = l1; }
+    const Cplx<R> u0 = ld(c), u1 = ld(3 + c);
+    if (S > 0) { h[c] = u0 + x0; h[3 + c] = u1 + x1; }
+    else { h[c] = u0 - x0; h[3 + c] = u1 - x1; }
+  }
+}
+
 // acc_u += g, acc_l += S * X_MU^dagger g
 template <int MU, int S, class R>
 __device__ __forceinline__ void spin_reconstruct_add(const Cplx<R> (&g)[6], Cplx<R> (&acc)[12]) {
@@ -99,33 +117,30 @@ __device__ __forceinline__ int offdiag_index(int i, int j) {  // i < j, 0..14
   return i * 6 - (i * (i + 1)) / 2 + (j - i - 1);
 }
 
-// out = A(x) psi: two Hermitian 6x6 chiral blocks
+// out = A(x) psi: two Hermitian 6x6 chiral blocks.  Each stored off-diagonal
+// entry a_ij (i < j) is loaded once and used for both a_ij psi_j and
+// conj(a_ij) psi_i, so only one entry is live at a time.
 template <class R, class TG>
 __device__ __forceinline__ void clover_apply(const TG* __restrict__ A, int blk, int loc, const Cplx<R> (&p)[12],
                                              Cplx<R> (&out)[12]) {
 #pragma unroll
   for (int chi = 0; chi < 2; ++chi) {
     const TG* a = A + ((size_t)(blk * 36 + chi * 18)) * 256 + loc;
-    R d[6];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      Cplx<R> v = Io<R, TG>::ld(a + q * 256);
-      d[2 * q] = v.re;
-      d[2 * q + 1] = v.im;
+      const Cplx<R> d = Io<R, TG>::ld(a + q * 256);
+      out[chi * 6 + 2 * q] = d.re * p[chi * 6 + 2 * q];
+      out[chi * 6 + 2 * q + 1] = d.im * p[chi * 6 + 2 * q + 1];
     }
-    Cplx<R> o[15];
+    int q = 3;
 #pragma unroll
-    for (int q = 0; q < 15; ++q) o[q] = Io<R, TG>::ld(a + (3 + q) * 256);
+    for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      Cplx<R> acc = d[i] * p[chi * 6 + i];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        if (j > i) cfma(acc, o[offdiag_index(i, j)], p[chi * 6 + j]);
-        if (j < i) cfma_conj(acc, o[offdiag_index(j, i)], p[chi * 6 + j]);
+      for (int j = i + 1; j < 6; ++j, ++q) {
+        const Cplx<R> o = Io<R, TG>::ld(a + q * 256);
+        cfma(out[chi * 6 + i], o, p[chi * 6 + j]);
+        cfma_conj(out[chi * 6 + j], o, p[chi * 6 + i]);
       }
-      out[chi * 6 + i] = acc;
-    }
   }
 }
 
@@ -156,13 +171,23 @@ template <int MU, class R, class TS, class TG>
 __device__ __forceinline__ void hops_global_dir(const Geom& g, const TS* __restrict__ f, const TG* __restrict__ U,
                                                 int blk, int loc, Cplx<R> (&acc)[12]) {
   int nb, nl;
-  Cplx<R> pn[12];
+  Cplx<R> h[6], gg[6], u[9];
   neighbour(g, blk, loc, MU, 1, nb, nl);
-  load_spinor<R>(f, nb, nl, pn);
-  hop_fwd<MU>(U, blk, loc, pn, acc);
+  {
+    const TS* q = f + (size_t)nb * 12 * 256 + nl;
+    spin_project_ld<MU, -1, R>([&](int c) { return Io<R, TS>::ldc(q + c * 256); }, h);
+  }
+  load_link<R>(U, blk, MU, loc, u);
+  su3_mul(u, h, gg);
+  spin_reconstruct_add<MU, -1>(gg, acc);
   neighbour(g, blk, loc, MU, -1, nb, nl);
-  load_spinor<R>(f, nb, nl, pn);
-  hop_bwd<MU>(U, nb, nl, pn, acc);
+  {
+    const TS* q = f + (size_t)nb * 12 * 256 + nl;
+    spin_project_ld<MU, 1, R>([&](int c) { return Io<R, TS>::ldc(q + c * 256); }, h);
+  }
+  load_link<R>(U, nb, MU, nl, u);
+  su3_dag_mul(u, h, gg);
+  spin_reconstruct_add<MU, 1>(gg, acc);
 }
 
 template <class R, class TS, class TG>

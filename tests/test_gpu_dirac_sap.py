@@ -128,3 +128,20 @@ def test_sap_zero_rhs_block_stays_finite():
     out = host(z)
     s.close()
     assert np.all(out == 0)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_sap_multi_rhs_matches_single(prec):
+    """Three right-hand sides in one launch equal three separate sweeps."""
+    torch = torch_cuda()
+    dims = (8, 8, 8, 16)
+    u = synth.random_gauge_field(dims, 0.5, 27)
+    s = _solver(torch, u, 1.0, 0.0, False, precision=prec, nrhs_max=3)
+    b = dev(torch, synth.random_spinor(dims, 28, nvec=3), torch.complex64)
+    z = torch.zeros_like(b)
+    s.smooth(b, z, 2)
+    for k in range(3):
+        zk = torch.zeros_like(b[k:k + 1])
+        s.smooth(b[k:k + 1].contiguous(), zk, 2)
+        assert torch.equal(zk[0], z[k])
+    s.close()
