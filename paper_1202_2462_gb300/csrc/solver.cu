@@ -428,7 +428,7 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
       TRY(fgmres_cycle(c, P64, P64, R, c->r64, act, c->x64, tol, c->p.maxiter - iters, done, est));
     } else {
       // FP64 defect correction around an FP32 flexible GMRES cycle on the normalised residual
-      Scal32 a = zero, unit = zero;
+      Scal32 a = zero;
       for (int q = 0; q < R; ++q) {
         if (act[q] > 0) a.v[q].x = 1.0 / act[q];
         inner[q] = act[q] > 0 ? std::max(2e-6, 0.5 * tol[q] / act[q]) : 1.0;
