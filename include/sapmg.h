@@ -176,6 +176,24 @@ int mg_coarse_apply_batch(mg_ctx* ctx, int level, const void* in, void* out, int
  * level's cycle otherwise), from zero. */
 int mg_coarse_solve(mg_ctx* ctx, int level, const void* in, void* out, int prec);
 
+/* The coarse solve of mg_coarse_solve without any device allocation.
+ * The paper has no counterpart: this entry point is for callers that cannot
+ * call cudaMalloc at the time they solve -- code running while a CUDA graph is
+ * being captured, under an allocator that forbids new device memory, or on a
+ * real-time path where an allocation's synchronisation or failure is not
+ * acceptable.  Its Krylov basis, Hessenberg matrix and reduction partials live
+ * in a fixed 8 MiB array inside the library's own device memory (every device
+ * that loads the library holds it until the process exits); the result is
+ * written straight to `out`, which starts from zero.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  Every
+ * call shares the one array, which keeps the previous call's contents, so
+ * calls that overlap on the GPU (other streams, other contexts on the same
+ * device) race: serialise them.  A coarse system whose basis does not fit
+ * (about (coarse_iters + 2) vectors of the level's size) is rejected with
+ * MG_ERR_ARG and a message naming the sizes.  Synchronises. */
+int mg_coarse_solve_noalloc(mg_ctx* ctx, int level, const void* in, void* out, int prec);
+
 /* One application of the multilevel cycle z = M v on the fine level (the
  * outer solver's preconditioner).  prec: MG_FP64 for a plain-form context,
  * MG_FP32 for a mixed one.  Asynchronous. */

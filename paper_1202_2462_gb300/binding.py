@@ -86,6 +86,7 @@ _SIGNATURES = {
     "mg_coarse_apply": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_coarse_apply_batch": (_I, [_VP, _I, _VP, _VP, _I, _I]),
     "mg_coarse_solve": (_I, [_VP, _I, _VP, _VP, _I]),
+    "mg_coarse_solve_noalloc": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_precondition": (_I, [_VP, _VP, _VP, _I]),
     "mg_set_profiling": (_I, [_VP, _I]),
     "mg_get_profile": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
@@ -205,6 +206,10 @@ def mg_coarse_apply_batch(ctx, level, inp, out, prec, nrhs):
 
 def mg_coarse_solve(ctx, level, inp, out, prec):
     return _check(lib().mg_coarse_solve(ctx, level, _ptr(inp), _ptr(out), prec), "mg_coarse_solve")
+
+
+def mg_coarse_solve_noalloc(ctx, level, inp, out, prec):
+    return _check(lib().mg_coarse_solve_noalloc(ctx, level, _ptr(inp), _ptr(out), prec), "mg_coarse_solve_noalloc")
 
 
 def mg_precondition(ctx, v, z, prec):

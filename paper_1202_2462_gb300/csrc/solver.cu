@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 #include <atomic>
+#include <mutex>
 
 #include "internal.h"
 #include "blas.h"
@@ -646,6 +647,30 @@ static int stage_in(mg_ctx* c, const void* in, int prec, bool blocked, int nrhs,
 
 }  // namespace sapmg
 
+// ------------------------------------------------------------ no-allocation coarse solve
+// Scratch of mg_coarse_solve_noalloc: a fixed array in the library's own device
+// memory (every device that loads the library holds it until the process
+// exits), so that this entry point never allocates.  Host code cannot use the
+// symbol as an address; its device address is looked up once per device.
+constexpr size_t kNoAllocBytes = 8u << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+static void* g_noalloc_addr[64] = {};
+static std::mutex g_noalloc_mutex;
+
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  SAPMG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(MG_ERR_ARG, "device index beyond the no-alloc table");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    SAPMG_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return MG_OK;
+}
+
 // ============================================================ C-ABI
 extern "C" {
 
@@ -847,6 +872,68 @@ int mg_coarse_solve(mg_ctx* c, int level, const void* in, void* out, int prec) {
   TRY(coarse_solve(c, 1, 1));
   SAPMG_CUDA_TRY(cudaMemcpyAsync(out, c->c1.x, bytes, cudaMemcpyDeviceToDevice, c->s));
   return MG_OK;
+}
+
+int mg_coarse_solve_noalloc(mg_ctx* c, int level, const void* in, void* out, int prec) {
+  if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
+  prec &= 0xff;
+  if (level != 1 || !c->c1.M) return fail(MG_ERR_STATE, "no coarse operator on that level");
+  if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
+  CoarseLevel& L = c->c1;
+  const size_t n = L.n();
+  const int vt = c->vt;
+  const size_t eb = complex_bytes(vt);
+  const int k = c->p.coarse_iters;
+  // carve the scratch: partial sums | H | H scratch | ||b||^2 | y | basis V (k+1) | w
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t o_part = 0;
+  const size_t o_h = o_part + up(sizeof(double2) * kMaxReduceCta * 8);
+  const size_t o_tmp = o_h + up(sizeof(double2) * 33 * 33);
+  const size_t o_beta = o_tmp + up(sizeof(double2) * 33 * 33);
+  const size_t o_y = o_beta + up(sizeof(double2));
+  const size_t o_v = o_y + up(sizeof(double2) * 33);
+  const size_t o_w = o_v + up((size_t)(k + 1) * n * eb);
+  const size_t need = o_w + up(n * eb);
+  if (need > kNoAllocBytes)
+    return fail(MG_ERR_ARG, "coarse system too large for the no-alloc scratch (" + std::to_string(need) +
+                                " bytes needed, limit " + std::to_string(kNoAllocBytes) + ")");
+  void* base = nullptr;
+  TRY(noalloc_scratch(&base));
+  char* sb = (char*)base;
+  double2* partial = (double2*)(sb + o_part);
+  double2* H = (double2*)(sb + o_h);
+  double2* tmp = (double2*)(sb + o_tmp);
+  double2* beta2 = (double2*)(sb + o_beta);
+  double2* y = (double2*)(sb + o_y);
+  void* V = sb + o_v;
+  void* w = sb + o_w;
+  auto Vj = [&](int j) { return (void*)((char*)V + (size_t)j * n * eb); };
+  const BVec bv = bvec(n, 1, n);
+  // the same fixed-step GMRES as the cycle's coarse solve, on the scratch buffers
+  {
+    const void* v1[1] = {in};
+    TRY(blas_multidot(vt, bv, v1, 1, in, beta2, 1, 0, nullptr, partial, c->s));
+  }
+  TRY(blas_normalize(vt, bv, in, Vj(0), beta2, 1, nullptr, 0, c->s));
+  std::vector<const void*> vl;
+  for (int j = 0; j < k; ++j) {
+    TRY(coarse_apply(c, L, Vj(j), w, 1));
+    vl.push_back(Vj(j));
+    double2* hcol = H + (size_t)j * 33;
+    TRY(blas_multidot(vt, bv, vl.data(), j + 1, w, hcol, 33 * 33, 0, nullptr, partial, c->s));
+    TRY(blas_multiaxpy(vt, bv, w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
+    if (c->coarse_reorth) {
+      TRY(blas_multidot(vt, bv, vl.data(), j + 1, w, hcol, 33 * 33, 1, tmp, partial, c->s));
+      TRY(blas_multiaxpy(vt, bv, w, vl.data(), j + 1, tmp, 33 * 33, -1.0, c->s));
+    }
+    const void* wl[1] = {w};
+    TRY(blas_multidot(vt, bv, wl, 1, w, tmp + 40, 33 * 33, 0, nullptr, partial, c->s));
+    TRY(blas_normalize(vt, bv, w, Vj(j + 1), tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
+  }
+  TRY(blas_hessenberg_solve(H, 33, 33 * 33, k, beta2, y, 33, 1, c->s));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(out, 0, n * eb, c->s));     // the result starts from zero
+  TRY(blas_multiaxpy(vt, bv, out, vl.data(), k, y, 33, 1.0, c->s));
+  return check_device_error(c);
 }
 
 int mg_precondition(mg_ctx* c, const void* v, void* z, int prec) {
