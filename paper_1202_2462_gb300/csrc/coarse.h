@@ -11,6 +11,26 @@ struct CGeom {
   int n2;
 };
 
+// A decomposition of a coarse lattice into boxes of b[0] x .. x b[3] sites.
+struct Box4 {
+  int b[4];
+  int nb[4];
+  int nboxes;
+  int sites;
+};
+inline Box4 make_box(const CGeom& c, const int b[4]) {
+  Box4 x;
+  x.nboxes = 1;
+  x.sites = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    x.b[mu] = b[mu];
+    x.nb[mu] = c.L[mu] / b[mu];
+    x.nboxes *= x.nb[mu];
+    x.sites *= b[mu];
+  }
+  return x;
+}
+
 // Level 0 -> 1 (4^4 aggregates = the fine blocks).
 int launch_transfer0(bool restrict_, int prec, const Geom& g, const void* in, void* out, const void* Pv, int N,
                      int nrhs, cudaStream_t s);
@@ -26,5 +46,14 @@ int launch_coarse_export(int prec, const CGeom& c, const void* M, double* out, c
 // err: device flag raised when a bounded wait gives up.
 int launch_coarse_apply_tma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
                             cudaStream_t s);
+
+// Intermediate level of a three-level hierarchy (coarse1.cu).
+int launch_coarse_sap(int prec, const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
+                      int n_mr, int nrhs, cudaStream_t s);
+int launch_transfer1(bool restrict_, int prec, const CGeom& c, const Box4& ag, const void* in, void* out,
+                     const void* W, int N1, int nrhs, cudaStream_t s);
+int launch_block_gs1(const CGeom& c, const Box4& ag, void* W64, int N1, cudaStream_t s);
+int launch_assemble1(const CGeom& c, const CGeom& c2, const Box4& ag, const void* W64, const void* M1_64, void* M2_64,
+                     int N1, cudaStream_t s);
 
 }  // namespace sapmg

@@ -126,8 +126,18 @@ struct mg_ctx {
   void *Us = nullptr, *As = nullptr;       // smoother precision (== U64/A64 or U32/A32 or half)
   int N0 = 0;
   void* V64 = nullptr;                     // locally orthonormal test vectors, FP64 vector-major
+  void* Vs64 = nullptr;                    // set-up only: the smoothed vectors before local orthonormalisation
   void* Pv = nullptr;                      // P in cycle storage, block-major
   CoarseLevel c1;
+  // three levels: level-1 Schwarz boxes, level-2 aggregates, level-1 vectors, level 2
+  Box4 sap1, agg1;
+  int N1 = 0;
+  void* W64 = nullptr;                     // level-1 locally orthonormal vectors, FP64 [N1][site][n2]
+  void* W = nullptr;                       // the same in the cycle's vector type
+  CoarseLevel c2;
+  // level-1 fixed-step flexible GMRES workspace
+  void *f1V = nullptr, *f1Z = nullptr, *f1w = nullptr;
+  double2 *f1H = nullptr, *f1tmp = nullptr, *f1beta2 = nullptr, *f1y = nullptr;
   // fine workspace
   void* zero_f = nullptr;                  // a zero fine field (cycle type)
   void* io_a = nullptr;                    // canonical <-> blocked staging (FP64, nrhs_max fields)
@@ -144,6 +154,10 @@ struct mg_ctx {
   double2* hh = nullptr;                   // pinned host mirror
   Prof prof;
 
+  void release(void* ptr) {
+    for (auto& q : allocs)
+      if (q == ptr) { cudaFree(q); q = nullptr; }
+  }
   void* alloc(size_t bytes) {
     void* ptr = nullptr;
     if (bytes == 0) bytes = 16;
@@ -155,7 +169,8 @@ struct mg_ctx {
     return ptr;
   }
   ~mg_ctx() {
-    for (void* q : allocs) cudaFree(q);
+    for (void* q : allocs)
+      if (q) cudaFree(q);
     if (hh) cudaFreeHost(hh);
   }
   size_t fine_n() const { return (size_t)g.V * 12; }
@@ -243,9 +258,74 @@ static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k, int R) {
   return MG_OK;
 }
 
+static int cycle1(mg_ctx* c, const void* v, void* z, int R);
+
+// Fixed-step flexible GMRES from zero on level 1 of a three-level hierarchy,
+// right-preconditioned by the level-1 cycle (the two-level method applied to
+// the coarse equation, Sec. 3): b = c1.b -> x = c1.x for R systems.
+static int fgmres_fixed1(mg_ctx* c, int k, int R) {
+  CoarseLevel& L = c->c1;
+  const size_t n = L.n();
+  const int vt = c->vt;
+  const size_t eb = complex_bytes(vt);
+  const BVec bv = bvec(n, R, n);
+  auto Vj = [&](int j) { return (void*)((char*)c->f1V + (size_t)j * R * n * eb); };
+  auto Zj = [&](int j) { return (void*)((char*)c->f1Z + (size_t)j * R * n * eb); };
+  TRY(dot_to(c, vt, bv, L.b, L.b, c->f1beta2, 1));
+  TRY(blas_normalize(vt, bv, L.b, Vj(0), c->f1beta2, 1, nullptr, 0, c->s));
+  std::vector<const void*> vl, zl;
+  for (int j = 0; j < k; ++j) {
+    TRY(cycle1(c, Vj(j), Zj(j), R));
+    TRY(coarse_apply(c, L, Zj(j), c->f1w, R));
+    vl.push_back(Vj(j));
+    zl.push_back(Zj(j));
+    double2* hcol = c->f1H + (size_t)j * 33;
+    TRY(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
+    TRY(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
+    if (c->coarse_reorth) {
+      TRY(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 1, c->f1tmp, c->partial, c->s));
+      TRY(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, c->f1tmp, 33 * 33, -1.0, c->s));
+    }
+    TRY(dot_to(c, vt, bv, c->f1w, c->f1w, c->f1tmp + 40, 33 * 33));
+    TRY(blas_normalize(vt, bv, c->f1w, Vj(j + 1), c->f1tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
+  }
+  TRY(blas_hessenberg_solve(c->f1H, 33, 33 * 33, k, c->f1beta2, c->f1y, 33, R, c->s));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, (size_t)R * n * eb, c->s));
+  TRY(blas_multiaxpy(vt, bv, L.x, zl.data(), k, c->f1y, 33, 1.0, c->s));
+  return MG_OK;
+}
+
 static int coarse_solve(mg_ctx* c, int level, int R) {
-  if (level != 1) return fail(MG_ERR_ARG, "coarse level out of range");
-  return coarse_gmres(c, c->c1, c->p.coarse_iters, R);
+  if (level == 1 && c->p.n_levels == 2) return coarse_gmres(c, c->c1, c->p.coarse_iters, R);
+  if (level == 1 && c->p.n_levels == 3) return fgmres_fixed1(c, c->p.inner_iters, R);
+  if (level == 2 && c->p.n_levels == 3) return coarse_gmres(c, c->c2, c->p.coarse_iters, R);
+  return fail(MG_ERR_ARG, "coarse level out of range");
+}
+
+// Schwarz sweeps on level 1 (boxes of coarse sites, red-black as on the fine level).
+static int smoother_sweeps1(mg_ctx* c, const void* b, void* z, int n_sweeps, int R) {
+  for (int it = 0; it < n_sweeps; ++it)
+    for (int col = 0; col < 2; ++col) {
+      ProfScope ps(c->prof, FAM_SAP, c->s);
+      TRY(launch_coarse_sap(c->c1.store == P64 ? P64 : P32, c->c1.cg, c->sap1, c->c1.M, z, b, col, c->p.n_mr, R,
+                            c->s));
+    }
+  return MG_OK;
+}
+
+// The level-1 cycle z = M1 v: restrict to level 2, fixed-step GMRES there,
+// interpolate, nu_post Schwarz sweeps on level 1.
+static int cycle1(mg_ctx* c, const void* v, void* z, int R) {
+  {
+    ProfScope ps(c->prof, FAM_RESTRICT, c->s);
+    TRY(launch_transfer1(true, c->vt, c->c1.cg, c->agg1, v, c->c2.b, c->W, c->N1, R, c->s));
+  }
+  TRY(coarse_gmres(c, c->c2, c->p.coarse_iters, R));
+  {
+    ProfScope ps(c->prof, FAM_PROLONG, c->s);
+    TRY(launch_transfer1(false, c->vt, c->c1.cg, c->agg1, c->c2.x, z, c->W, c->N1, R, c->s));
+  }
+  return smoother_sweeps1(c, v, z, c->p.nu_post, R);
 }
 
 // The multilevel cycle z = M v on the fine level for R right-hand sides (cycle vector type).
@@ -472,8 +552,7 @@ static int check_finite(mg_ctx* c, const double* x, size_t n_doubles) {
 
 // Global orthonormalisation of the N set-up vectors (FP64): classical
 // Gram-Schmidt against the previous vectors, applied twice, then normalise.
-static int orthonormalise(mg_ctx* c, void* V, int N) {
-  const size_t n = c->fine_n();
+static int orthonormalise(mg_ctx* c, void* V, int N, size_t n) {
   const BVec one = bvec(n, 1, n);
   auto Vk = [&](int k) { return (void*)((char*)V + (size_t)k * n * 16); };
   std::vector<const void*> vl;
@@ -513,7 +592,12 @@ static int setup_level0(mg_ctx* c) {
         TRY(blas_axpby2(P32, one, c->io_b, n, P64, zero, vk, n, n, 1, c->s));
       }
     }
-    TRY(orthonormalise(c, c->V64, N));
+    TRY(orthonormalise(c, c->V64, N, n));
+  }
+  if (p.n_levels == 3) {                   // the smoothed vectors start level 1 (restricted below)
+    c->Vs64 = c->alloc((size_t)N * n * 16);
+    if (!c->Vs64) return fail(MG_ERR_OOM, "set-up vectors");
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->Vs64, c->V64, (size_t)N * n * 16, cudaMemcpyDeviceToDevice, c->s));
   }
   TRY(launch_block_gs0(c->g, c->V64, N, c->s));
   c->Pv = c->alloc((size_t)N * n * complex_bytes(c->pv_prec));
@@ -539,6 +623,96 @@ static int setup_level0(mg_ctx* c) {
   return MG_OK;
 }
 
+// Bootstrap part 1 on level 1 (Sec. 3: the procedure continues recursively on
+// the coarser grid): the smoothed fine vectors restricted with P^dagger start
+// N1 level-1 vectors; setup_iters Schwarz sweeps of the level-1 smoother on
+// D_c x = 0 each, kept orthonormal; local orthonormalisation on the level-2
+// aggregates; D_c2 = P1^dagger D_c1 P1.
+static int setup_level1(mg_ctx* c) {
+  const mg_params& p = c->p;
+  const size_t nf = c->fine_n();
+  CoarseLevel& L1 = c->c1;
+  const size_t n1 = L1.n();
+  const int N0 = c->N0, N1 = c->N1;
+  c->sap1 = make_box(L1.cg, p.sap_block2);
+  c->agg1 = make_box(L1.cg, p.agg2);
+  // FP64 P0 (block-major) to restrict the smoothed fine vectors
+  void* p0buf = c->alloc((size_t)N0 * nf * 16);
+  c->W64 = c->alloc((size_t)N1 * n1 * 16);
+  if (!p0buf || !c->W64) return fail(MG_ERR_OOM, "level-1 vectors");
+  TRY(launch_store_p0(P64, c->g, c->V64, p0buf, N0, c->s));
+  for (int k = 0; k < N1; ++k)
+    TRY(launch_transfer0(true, P64, c->g, (char*)c->Vs64 + (size_t)k * nf * 16, (char*)c->W64 + (size_t)k * n1 * 16,
+                         p0buf, N0, 1, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  c->release(p0buf);
+  c->release(c->Vs64);
+  c->Vs64 = nullptr;
+  // level-1 smoothing of the vectors (S^nu on D_c1 x = 0), kept orthonormal
+  void* zero1 = c->alloc(n1 * 16);
+  void* t32 = c->alloc(n1 * 8);
+  if (!zero1 || !t32) return fail(MG_ERR_OOM, "level-1 set-up");
+  SAPMG_CUDA_TRY(cudaMemsetAsync(zero1, 0, n1 * 16, c->s));
+  const Scal32 one = scal_all(1.0, 1), zero = scal_all(0.0, 1);
+  for (int it = 0; it < p.setup_iters; ++it) {
+    for (int k = 0; k < N1; ++k) {
+      void* wk = (char*)c->W64 + (size_t)k * n1 * 16;
+      if (c->vt == P64) {
+        TRY(smoother_sweeps1(c, zero1, wk, 1, 1));
+      } else {
+        TRY(blas_axpby2(P64, one, wk, n1, P32, zero, t32, n1, n1, 1, c->s));
+        TRY(smoother_sweeps1(c, zero1, t32, 1, 1));
+        TRY(blas_axpby2(P32, one, t32, n1, P64, zero, wk, n1, n1, 1, c->s));
+      }
+    }
+    TRY(orthonormalise(c, c->W64, N1, n1));
+  }
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  c->release(zero1);
+  c->release(t32);
+  TRY(launch_block_gs1(L1.cg, c->agg1, c->W64, N1, c->s));
+  if (c->vt == P64) {
+    c->W = c->W64;
+  } else {
+    c->W = c->alloc((size_t)N1 * n1 * 8);
+    if (!c->W) return fail(MG_ERR_OOM, "level-1 vectors");
+    TRY(launch_convert(P64, c->W64, P32, c->W, (size_t)N1 * n1, c->s));
+  }
+  // level 2
+  CoarseLevel& L2 = c->c2;
+  for (int mu = 0; mu < 4; ++mu) L2.cg.L[mu] = c->agg1.nb[mu];
+  L2.cg.nsites = c->agg1.nboxes;
+  L2.cg.n2 = 2 * N1;
+  const size_t msz = (size_t)L2.cg.nsites * 9 * L2.cg.n2 * L2.cg.n2;
+  L2.M64 = c->alloc(msz * 16);
+  if (!L2.M64) return fail(MG_ERR_OOM, "level-2 operator");
+  TRY(launch_assemble1(L1.cg, L2.cg, c->agg1, c->W64, L1.M64, L2.M64, N1, c->s));
+  L2.store = c->dc_prec;
+  if (c->dc_prec == P64) {
+    L2.M = L2.M64;
+  } else {
+    L2.M = c->alloc(msz * complex_bytes(c->dc_prec));
+    if (!L2.M) return fail(MG_ERR_OOM, "level-2 operator");
+    TRY(launch_convert(P64, L2.M64, c->dc_prec, L2.M, msz, c->s));
+  }
+  return MG_OK;
+}
+
+static int alloc_fgmres1_ws(mg_ctx* c, int k, int R) {
+  const size_t n = c->c1.n(), eb = complex_bytes(c->vt);
+  c->f1V = c->alloc((size_t)(k + 1) * R * n * eb);
+  c->f1Z = c->alloc((size_t)k * R * n * eb);
+  c->f1w = c->alloc((size_t)R * n * eb);
+  c->f1H = (double2*)c->alloc(sizeof(double2) * 33 * 33 * R);
+  c->f1tmp = (double2*)c->alloc(sizeof(double2) * 33 * 33 * R);
+  c->f1beta2 = (double2*)c->alloc(sizeof(double2) * R);
+  c->f1y = (double2*)c->alloc(sizeof(double2) * 33 * R);
+  if (!c->f1V || !c->f1Z || !c->f1w || !c->f1H || !c->f1tmp || !c->f1beta2 || !c->f1y)
+    return fail(MG_ERR_OOM, "level-1 workspace");
+  SAPMG_CUDA_TRY(cudaMemsetAsync(c->f1H, 0, sizeof(double2) * 33 * 33 * R, c->s));
+  return MG_OK;
+}
+
 static int alloc_coarse_ws(mg_ctx* c, CoarseLevel& L, int kmax, int R) {
   const size_t n = L.n(), eb = complex_bytes(c->vt);
   L.V = c->alloc((size_t)(kmax + 1) * R * n * eb);
@@ -558,7 +732,23 @@ static int validate(const mg_params* p) {
   for (int mu = 0; mu < 4; ++mu)
     if (p->dims[mu] <= 0 || p->dims[mu] % 8 != 0)
       return fail(MG_ERR_ARG, "every lattice dim must be a positive multiple of 8 (even number of 4^4 blocks)");
-  if (p->n_levels < 1 || p->n_levels > 2) return fail(MG_ERR_ARG, "n_levels must be 1 or 2");
+  if (p->n_levels < 1 || p->n_levels > 3) return fail(MG_ERR_ARG, "n_levels must be 1, 2 or 3");
+  if (p->n_levels == 3) {
+    if (p->n_vec[1] < 1 || p->n_vec[1] > p->n_vec[0]) return fail(MG_ERR_ARG, "n_vec[1] must be in 1..n_vec[0]");
+    if (p->inner_iters < 1 || p->inner_iters > 32) return fail(MG_ERR_ARG, "inner_iters must be in 1..32");
+    int sb = 1, ab = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+      const int l1 = p->dims[mu] / 4;
+      if (p->sap_block2[mu] < 1 || l1 % p->sap_block2[mu] != 0 || (l1 / p->sap_block2[mu]) % 2 != 0)
+        return fail(MG_ERR_ARG, "level-1 Schwarz blocks must cut the level-1 lattice into an even number per dim");
+      if (p->agg2[mu] < 1 || l1 % p->agg2[mu] != 0)
+        return fail(MG_ERR_ARG, "level-2 aggregates must divide the level-1 lattice");
+      sb *= p->sap_block2[mu];
+      ab *= p->agg2[mu];
+    }
+    if (sb * 2 * p->n_vec[0] > 1024 || ab * 2 * p->n_vec[0] > 1024)
+      return fail(MG_ERR_ARG, "level-1 block or aggregate too large (sites x 2N must be <= 1024)");
+  }
   if (p->n_levels >= 2 && (p->n_vec[0] < 1 || p->n_vec[0] > 32)) return fail(MG_ERR_ARG, "n_vec[0] must be in 1..32");
   if (p->setup_iters < 0 || p->n_mr < 0 || p->nu_post < 0) return fail(MG_ERR_ARG, "negative iteration count");
   if (p->coarse_iters < 1 || p->coarse_iters > 32) return fail(MG_ERR_ARG, "coarse_iters must be in 1..32");
@@ -631,6 +821,12 @@ static int do_setup(mg_ctx* c, const double* U) {
     c->N0 = p.n_vec[0];
     TRY(setup_level0(c));
     TRY(alloc_coarse_ws(c, c->c1, p.coarse_iters, R));
+  }
+  if (p.n_levels == 3) {
+    c->N1 = p.n_vec[1];
+    TRY(setup_level1(c));
+    TRY(alloc_coarse_ws(c, c->c2, p.coarse_iters, R));
+    TRY(alloc_fgmres1_ws(c, p.inner_iters, R));
   }
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
   return MG_OK;
@@ -809,22 +1005,37 @@ int mg_clover_export(mg_ctx* c, double* out) {
 
 int mg_get_vectors(mg_ctx* c, int level, double* out) {
   if (!c || !out) return fail(MG_ERR_ARG, "bad argument");
-  if (level != 0 || !c->V64) return fail(MG_ERR_STATE, "no test vectors on that level");
-  return launch_unpack_spinor(P64, c->V64, P64, out, c->g, c->N0, c->s);
+  if (level == 0 && c->V64) return launch_unpack_spinor(P64, c->V64, P64, out, c->g, c->N0, c->s);
+  if (level == 1 && c->W64) {
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(out, c->W64, (size_t)c->N1 * c->c1.n() * 16, cudaMemcpyDeviceToDevice, c->s));
+    return MG_OK;
+  }
+  return fail(MG_ERR_STATE, "no test vectors on that level");
+}
+
+static CoarseLevel* coarse_level(mg_ctx* c, int level) {
+  if (level == 1 && c->c1.M) return &c->c1;
+  if (level == 2 && c->c2.M) return &c->c2;
+  return nullptr;
 }
 
 int mg_get_coarse_op(mg_ctx* c, int level, double* out) {
   if (!c || !out) return fail(MG_ERR_ARG, "bad argument");
-  if (level != 1 || !c->c1.M64) return fail(MG_ERR_STATE, "no coarse operator on that level");
-  return launch_coarse_export(P64, c->c1.cg, c->c1.M64, out, c->s);
+  CoarseLevel* L = coarse_level(c, level);
+  if (!L) return fail(MG_ERR_STATE, "no coarse operator on that level");
+  return launch_coarse_export(P64, L->cg, L->M64, out, c->s);
 }
 
 int mg_restrict(mg_ctx* c, int level, const void* in, void* out, int prec) {
   if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
   const bool blocked = (prec & MG_BLOCKED) != 0;
   prec &= 0xff;
-  if (level != 0 || !c->Pv) return fail(MG_ERR_STATE, "no interpolation on that level");
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
+  if (level == 1 && c->W) {
+    ProfScope ps(c->prof, FAM_RESTRICT, c->s);
+    return launch_transfer1(true, c->vt, c->c1.cg, c->agg1, in, out, c->W, c->N1, 1, c->s);
+  }
+  if (level != 0 || !c->Pv) return fail(MG_ERR_STATE, "no interpolation on that level");
   const void* src;
   TRY(stage_in(c, in, prec, blocked, 1, &src));
   ProfScope ps(c->prof, FAM_RESTRICT, c->s);
@@ -835,8 +1046,12 @@ int mg_prolong(mg_ctx* c, int level, const void* in, void* out, int prec) {
   if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
   const bool blocked = (prec & MG_BLOCKED) != 0;
   prec &= 0xff;
-  if (level != 0 || !c->Pv) return fail(MG_ERR_STATE, "no interpolation on that level");
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
+  if (level == 1 && c->W) {
+    ProfScope ps(c->prof, FAM_PROLONG, c->s);
+    return launch_transfer1(false, c->vt, c->c1.cg, c->agg1, in, out, c->W, c->N1, 1, c->s);
+  }
+  if (level != 0 || !c->Pv) return fail(MG_ERR_STATE, "no interpolation on that level");
   void* dst = blocked ? out : c->io_b;
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
@@ -856,22 +1071,24 @@ int mg_coarse_apply(mg_ctx* c, int level, const void* in, void* out, int prec) {
 int mg_coarse_apply_batch(mg_ctx* c, int level, const void* in, void* out, int prec, int nrhs) {
   if (!c || !in || !out || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
   prec &= 0xff;
-  if (level != 1 || !c->c1.M) return fail(MG_ERR_STATE, "no coarse operator on that level");
+  CoarseLevel* L = coarse_level(c, level);
+  if (!L) return fail(MG_ERR_STATE, "no coarse operator on that level");
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
-  TRY(coarse_apply(c, c->c1, in, out, nrhs));
+  TRY(coarse_apply(c, *L, in, out, nrhs));
   return check_device_error(c);
 }
 
 int mg_coarse_solve(mg_ctx* c, int level, const void* in, void* out, int prec) {
   if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
   prec &= 0xff;
-  if (level != 1 || !c->c1.M) return fail(MG_ERR_STATE, "no coarse operator on that level");
+  CoarseLevel* L = coarse_level(c, level);
+  if (!L) return fail(MG_ERR_STATE, "no coarse operator on that level");
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
-  const size_t bytes = c->c1.n() * complex_bytes(c->vt);
-  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->c1.b, in, bytes, cudaMemcpyDeviceToDevice, c->s));
-  TRY(coarse_solve(c, 1, 1));
-  SAPMG_CUDA_TRY(cudaMemcpyAsync(out, c->c1.x, bytes, cudaMemcpyDeviceToDevice, c->s));
-  return MG_OK;
+  const size_t bytes = L->n() * complex_bytes(c->vt);
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(L->b, in, bytes, cudaMemcpyDeviceToDevice, c->s));
+  TRY(coarse_solve(c, level, 1));
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(out, L->x, bytes, cudaMemcpyDeviceToDevice, c->s));
+  return check_device_error(c);
 }
 
 int mg_coarse_solve_noalloc(mg_ctx* c, int level, const void* in, void* out, int prec) {
