@@ -24,7 +24,7 @@ WORKLOADS = {
     # Plain vs mixed precision, three levels.
     "16^3x32": dict(
         dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.55,
-        rhs="z2", rhs_seed=202, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
+        rhs="z2", rhs_seed=202, n_levels=3, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
         precision="fp16", metric=METRIC, ref_iterations=60),
     # Multi-RHS: 12 spin-colour point sources.
