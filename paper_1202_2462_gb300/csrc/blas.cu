@@ -15,7 +15,9 @@ template <class T2> struct RealOf;
 template <> struct RealOf<double2> { typedef double R; };
 template <> struct RealOf<float2> { typedef float R; };
 
-template <class T2> struct Ptrs8 { const T2* p[8]; };
+// up to 16 vectors per launch
+constexpr int kChunk = 16;
+template <class T2> struct Ptrs8 { const T2* p[kChunk]; };
 
 // CTAs per right-hand side of a reduction: at least 8 elements per thread, and
 // R * CTAs within the partial buffer.
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(256) multidot_partial(Ptrs8<T2> v, const T2* _
   if (threadIdx.x < K) {
     double s = 0, m = 0;
     for (int q = 0; q < 8; ++q) { s += red[q][2 * threadIdx.x]; m += red[q][2 * threadIdx.x + 1]; }
-    partial[((size_t)r * gridDim.x + blockIdx.x) * 8 + threadIdx.x] = make_double2(s, m);
+    partial[((size_t)r * gridDim.x + blockIdx.x) * kChunk + threadIdx.x] = make_double2(s, m);
   }
 }
 
@@ -68,7 +70,7 @@ __global__ void multidot_finalize(const double2* __restrict__ partial, int ncta,
   for (int j = 0; j < k; ++j) {
     double s = 0, m = 0;
     for (int c = threadIdx.x; c < ncta; c += blockDim.x) {
-      const double2 v = partial[((size_t)r * ncta + c) * 8 + j];
+      const double2 v = partial[((size_t)r * ncta + c) * kChunk + j];
       s += v.x;
       m += v.y;
     }
@@ -102,21 +104,18 @@ static int multidot_t(const BVec& b, const void* const* v, int k, const void* w,
                       double2* out2, double2* partial, cudaStream_t s) {
   const int ncta = reduce_ctas(b.n, b.R);
   const dim3 grid(ncta, b.R);
-  for (int j0 = 0; j0 < k; j0 += 8) {
-    const int kk = std::min(8, k - j0);
+  for (int j0 = 0; j0 < k; j0 += kChunk) {
+    const int kk = std::min(kChunk, k - j0);
     Ptrs8<T2> p;
-    for (int j = 0; j < 8; ++j) p.p[j] = (const T2*)v[j0 + std::min(j, kk - 1)];
+    for (int j = 0; j < kChunk; ++j) p.p[j] = (const T2*)v[j0 + std::min(j, kk - 1)];
     const T2* wp = (const T2*)w;
+#define SAPMG_MD(K) case K: md_launch<T2, K>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
     switch (kk) {
-      case 1: md_launch<T2, 1>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
-      case 2: md_launch<T2, 2>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
-      case 3: md_launch<T2, 3>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
-      case 4: md_launch<T2, 4>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
-      case 5: md_launch<T2, 5>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
-      case 6: md_launch<T2, 6>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
-      case 7: md_launch<T2, 7>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
-      default: md_launch<T2, 8>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
+      SAPMG_MD(1) SAPMG_MD(2) SAPMG_MD(3) SAPMG_MD(4) SAPMG_MD(5) SAPMG_MD(6) SAPMG_MD(7) SAPMG_MD(8)
+      SAPMG_MD(9) SAPMG_MD(10) SAPMG_MD(11) SAPMG_MD(12) SAPMG_MD(13) SAPMG_MD(14) SAPMG_MD(15)
+      default: md_launch<T2, 16>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
     }
+#undef SAPMG_MD
     multidot_finalize<<<b.R, 256, 0, s>>>(partial, ncta, kk, out ? out + j0 : nullptr, ldo, mode,
                                           out2 ? out2 + j0 : nullptr); count_launches(1);
   }
@@ -132,11 +131,13 @@ int blas_multidot(int type, const BVec& b, const void* const* v, int k, const vo
   return MG_ERR_ARG;
 }
 
-// w[r] += sign * sum_j coeff[r*ldc + j] v_j[r]
+// w[r] += sign * sum_j coeff[r*ldc + j] v_j[r]; with partial != nullptr the
+// CTA also writes its part of ||w_new||^2 (finished by multidot_finalize).
 template <class T2, int K>
 __global__ void __launch_bounds__(256) multiaxpy_kernel(T2* __restrict__ w, Ptrs8<T2> v,
                                                         const double2* __restrict__ coeff, int ldc, double sign,
-                                                        size_t n, size_t vstride, size_t wstride) {
+                                                        size_t n, size_t vstride, size_t wstride,
+                                                        double2* __restrict__ partial) {
   typedef typename RealOf<T2>::R R;
   const int r = blockIdx.y;
   R cr[K], ci[K];
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(256) multiaxpy_kernel(T2* __restrict__ w, Ptrs
     ci[j] = (R)(sign * c.y);
   }
   T2* wr = w + r * wstride;
+  R nn = 0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     T2 x = wr[i];
 #pragma unroll
@@ -156,6 +158,19 @@ __global__ void __launch_bounds__(256) multiaxpy_kernel(T2* __restrict__ w, Ptrs
       x.y = fma(cr[j], a.y, fma(ci[j], a.x, x.y));
     }
     wr[i] = x;
+    nn = fma(x.x, x.x, fma(x.y, x.y, nn));
+  }
+  if (partial) {
+    __shared__ double red[8];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const R t = warp_sum(nn);
+    if (lane == 0) red[wid] = (double)t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0;
+      for (int q = 0; q < 8; ++q) sum += red[q];
+      partial[((size_t)r * gridDim.x + blockIdx.x) * kChunk] = make_double2(sum, 0.0);
+    }
   }
 }
 
@@ -166,29 +181,32 @@ static dim3 stream_grid(size_t n, int R) {
 }
 
 template <class T2, int K>
-static void ma_launch(T2* w, const Ptrs8<T2>& p, const double2* c, int ldc, double sign, const BVec& b,
-                      cudaStream_t s) {
-  multiaxpy_kernel<T2, K><<<stream_grid(b.n, b.R), 256, 0, s>>>(w, p, c, ldc, sign, b.n, b.vstride, b.wstride); count_launches(1);
+static void ma_launch(dim3 g, T2* w, const Ptrs8<T2>& p, const double2* c, int ldc, double sign, const BVec& b,
+                      double2* partial, cudaStream_t s) {
+  multiaxpy_kernel<T2, K><<<g, 256, 0, s>>>(w, p, c, ldc, sign, b.n, b.vstride, b.wstride, partial); count_launches(1);
 }
 
 template <class T2>
 static int multiaxpy_t(const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc,
-                       double sign, cudaStream_t s) {
-  for (int j0 = 0; j0 < k; j0 += 8) {
-    const int kk = std::min(8, k - j0);
+                       double sign, double2* nrm2, int ldn, double2* partial, cudaStream_t s) {
+  const dim3 g = nrm2 ? dim3(reduce_ctas(b.n, b.R), b.R) : stream_grid(b.n, b.R);
+  for (int j0 = 0; j0 < k; j0 += kChunk) {
+    const int kk = std::min(kChunk, k - j0);
+    const bool last = j0 + kChunk >= k;
     Ptrs8<T2> p;
-    for (int j = 0; j < 8; ++j) p.p[j] = (const T2*)v[j0 + std::min(j, kk - 1)];
+    for (int j = 0; j < kChunk; ++j) p.p[j] = (const T2*)v[j0 + std::min(j, kk - 1)];
     const double2* c = coeff + j0;
+    double2* part = (last && nrm2) ? partial : nullptr;
+#define SAPMG_MA(K) case K: ma_launch<T2, K>(g, (T2*)w, p, c, ldc, sign, b, part, s); break;
     switch (kk) {
-      case 1: ma_launch<T2, 1>((T2*)w, p, c, ldc, sign, b, s); break;
-      case 2: ma_launch<T2, 2>((T2*)w, p, c, ldc, sign, b, s); break;
-      case 3: ma_launch<T2, 3>((T2*)w, p, c, ldc, sign, b, s); break;
-      case 4: ma_launch<T2, 4>((T2*)w, p, c, ldc, sign, b, s); break;
-      case 5: ma_launch<T2, 5>((T2*)w, p, c, ldc, sign, b, s); break;
-      case 6: ma_launch<T2, 6>((T2*)w, p, c, ldc, sign, b, s); break;
-      case 7: ma_launch<T2, 7>((T2*)w, p, c, ldc, sign, b, s); break;
-      default: ma_launch<T2, 8>((T2*)w, p, c, ldc, sign, b, s); break;
+      SAPMG_MA(1) SAPMG_MA(2) SAPMG_MA(3) SAPMG_MA(4) SAPMG_MA(5) SAPMG_MA(6) SAPMG_MA(7) SAPMG_MA(8)
+      SAPMG_MA(9) SAPMG_MA(10) SAPMG_MA(11) SAPMG_MA(12) SAPMG_MA(13) SAPMG_MA(14) SAPMG_MA(15)
+      default: ma_launch<T2, 16>(g, (T2*)w, p, c, ldc, sign, b, part, s); break;
     }
+#undef SAPMG_MA
+  }
+  if (nrm2) {
+    multidot_finalize<<<b.R, 256, 0, s>>>(partial, (int)g.x, 1, nrm2, ldn, 0, nullptr); count_launches(1);
   }
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
@@ -197,8 +215,16 @@ static int multiaxpy_t(const BVec& b, void* w, const void* const* v, int k, cons
 int blas_multiaxpy(int type, const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc,
                    double sign, cudaStream_t s) {
   if (k <= 0 || b.R <= 0) return MG_OK;
-  if (type == P64) return multiaxpy_t<double2>(b, w, v, k, coeff, ldc, sign, s);
-  if (type == P32) return multiaxpy_t<float2>(b, w, v, k, coeff, ldc, sign, s);
+  if (type == P64) return multiaxpy_t<double2>(b, w, v, k, coeff, ldc, sign, nullptr, 0, nullptr, s);
+  if (type == P32) return multiaxpy_t<float2>(b, w, v, k, coeff, ldc, sign, nullptr, 0, nullptr, s);
+  return MG_ERR_ARG;
+}
+
+int blas_multiaxpy_norm(int type, const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc,
+                        double sign, double2* nrm2, int ldn, double2* partial, cudaStream_t s) {
+  if (k <= 0 || b.R <= 0) return MG_OK;
+  if (type == P64) return multiaxpy_t<double2>(b, w, v, k, coeff, ldc, sign, nrm2, ldn, partial, s);
+  if (type == P32) return multiaxpy_t<float2>(b, w, v, k, coeff, ldc, sign, nrm2, ldn, partial, s);
   return MG_ERR_ARG;
 }
 

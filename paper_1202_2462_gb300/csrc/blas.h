@@ -5,8 +5,9 @@
 namespace sapmg {
 
 // Upper bound on the CTAs of one reduction over all right-hand sides; the
-// partial buffer holds kMaxReduceCta * 8 double2.
+// partial buffer holds kMaxReduceCta * 16 double2.
 constexpr int kMaxReduceCta = 4096;
+constexpr size_t kPartialDouble2 = (size_t)kMaxReduceCta * 16;
 
 // Geometry of a batched vector operation: R systems, n elements each; the
 // vector v_j of system r is at v_j + r*vstride, w of system r at w + r*wstride.
@@ -27,6 +28,9 @@ int blas_multidot(int type, const BVec& b, const void* const* v, int k, const vo
 // w[r] += sign * sum_j coeff[r*ldc + j] v_j[r] with device coefficients.
 int blas_multiaxpy(int type, const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc,
                    double sign, cudaStream_t s);
+// The same, and nrm2[r*ldn] = ||w_new[r]||^2 computed in the same pass.
+int blas_multiaxpy_norm(int type, const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc,
+                        double sign, double2* nrm2, int ldn, double2* partial, cudaStream_t s);
 // y[r] = a_r x[r] + b_r y[r]; element types tx, ty (P64 / P32); b_r = 0: y not read.
 int blas_axpby2(int tx, const Scal32& a, const void* x, size_t xs, int ty, const Scal32& b, void* y, size_t ys,
                 size_t n, int R, cudaStream_t s);

@@ -74,6 +74,125 @@ __global__ void __launch_bounds__(256) prolong0_kernel(const TC* __restrict__ in
   store_spinor<R>(out + (size_t)rhs * nblocks * 12 * 256, blk, loc, o);
 }
 
+// Multi-RHS forms for the mixed precision (FP32 vectors):
+//
+// K3': CTA (block, chirality, group of RG right-hand sides).  The group's
+// residual half-spinors (6 components x 256 sites each) are staged in shared
+// memory; warp w owns the outputs (k, r) with k = w, w+8, w+16, ... and lane l
+// sums the terms K = l, l+32, ... of the 1536-term dot products, then the
+// lanes are reduced.  P is read once per group (not once per right-hand side).
+template <int RG, class TV>
+__global__ void __launch_bounds__(256) restrict0_mrhs_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                             const TV* __restrict__ Pv, int N, int nrhs,
+                                                             int nblocks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* rs = reinterpret_cast<float2*>(smem_raw);             // [RG][1536]
+  // right-hand-side group fastest in the grid: the groups of one (block,
+  // chirality) run back to back and share its P rows through L2
+  const int ngrp = (nrhs + RG - 1) / RG;
+  const int r0 = (blockIdx.x % ngrp) * RG;
+  const int blk = blockIdx.x / ngrp / 2, chi = (blockIdx.x / ngrp) % 2;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const size_t fs = (size_t)nblocks * 12 * 256;
+  const int rg = min(RG, nrhs - r0);
+  for (int e = tid; e < RG * 1536; e += 256) {
+    const int r = e / 1536, K = e % 1536;
+    rs[e] = r < rg ? in[(size_t)(r0 + r) * fs + ((size_t)blk * 12 + 6 * chi) * 256 + K] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  constexpr int KW = 3;                                           // k = w + 8*q, q < KW (N <= 24)
+  float are[KW][RG], aim[KW][RG];
+#pragma unroll
+  for (int q = 0; q < KW; ++q)
+#pragma unroll
+    for (int r = 0; r < RG; ++r) are[q][r] = aim[q][r] = 0.f;
+  for (int K = lane; K < 1536; K += 32) {
+    float2 x[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) x[r] = rs[r * 1536 + K];
+#pragma unroll
+    for (int q = 0; q < KW; ++q) {
+      const int k = w + 8 * q;
+      if (k < N) {
+        const Cplx<float> v = Io<float, TV>::ld(Pv + ((size_t)(blk * N + k) * 12 + 6 * chi) * 256 + K);
+#pragma unroll
+        for (int r = 0; r < RG; ++r) {
+          are[q][r] = fmaf(v.re, x[r].x, fmaf(v.im, x[r].y, are[q][r]));
+          aim[q][r] = fmaf(v.re, x[r].y, fmaf(-v.im, x[r].x, aim[q][r]));
+        }
+      }
+    }
+  }
+  const int n2 = 2 * N;
+#pragma unroll
+  for (int q = 0; q < KW; ++q) {
+    const int k = w + 8 * q;
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+      const float sr = warp_sum(are[q][r]), si = warp_sum(aim[q][r]);
+      if (lane == 0 && k < N && r < rg)
+        out[(size_t)(r0 + r) * nblocks * n2 + (size_t)blk * n2 + chi * N + k] = make_float2(sr, si);
+    }
+  }
+}
+
+// K4': CTA (block, spin-colour component c): thread = site; out_r[c] =
+// sum_k v_k[c] e_r[blk][chi(c)*N + k] for all right-hand sides; P read once.
+template <class TV>
+__global__ void __launch_bounds__(256) prolong0_mrhs_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                            const TV* __restrict__ Pv, int N, int nrhs,
+                                                            int nblocks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* es = reinterpret_cast<float2*>(smem_raw);              // [nrhs][N] of this chirality
+  const int blk = blockIdx.x, c = blockIdx.y, loc = threadIdx.x;
+  const int chi = c / 6, n2 = 2 * N;
+  for (int e = loc; e < nrhs * N; e += 256) {
+    const int r = e / N, k = e % N;
+    es[e] = in[(size_t)r * nblocks * n2 + (size_t)blk * n2 + chi * N + k];
+  }
+  __syncthreads();
+  const size_t fs = (size_t)nblocks * 12 * 256;
+  for (int r0 = 0; r0 < nrhs; r0 += 12) {
+    const int rc = min(12, nrhs - r0);
+    float2 acc[12];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int k = 0; k < N; ++k) {
+      const Cplx<float> v = Io<float, TV>::ld(Pv + ((size_t)(blk * N + k) * 12 + c) * 256 + loc);
+#pragma unroll
+      for (int r = 0; r < 12; ++r) {
+        if (r < rc) {
+          const float2 e = es[(r0 + r) * N + k];
+          acc[r].x = fmaf(v.re, e.x, fmaf(-v.im, e.y, acc[r].x));
+          acc[r].y = fmaf(v.re, e.y, fmaf(v.im, e.x, acc[r].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 12; ++r)
+      if (r < rc) out[(size_t)(r0 + r) * fs + ((size_t)blk * 12 + c) * 256 + loc] = acc[r];
+  }
+}
+
+template <class TV>
+static int transfer0_mrhs(bool restrict_, const Geom& g, const void* in, void* out, const void* Pv, int N, int nrhs,
+                          cudaStream_t s) {
+  if (restrict_) {
+    constexpr int RG = 4;
+    const size_t smem = sizeof(float2) * RG * 1536;
+    const unsigned grid = (unsigned)(g.nblocks * 2 * ((nrhs + RG - 1) / RG));
+    restrict0_mrhs_kernel<RG, TV><<<grid, 256, smem, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs,
+                                                          g.nblocks); count_launches(1);
+  } else {
+    const size_t smem = sizeof(float2) * nrhs * N;
+    dim3 grid(g.nblocks, 12);
+    prolong0_mrhs_kernel<TV><<<grid, 256, smem, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs,
+                                                     g.nblocks); count_launches(1);
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
 template <class R, class TS, class TV, class TC>
 static int transfer0_run(bool restrict_, const Geom& g, const void* in, void* out, const void* Pv, int N, int nrhs,
                          cudaStream_t s) {
@@ -93,6 +212,15 @@ static int transfer0_run(bool restrict_, const Geom& g, const void* in, void* ou
 
 int launch_transfer0(bool restrict_, int prec, const Geom& g, const void* in, void* out, const void* Pv, int N,
                      int nrhs, cudaStream_t s) {
+  // several right-hand sides in the mixed form: the forms that read P once
+  if (nrhs > 1 && prec != P64 && N <= 24) {
+    switch (prec) {
+      case P32: return transfer0_mrhs<float2>(restrict_, g, in, out, Pv, N, nrhs, s);
+      case P16: return transfer0_mrhs<__half2>(restrict_, g, in, out, Pv, N, nrhs, s);
+      case PBF: return transfer0_mrhs<__nv_bfloat162>(restrict_, g, in, out, Pv, N, nrhs, s);
+      default: break;
+    }
+  }
   switch (prec) {
     case P64: return transfer0_run<double, double2, double2, double2>(restrict_, g, in, out, Pv, N, nrhs, s);
     case P32: return transfer0_run<float, float2, float2, float2>(restrict_, g, in, out, Pv, N, nrhs, s);

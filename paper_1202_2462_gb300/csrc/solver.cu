@@ -244,12 +244,15 @@ static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k, int R) {
     vl.push_back(Vj(j));
     double2* hcol = L.H + (size_t)j * 33;
     TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
-    TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
     if (c->coarse_reorth) {
+      TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
       TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 1, L.tmp, c->partial, c->s));
-      TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, c->s));
+      TRY(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
+                              c->s));
+    } else {
+      TRY(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
+                              c->s));
     }
-    TRY(dot_to(c, vt, bv, L.w, L.w, L.tmp + 40, 33 * 33));
     TRY(blas_normalize(vt, bv, L.w, Vj(j + 1), L.tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
   }
   TRY(blas_hessenberg_solve(L.H, 33, 33 * 33, k, L.beta2, L.y, 33, R, c->s));
@@ -281,12 +284,15 @@ static int fgmres_fixed1(mg_ctx* c, int k, int R) {
     zl.push_back(Zj(j));
     double2* hcol = c->f1H + (size_t)j * 33;
     TRY(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
-    TRY(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
     if (c->coarse_reorth) {
+      TRY(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
       TRY(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 1, c->f1tmp, c->partial, c->s));
-      TRY(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, c->f1tmp, 33 * 33, -1.0, c->s));
+      TRY(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, c->f1tmp, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
+                              c->partial, c->s));
+    } else {
+      TRY(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
+                              c->partial, c->s));
     }
-    TRY(dot_to(c, vt, bv, c->f1w, c->f1w, c->f1tmp + 40, 33 * 33));
     TRY(blas_normalize(vt, bv, c->f1w, Vj(j + 1), c->f1tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
   }
   TRY(blas_hessenberg_solve(c->f1H, 33, 33 * 33, k, c->f1beta2, c->f1y, 33, R, c->s));
@@ -388,8 +394,7 @@ static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, cons
     vl.push_back(c->w);                  // h = V^dagger w and ||w||^2 in one pass
     TRY(blas_multidot(ft, bv, vl.data(), j + 2, c->w, c->hd, ld, 0, nullptr, c->partial, c->s));
     vl.pop_back();
-    TRY(blas_multiaxpy(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->s));
-    TRY(dot_to(c, ft, bv, c->w, c->w, c->hd + j + 2, ld));
+    TRY(blas_multiaxpy_norm(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->hd + j + 2, ld, c->partial, c->s));
     SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * R * ld, cudaMemcpyDeviceToHost, c->s));
     SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
     bool again = false;
@@ -401,8 +406,7 @@ static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, cons
     }
     if (again) {
       TRY(blas_multidot(ft, bv, vl.data(), j + 1, c->w, c->hd, ld, 0, nullptr, c->partial, c->s));
-      TRY(blas_multiaxpy(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->s));
-      TRY(dot_to(c, ft, bv, c->w, c->w, c->hd + j + 2, ld));
+      TRY(blas_multiaxpy_norm(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->hd + j + 2, ld, c->partial, c->s));
       SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * R * ld, cudaMemcpyDeviceToHost, c->s));
       SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
       for (int q = 0; q < R; ++q) {
@@ -793,7 +797,7 @@ static int do_setup(mg_ctx* c, const double* U) {
   // workspace
   const size_t eb = complex_bytes(c->vt);
   const int R = p.nrhs_max;
-  c->partial = (double2*)c->alloc(sizeof(double2) * kMaxReduceCta * 8);
+  c->partial = (double2*)c->alloc(sizeof(double2) * kPartialDouble2);
   c->dev_err = (int*)c->alloc(sizeof(int));
   if (!c->dev_err) return fail(MG_ERR_OOM, "workspace");
   SAPMG_CUDA_TRY(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->s));
@@ -1104,7 +1108,7 @@ int mg_coarse_solve_noalloc(mg_ctx* c, int level, const void* in, void* out, int
   // carve the scratch: partial sums | H | H scratch | ||b||^2 | y | basis V (k+1) | w
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t o_part = 0;
-  const size_t o_h = o_part + up(sizeof(double2) * kMaxReduceCta * 8);
+  const size_t o_h = o_part + up(sizeof(double2) * kPartialDouble2);
   const size_t o_tmp = o_h + up(sizeof(double2) * 33 * 33);
   const size_t o_beta = o_tmp + up(sizeof(double2) * 33 * 33);
   const size_t o_y = o_beta + up(sizeof(double2));
