@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(256) restrict0_mrhs_kernel(const float2* __res
   for (int q = 0; q < KW; ++q)
 #pragma unroll
     for (int r = 0; r < RG; ++r) are[q][r] = aim[q][r] = 0.f;
+#pragma unroll 4
   for (int K = lane; K < 1536; K += 32) {
     float2 x[RG];
 #pragma unroll
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(256) prolong0_mrhs_kernel(const float2* __rest
     float2 acc[12];
 #pragma unroll
     for (int r = 0; r < 12; ++r) acc[r] = make_float2(0.f, 0.f);
+#pragma unroll 4
     for (int k = 0; k < N; ++k) {
       const Cplx<float> v = Io<float, TV>::ld(Pv + ((size_t)(blk * N + k) * 12 + c) * 256 + loc);
 #pragma unroll

@@ -35,6 +35,14 @@ static int fail(int code, const std::string& m) {
     if (rc__ < 0) return rc__;  \
   } while (0)
 
+// TRY for a vector-kernel call, timed as the BLAS family when profiling is on
+#define BLAS(x)                                     \
+  do {                                              \
+    ProfScope ps__(c->prof, FAM_BLAS, c->s);        \
+    int rc__ = (x);                                 \
+    if (rc__ < 0) return rc__;                      \
+  } while (0)
+
 enum { FAM_DIRAC = 0, FAM_SAP = 1, FAM_COARSE = 2, FAM_RESTRICT = 3, FAM_PROLONG = 4, FAM_BLAS = 5, FAM_N = 6 };
 
 struct Prof {
@@ -236,28 +244,28 @@ static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k, int R) {
   const size_t eb = complex_bytes(vt);
   const BVec bv = bvec(n, R, n);
   auto Vj = [&](int j) { return (void*)((char*)L.V + (size_t)j * R * n * eb); };
-  TRY(dot_to(c, vt, bv, L.b, L.b, L.beta2, 1));
-  TRY(blas_normalize(vt, bv, L.b, Vj(0), L.beta2, 1, nullptr, 0, c->s));
+  BLAS(dot_to(c, vt, bv, L.b, L.b, L.beta2, 1));
+  BLAS(blas_normalize(vt, bv, L.b, Vj(0), L.beta2, 1, nullptr, 0, c->s));
   std::vector<const void*> vl;
   for (int j = 0; j < k; ++j) {
     TRY(coarse_apply(c, L, Vj(j), L.w, R));
     vl.push_back(Vj(j));
     double2* hcol = L.H + (size_t)j * 33;
-    TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
+    BLAS(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
     if (c->coarse_reorth) {
-      TRY(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
-      TRY(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 1, L.tmp, c->partial, c->s));
-      TRY(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
+      BLAS(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
+      BLAS(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 1, L.tmp, c->partial, c->s));
+      BLAS(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
                               c->s));
     } else {
-      TRY(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
+      BLAS(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
                               c->s));
     }
-    TRY(blas_normalize(vt, bv, L.w, Vj(j + 1), L.tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
+    BLAS(blas_normalize(vt, bv, L.w, Vj(j + 1), L.tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
   }
-  TRY(blas_hessenberg_solve(L.H, 33, 33 * 33, k, L.beta2, L.y, 33, R, c->s));
+  BLAS(blas_hessenberg_solve(L.H, 33, 33 * 33, k, L.beta2, L.y, 33, R, c->s));
   SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, (size_t)R * n * eb, c->s));
-  TRY(blas_multiaxpy(vt, bv, L.x, vl.data(), k, L.y, 33, 1.0, c->s));
+  BLAS(blas_multiaxpy(vt, bv, L.x, vl.data(), k, L.y, 33, 1.0, c->s));
   return MG_OK;
 }
 
@@ -274,8 +282,8 @@ static int fgmres_fixed1(mg_ctx* c, int k, int R) {
   const BVec bv = bvec(n, R, n);
   auto Vj = [&](int j) { return (void*)((char*)c->f1V + (size_t)j * R * n * eb); };
   auto Zj = [&](int j) { return (void*)((char*)c->f1Z + (size_t)j * R * n * eb); };
-  TRY(dot_to(c, vt, bv, L.b, L.b, c->f1beta2, 1));
-  TRY(blas_normalize(vt, bv, L.b, Vj(0), c->f1beta2, 1, nullptr, 0, c->s));
+  BLAS(dot_to(c, vt, bv, L.b, L.b, c->f1beta2, 1));
+  BLAS(blas_normalize(vt, bv, L.b, Vj(0), c->f1beta2, 1, nullptr, 0, c->s));
   std::vector<const void*> vl, zl;
   for (int j = 0; j < k; ++j) {
     TRY(cycle1(c, Vj(j), Zj(j), R));
@@ -283,21 +291,21 @@ static int fgmres_fixed1(mg_ctx* c, int k, int R) {
     vl.push_back(Vj(j));
     zl.push_back(Zj(j));
     double2* hcol = c->f1H + (size_t)j * 33;
-    TRY(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
+    BLAS(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
     if (c->coarse_reorth) {
-      TRY(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
-      TRY(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 1, c->f1tmp, c->partial, c->s));
-      TRY(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, c->f1tmp, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
+      BLAS(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
+      BLAS(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 1, c->f1tmp, c->partial, c->s));
+      BLAS(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, c->f1tmp, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
                               c->partial, c->s));
     } else {
-      TRY(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
+      BLAS(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
                               c->partial, c->s));
     }
-    TRY(blas_normalize(vt, bv, c->f1w, Vj(j + 1), c->f1tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
+    BLAS(blas_normalize(vt, bv, c->f1w, Vj(j + 1), c->f1tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
   }
-  TRY(blas_hessenberg_solve(c->f1H, 33, 33 * 33, k, c->f1beta2, c->f1y, 33, R, c->s));
+  BLAS(blas_hessenberg_solve(c->f1H, 33, 33 * 33, k, c->f1beta2, c->f1y, 33, R, c->s));
   SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, (size_t)R * n * eb, c->s));
-  TRY(blas_multiaxpy(vt, bv, L.x, zl.data(), k, c->f1y, 33, 1.0, c->s));
+  BLAS(blas_multiaxpy(vt, bv, L.x, zl.data(), k, c->f1y, 33, 1.0, c->s));
   return MG_OK;
 }
 
@@ -384,7 +392,7 @@ static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, cons
     g[(size_t)q * (m + 1)] = rnorm[q];
   }
   if (n_active == 0) return MG_OK;
-  TRY(blas_axpby2(ft, a, r, n, ft, zero, Vj(0), n, n, R, c->s));
+  BLAS(blas_axpby2(ft, a, r, n, ft, zero, Vj(0), n, n, R, c->s));
   auto Hq = [&](int q, int i, int j) -> cd& { return H[(size_t)q * (m + 1) * m + i + (size_t)j * (m + 1)]; };
   std::vector<const void*> vl;
   for (int j = 0; j < m; ++j) {
@@ -392,9 +400,9 @@ static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, cons
     TRY(fine_dirac(c, aprec, c->w, Zj(j), R));
     vl.push_back(Vj(j));
     vl.push_back(c->w);                  // h = V^dagger w and ||w||^2 in one pass
-    TRY(blas_multidot(ft, bv, vl.data(), j + 2, c->w, c->hd, ld, 0, nullptr, c->partial, c->s));
+    BLAS(blas_multidot(ft, bv, vl.data(), j + 2, c->w, c->hd, ld, 0, nullptr, c->partial, c->s));
     vl.pop_back();
-    TRY(blas_multiaxpy_norm(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->hd + j + 2, ld, c->partial, c->s));
+    BLAS(blas_multiaxpy_norm(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->hd + j + 2, ld, c->partial, c->s));
     SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * R * ld, cudaMemcpyDeviceToHost, c->s));
     SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
     bool again = false;
@@ -405,8 +413,8 @@ static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, cons
       if (active[q] && h[j + 2].x < 0.5 * h[j + 1].x) again = true;
     }
     if (again) {
-      TRY(blas_multidot(ft, bv, vl.data(), j + 1, c->w, c->hd, ld, 0, nullptr, c->partial, c->s));
-      TRY(blas_multiaxpy_norm(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->hd + j + 2, ld, c->partial, c->s));
+      BLAS(blas_multidot(ft, bv, vl.data(), j + 1, c->w, c->hd, ld, 0, nullptr, c->partial, c->s));
+      BLAS(blas_multiaxpy_norm(ft, bv, c->w, vl.data(), j + 1, c->hd, ld, -1.0, c->hd + j + 2, ld, c->partial, c->s));
       SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, sizeof(double2) * R * ld, cudaMemcpyDeviceToHost, c->s));
       SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
       for (int q = 0; q < R; ++q) {
@@ -448,7 +456,7 @@ static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, cons
       ++n_active;
     }
     if (n_active == 0 || j + 1 == m) break;
-    TRY(blas_axpby2(ft, a, c->w, n, ft, zero, Vj(j + 1), n, n, R, c->s));
+    BLAS(blas_axpby2(ft, a, c->w, n, ft, zero, Vj(j + 1), n, n, R, c->s));
   }
   // back substitution per system and x += Z y
   int jmax = 0;
@@ -468,7 +476,7 @@ static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, cons
   SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hd, c->hh, sizeof(double2) * R * ld, cudaMemcpyHostToDevice, c->s));
   std::vector<const void*> zl;
   for (int i = 0; i < jmax; ++i) zl.push_back(Zj(i));
-  TRY(blas_multiaxpy(ft, bv, x, zl.data(), jmax, c->hd, ld, 1.0, c->s));
+  BLAS(blas_multiaxpy(ft, bv, x, zl.data(), jmax, c->hd, ld, 1.0, c->s));
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));   // hh is reused by the next cycle
   return MG_OK;
 }
@@ -488,7 +496,7 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
   const size_t n = c->fine_n();
   std::vector<double> bn, rn, tol(R), ones(R, 1.0), inner(R), est;
   std::vector<int> done;
-  TRY(host_norms(c, P64, c->b64, R, bn));
+  BLAS(host_norms(c, P64, c->b64, R, bn));
   SAPMG_CUDA_TRY(cudaMemsetAsync(c->x64, 0, (size_t)R * n * 16, c->s));
   SAPMG_CUDA_TRY(cudaMemcpyAsync(c->r64, c->b64, (size_t)R * n * 16, cudaMemcpyDeviceToDevice, c->s));
   for (int q = 0; q < R; ++q) tol[q] = c->p.tol * bn[q];
@@ -496,7 +504,7 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
   restarts = 0;
   const Scal32 one = scal_all(1.0, R), zero = scal_all(0.0, R), minus = scal_all(-1.0, R);
   for (;;) {
-    TRY(host_norms(c, P64, c->r64, R, rn));
+    BLAS(host_norms(c, P64, c->r64, R, rn));
     relres = 0;
     bool all = true;
     for (int q = 0; q < R; ++q) {
@@ -520,19 +528,19 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
       }
       std::vector<double> unorm(R);
       for (int q = 0; q < R; ++q) unorm[q] = act[q] > 0 ? 1.0 : 0.0;
-      TRY(blas_axpby2(P64, a, c->r64, n, P32, zero, c->t64, n, n, R, c->s));
+      BLAS(blas_axpby2(P64, a, c->r64, n, P32, zero, c->t64, n, n, R, c->s));
       SAPMG_CUDA_TRY(cudaMemsetAsync(c->e32, 0, (size_t)R * n * 8, c->s));
       TRY(fgmres_cycle(c, P32, P32, R, c->t64, unorm, c->e32, inner, c->p.maxiter - iters, done, est));
       Scal32 sc = zero;
       for (int q = 0; q < R; ++q) sc.v[q].x = act[q];
-      TRY(blas_axpby2(P32, sc, c->e32, n, P64, one, c->x64, n, n, R, c->s));
+      BLAS(blas_axpby2(P32, sc, c->e32, n, P64, one, c->x64, n, n, R, c->s));
     }
     int step = 0;
     for (int q = 0; q < R; ++q) step = std::max(step, done[q]);
     iters += step;
     restarts += 1;
     TRY(fine_dirac(c, P64, c->r64, c->x64, R));
-    TRY(blas_axpby2(P64, one, c->b64, n, P64, minus, c->r64, n, n, R, c->s));
+    BLAS(blas_axpby2(P64, one, c->b64, n, P64, minus, c->r64, n, n, R, c->s));
     if (step == 0) return MG_NOT_CONVERGED;
   }
 }
