@@ -9,6 +9,8 @@
 #include "internal.h"
 #include "blas.h"
 
+#include <type_traits>
+
 namespace sapmg {
 
 template <class T2> struct RealOf;
@@ -37,12 +39,15 @@ __global__ void __launch_bounds__(256) multidot_partial(Ptrs8<T2> v, const T2* _
 #pragma unroll
   for (int j = 0; j < K; ++j) are[j] = aim[j] = 0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const T2 x = wr[i];
+    // issue every load of the element before any arithmetic (memory-level parallelism)
+    T2 a[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) a[j] = __ldg(&v.p[j][r * vstride + i]);
+    const T2 x = __ldg(&wr[i]);
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      const T2 a = v.p[j][r * vstride + i];
-      are[j] = fma(a.x, x.x, fma(a.y, x.y, are[j]));
-      aim[j] = fma(a.x, x.y, fma(-a.y, x.x, aim[j]));
+      are[j] = fma(a[j].x, x.x, fma(a[j].y, x.y, are[j]));
+      aim[j] = fma(a[j].x, x.y, fma(-a[j].y, x.x, aim[j]));
     }
   }
   __shared__ double red[8][2 * K];
@@ -52,6 +57,44 @@ __global__ void __launch_bounds__(256) multidot_partial(Ptrs8<T2> v, const T2* _
   for (int j = 0; j < K; ++j) {
     const R s = warp_sum(are[j]);
     const R m = warp_sum(aim[j]);
+    if (lane == 0) { red[wid][2 * j] = (double)s; red[wid][2 * j + 1] = (double)m; }
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0, m = 0;
+    for (int q = 0; q < 8; ++q) { s += red[q][2 * threadIdx.x]; m += red[q][2 * threadIdx.x + 1]; }
+    partial[((size_t)r * gridDim.x + blockIdx.x) * kChunk + threadIdx.x] = make_double2(s, m);
+  }
+}
+
+// FP32 vectors with an even length: two complex numbers per 16-byte load.
+template <int K>
+__global__ void __launch_bounds__(256) multidot_partial_f4(Ptrs8<float2> v, const float2* __restrict__ w, size_t n,
+                                                           size_t vstride, size_t wstride,
+                                                           double2* __restrict__ partial) {
+  const int r = blockIdx.y;
+  const float4* wr = reinterpret_cast<const float4*>(w + r * wstride);
+  const size_t n4 = n / 2;
+  float are[K], aim[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) are[j] = aim[j] = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    float4 a[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) a[j] = __ldg(reinterpret_cast<const float4*>(v.p[j] + r * vstride) + i);
+    const float4 x = __ldg(wr + i);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      are[j] = fmaf(a[j].x, x.x, fmaf(a[j].y, x.y, fmaf(a[j].z, x.z, fmaf(a[j].w, x.w, are[j]))));
+      aim[j] = fmaf(a[j].x, x.y, fmaf(-a[j].y, x.x, fmaf(a[j].z, x.w, fmaf(-a[j].w, x.z, aim[j]))));
+    }
+  }
+  __shared__ double red[8][2 * K];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const float s = warp_sum(are[j]);
+    const float m = warp_sum(aim[j]);
     if (lane == 0) { red[wid][2 * j] = (double)s; red[wid][2 * j + 1] = (double)m; }
   }
   __syncthreads();
@@ -99,21 +142,37 @@ static void md_launch(dim3 grid, const Ptrs8<T2>& p, const T2* w, size_t n, size
   multidot_partial<T2, K><<<grid, 256, 0, s>>>(p, w, n, vs, ws, part); count_launches(1);
 }
 
+template <class T2, int K>
+static void md_launch_any(bool vec4, dim3 grid, const Ptrs8<T2>& p, const T2* w, size_t n, size_t vs, size_t ws,
+                          double2* part, cudaStream_t s) {
+  if constexpr (std::is_same<T2, float2>::value) {
+    if (vec4) {
+      multidot_partial_f4<K><<<grid, 256, 0, s>>>(p, w, n, vs, ws, part); count_launches(1);
+      return;
+    }
+  }
+  md_launch<T2, K>(grid, p, w, n, vs, ws, part, s);
+}
+
 template <class T2>
 static int multidot_t(const BVec& b, const void* const* v, int k, const void* w, double2* out, int ldo, int mode,
                       double2* out2, double2* partial, cudaStream_t s) {
-  const int ncta = reduce_ctas(b.n, b.R);
+  // two complex numbers per load when every vector is 16-byte aligned and n is even
+  bool vec4 = (b.n % 2 == 0) && (b.vstride % 2 == 0) && (b.wstride % 2 == 0) &&
+              ((reinterpret_cast<uintptr_t>(w) & 15) == 0);
+  for (int j = 0; j < k; ++j) vec4 = vec4 && ((reinterpret_cast<uintptr_t>(v[j]) & 15) == 0);
+  const int ncta = reduce_ctas(vec4 ? b.n / 2 : b.n, b.R);
   const dim3 grid(ncta, b.R);
   for (int j0 = 0; j0 < k; j0 += kChunk) {
     const int kk = std::min(kChunk, k - j0);
     Ptrs8<T2> p;
     for (int j = 0; j < kChunk; ++j) p.p[j] = (const T2*)v[j0 + std::min(j, kk - 1)];
     const T2* wp = (const T2*)w;
-#define SAPMG_MD(K) case K: md_launch<T2, K>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
+#define SAPMG_MD(K) case K: md_launch_any<T2, K>(vec4, grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
     switch (kk) {
       SAPMG_MD(1) SAPMG_MD(2) SAPMG_MD(3) SAPMG_MD(4) SAPMG_MD(5) SAPMG_MD(6) SAPMG_MD(7) SAPMG_MD(8)
       SAPMG_MD(9) SAPMG_MD(10) SAPMG_MD(11) SAPMG_MD(12) SAPMG_MD(13) SAPMG_MD(14) SAPMG_MD(15)
-      default: md_launch<T2, 16>(grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
+      default: md_launch_any<T2, 16>(vec4, grid, p, wp, b.n, b.vstride, b.wstride, partial, s); break;
     }
 #undef SAPMG_MD
     multidot_finalize<<<b.R, 256, 0, s>>>(partial, ncta, kk, out ? out + j0 : nullptr, ldo, mode,

@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) restrict0_mrhs_kernel(const float2* __res
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const size_t fs = (size_t)nblocks * 12 * 256;
   const int rg = min(RG, nrhs - r0);
+#pragma unroll 8
   for (int e = tid; e < RG * 1536; e += 256) {
     const int r = e / 1536, K = e % 1536;
     rs[e] = r < rg ? in[(size_t)(r0 + r) * fs + ((size_t)blk * 12 + 6 * chi) * 256 + K] : make_float2(0.f, 0.f);

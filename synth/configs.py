@@ -39,6 +39,12 @@ WORKLOADS = {
         rhs="gaussian", rhs_seed=204, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(12,),
         n_mr=4, nu_post=2, setup_iters=2, coarse_iters=12, fgmres_m=10, tol=1e-10, maxiter=30,
         precision="bf16", metric=METRIC, ref_iterations=60),
+    # 12 point sources on a small lattice: Nsight Compute captures of the multi-RHS kernels.
+    "16^3x32-12rhs": dict(
+        dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.55,
+        rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(20,),
+        n_mr=4, nu_post=2, setup_iters=2, coarse_iters=12, fgmres_m=6, tol=1e-10, maxiter=12,
+        precision="bf16", metric=METRIC, ref_iterations=60),
 }
 
 
