@@ -189,3 +189,39 @@ def free_spectrum(dims, m0, antiperiodic_t=False):
     im = np.sqrt(sum(np.sin(q) ** 2 for q in p))
     ev = np.concatenate([re.ravel() + 1j * im.ravel(), re.ravel() - 1j * im.ravel()])
     return np.repeat(ev, 6)
+
+
+def patch(field, origin, size, lat_axes=4):
+    """The periodic sub-box of a field (Lt, Lz, Ly, Lx, ...) starting at origin
+    (x, y, z, t) with edge ``size`` (indices wrap around the lattice)."""
+    out = field
+    for mu in range(4):
+        axis = 3 - mu
+        n = field.shape[axis]
+        idx = (origin[mu] + np.arange(size)) % n
+        out = np.take(out, idx, axis=axis)
+    return out
+
+
+def apply_at_sites(u, psi, m0, c_sw, sites, antiperiodic_t=False, round_fields=None):
+    """(D psi)(x) for a list of sites x = (x, y, z, t), each evaluated on its own
+    5^4 periodic patch centred on x: the clover term at x reaches two sites
+    out, the hops one, so the patch wrap never touches them.  Returns an array
+    (len(sites), 4, 3).  ``round_fields`` (a function) is applied to the links
+    of the hops and to the clover matrix, to mimic reduced storage.
+
+    An antiperiodic time boundary is not supported here (the patch loses the
+    global position of the boundary)."""
+    if antiperiodic_t:
+        raise NotImplementedError("site evaluation supports periodic boundaries only")
+    out = []
+    for x in sites:
+        origin = tuple(c - 2 for c in x)
+        up = patch(u, origin, 5)
+        pp = patch(psi, origin, 5)
+        op = WilsonClover(up, m0, c_sw)
+        if round_fields is not None:
+            op.a = round_fields(op.a)
+            op.u = round_fields(op.u)
+        out.append(op.apply(pp)[2, 2, 2, 2])
+    return np.array(out)

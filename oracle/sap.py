@@ -154,3 +154,43 @@ def sap(op, blocks, b, z0, n_sweeps, n_mr):
     for _ in range(n_sweeps):
         z = sap_sweep(op, blocks, b, z, n_mr)
     return z
+
+
+def mr_on_mask(op, mask, r, n_mr):
+    """n_mr MR steps on the single block selected by the 0/1 site mask (the
+    operator mask D mask), from e = 0; returns e."""
+    m = _expand(mask, op.tail)
+    axes = tuple(range(-op.tail - 4, 0))
+    e = np.zeros_like(r)
+    rho = m * r
+    for _ in range(n_mr):
+        p = m * op.apply(m * rho)
+        pr = np.sum(np.conj(p) * rho, axis=axes)
+        pp = np.sum((np.conj(p) * p).real, axis=axes)
+        alpha = pr / pp if pp > 0 else 0.0
+        e = e + alpha * rho
+        rho = rho - alpha * p
+    return e
+
+
+def colour_pass_on_block(u, m0, c_sw, b, z, block_origin, n_mr, round_fields=None):
+    """One Schwarz colour pass (Algorithm 1) restricted to the 4^4 block at
+    block_origin = (x, y, z, t) of a periodic lattice: r = b - D z on the block,
+    n_mr MR steps with the block operator, z + e on the block.  Evaluated on an
+    8^4 patch with the block at offset 2, far enough from the patch wrap for
+    the clover term and the hops.  Returns the block's new z, (4, 4, 4, 4, 4, 3)
+    indexed (t, z, y, x)."""
+    from .dirac import WilsonClover, patch
+    origin = tuple(c - 2 for c in block_origin)
+    up = patch(u, origin, 8)
+    op = WilsonClover(up, m0, c_sw)
+    if round_fields is not None:
+        op.a = round_fields(op.a)
+        op.u = round_fields(op.u)
+    bp = patch(b, origin, 8)
+    zp = patch(z, origin, 8)
+    mask = np.zeros((8, 8, 8, 8))
+    mask[2:6, 2:6, 2:6, 2:6] = 1.0
+    r = (bp - op.apply(zp)) * mask[..., None, None]
+    e = mr_on_mask(op, mask, r, n_mr)
+    return (zp + e)[2:6, 2:6, 2:6, 2:6]
