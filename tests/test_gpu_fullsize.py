@@ -68,7 +68,7 @@ def test_fullsize_schwarz_sweep_sampled_blocks(big):
     torch.cuda.synchronize()
     s.close()
     lx, ly, lz, lt = dims
-    blocks = [(0, 0, 0, 0), (lx - 4, ly - 4, lz - 4, lt - 4), (4, 4, 0, 0), (8, 12, 20, 36)]
+    blocks = [(0, 0, 0, 0), (lx - 4, ly - 4, lz - 4, lt - 4), (4, 4, 0, 0), (8, 12, 20, 40)]
     for o in blocks:
         assert (sum(c // 4 for c in o)) % 2 == 0                       # colour 0: final after the sweep
     for r in (0, 7):
