@@ -46,6 +46,10 @@ int launch_coarse_export(int prec, const CGeom& c, const void* M, double* out, c
 // err: device flag raised when a bounded wait gives up.
 int launch_coarse_apply_tma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
                             cudaStream_t s);
+// The same stencil with the block products on tensor cores (TF32 inputs, FP32
+// accumulation; n2 % 8 == 0, n2 <= 64).
+int launch_coarse_apply_mma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
+                            cudaStream_t s);
 
 // Intermediate level of a three-level hierarchy (coarse1.cu).
 int launch_coarse_sap(int prec, const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,

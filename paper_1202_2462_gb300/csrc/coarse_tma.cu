@@ -179,6 +179,180 @@ static void launch_tma(const CGeom& c, const float2* M, const float2* x, float2*
   coarse_apply_tma_kernel<RB, APT><<<grid, 256, smem, s>>>(M, x, out, c, r0, err); count_launches(1);
 }
 
+// ---------------------------------------------------------------- tensor-core form
+// The same stencil with the per-block products on tensor cores
+// (mma.sync m16n8k8, TF32 inputs, FP32 accumulation).  For one block M_d(a)
+// and the RB right-hand sides the complex product out += M x is the real
+// product Y += A X with
+//   A[2i][2j] = Re M_ij, A[2i][2j+1] = -Im M_ij, A[2i+1][2j] = Im M_ij,
+//   A[2i+1][2j+1] = Re M_ij,   X[2j][r] = Re x_r(j), X[2j+1][r] = Im x_r(j),
+// Y[2i][r] = Re out_r(i), Y[2i+1][r] = Im out_r(i): 2n2 x 2n2 times 2n2 x 16.
+// Warp w owns rows 16w..16w+15 of Y (both 8-column tiles); the 9 blocks of a
+// site accumulate in the same fragments.  Needs n2 % 8 == 0.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// component (a, b) of the real embedding of complex m: (0,0) re, (0,1) -im, (1,0) im, (1,1) re
+__device__ __forceinline__ float embed(float2 m, int a, int b) {
+  return a == b ? m.x : (a ? m.y : -m.y);
+}
+
+template <int RB>
+__global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const float2* __restrict__ M,
+                                                               const float2* __restrict__ x,
+                                                               float2* __restrict__ out, CGeom c, int r0,
+                                                               int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int n2 = c.n2;
+  const int xst = n2 + 2;                                     // padded row stride of the staged vectors
+  const int tile = n2 * n2;
+  const uint32_t tile_bytes = (uint32_t)tile * sizeof(float2);
+  float2* buf0 = reinterpret_cast<float2*>(smem);
+  float2* buf1 = buf0 + tile;
+  float2* xs = buf1 + tile;                                   // [16][xst], rows >= RB are zero
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tig = lane & 3;
+  const size_t fs = (size_t)c.nsites * n2;
+  const float2* xr = x + (size_t)r0 * fs;
+  const int nsite_cta = (c.nsites - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int T = 9 * nsite_cta;
+  if (T <= 0) return;
+  for (int e = tid; e < 16 * xst; e += blockDim.x) xs[e] = make_float2(0.f, 0.f);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto tile_src = [&](int t) {
+    const int site = (int)blockIdx.x + (t / 9) * (int)gridDim.x;
+    return M + ((size_t)site * 9 + (t % 9)) * tile;
+  };
+  if (tid == 0) {
+    mbar_expect_tx(&bar[0], tile_bytes);
+    bulk_copy_g2s(buf0, tile_src(0), tile_bytes, &bar[0]);
+  }
+  const int m0 = warp * 16;                                   // rows of Y owned by this warp
+  float acc[2][4];
+  int tfail = -1;
+  for (int t = 0; t < T; ++t) {
+    const int d = t % 9;
+    const int site = (int)blockIdx.x + (t / 9) * (int)gridDim.x;
+    if (d == 0) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+    }
+    if (tid == 0 && t + 1 < T) {
+      uint64_t* b = &bar[(t + 1) & 1];
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(b, tile_bytes);
+      bulk_copy_g2s(((t + 1) & 1) ? buf1 : buf0, tile_src(t + 1), tile_bytes, b);
+    }
+    {
+      int nb = site;
+      if (d > 0) {
+        const int mu = (d - 1) >> 1, step = (d & 1) ? 1 : -1;
+        int stride = 1;
+        for (int m = 0; m < mu; ++m) stride *= c.L[m];
+        const int xc = (site / stride) % c.L[mu];
+        nb = site + (((xc + step + c.L[mu]) % c.L[mu]) - xc) * stride;
+      }
+      for (int e = tid; e < RB * n2; e += blockDim.x)
+        xs[(e / n2) * xst + e % n2] = xr[(size_t)(e / n2) * fs + (size_t)nb * n2 + e % n2];
+    }
+    const bool waited = mbar_wait(&bar[t & 1], (uint32_t)((t >> 1) & 1));
+    if (__syncthreads_or(!waited)) {
+      tfail = t;
+      break;
+    }
+    const float2* mt = (t & 1) ? buf1 : buf0;
+    if (m0 < 2 * n2) {
+      const int i0 = (m0 >> 1) + (g >> 1), a = g & 1;        // output row pair of A rows m0+g, m0+g+8
+      for (int k0 = 0; k0 < 2 * n2; k0 += 8) {
+        const int j0 = (k0 >> 1) + (tig >> 1), bb = tig & 1;  // input column pair of A cols k0+tig, +4
+        const uint32_t a0 = to_tf32(embed(mt[j0 * n2 + i0], a, bb));
+        const uint32_t a1 = to_tf32(embed(mt[j0 * n2 + i0 + 4], a, bb));
+        const uint32_t a2 = to_tf32(embed(mt[(j0 + 2) * n2 + i0], a, bb));
+        const uint32_t a3 = to_tf32(embed(mt[(j0 + 2) * n2 + i0 + 4], a, bb));
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const float2 x0 = xs[(8 * q + g) * xst + j0];
+          const float2 x1 = xs[(8 * q + g) * xst + j0 + 2];
+          const uint32_t b0 = to_tf32(bb ? x0.y : x0.x);
+          const uint32_t b1 = to_tf32(bb ? x1.y : x1.x);
+          mma_tf32(acc[q], a0, a1, a2, a3, b0, b1);
+        }
+      }
+      if (d == 8) {
+        // Y rows m0+g (and +8) = (re or im) of out_r(i0) (and out_r(i0 + 4)), columns 2 tig, 2 tig + 1
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = 8 * q + 2 * tig + h;
+            if (r < RB) {
+              float* o = reinterpret_cast<float*>(out + (size_t)(r0 + r) * fs + (size_t)site * n2);
+              o[2 * i0 + a] = acc[q][h];
+              o[2 * (i0 + 4) + a] = acc[q][2 + h];
+            }
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (tfail >= 0) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      mbar_wait(&bar[tfail & 1], (uint32_t)((tfail >> 1) & 1));
+      if (tfail + 1 < T) mbar_wait(&bar[(tfail + 1) & 1], (uint32_t)(((tfail + 1) >> 1) & 1));
+    }
+    __syncthreads();
+  }
+}
+
+template <int RB>
+static void launch_mma(const CGeom& c, const float2* M, const float2* x, float2* out, int r0, int* err,
+                       cudaStream_t s) {
+  const size_t smem = (size_t)(2 * c.n2 * c.n2 + 16 * (c.n2 + 2)) * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(coarse_apply_mma_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const int threads = 32 * (c.n2 / 8);                        // one warp per 16 rows of the 2 n2 real rows
+  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / (smem + 1024)));
+  const int grid = std::min(c.nsites, 152 * per_sm);
+  coarse_apply_mma_kernel<RB><<<grid, threads, smem, s>>>(M, x, out, c, r0, err); count_launches(1);
+}
+
+// Tensor-core form: n2 % 8 == 0 and n2 <= 64; up to 16 right-hand sides per launch.
+int launch_coarse_apply_mma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
+                            cudaStream_t s) {
+  if (c.n2 % 8 != 0 || c.n2 > 64) return MG_ERR_ARG;
+  for (int r0 = 0; r0 < nrhs; r0 += 16) {
+    const int rb = std::min(16, nrhs - r0);
+    if (rb > 12) launch_mma<16>(c, (const float2*)M, (const float2*)x, (float2*)out, r0, err, s);
+    else if (rb > 4) launch_mma<12>(c, (const float2*)M, (const float2*)x, (float2*)out, r0, err, s);
+    else if (rb > 1) launch_mma<4>(c, (const float2*)M, (const float2*)x, (float2*)out, r0, err, s);
+    else launch_mma<1>(c, (const float2*)M, (const float2*)x, (float2*)out, r0, err, s);
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
 // Requires 16-byte aligned blocks (n2 even) and n2 <= 64; the caller routes
 // other shapes to the generic kernel.
 int launch_coarse_apply_tma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,

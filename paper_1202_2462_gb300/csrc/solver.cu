@@ -126,6 +126,7 @@ struct mg_ctx {
   int pv_prec = P64; // storage of the interpolation P (FP16 for both half modes)
   int coarse_reorth = 0;  // second Gram-Schmidt pass in the coarse GMRES (SAPMG_COARSE_REORTH=1)
   int generic_coarse = 0; // use the generic coarse stencil kernel (SAPMG_GENERIC_COARSE=1)
+  int coarse_tf32 = 1;    // tensor-core (TF32) coarse stencil in the mixed form (SAPMG_COARSE_TF32=0 disables)
   int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
   double m0 = 0, csw = 0;
   std::vector<void*> allocs;
@@ -212,6 +213,8 @@ static int dot_to(mg_ctx* c, int type, const BVec& b, const void* x, const void*
 // D_c x on a coarse level: the bulk-copy kernel for an FP32 operator, else the generic one.
 static int coarse_apply(mg_ctx* c, CoarseLevel& L, const void* x, void* out, int R) {
   ProfScope ps(c->prof, FAM_COARSE, c->s);
+  if (L.store == P32 && c->vt == P32 && c->coarse_tf32 && L.cg.n2 % 8 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
+    return launch_coarse_apply_mma(L.cg, L.M, x, out, R, c->dev_err, c->s);
   if (L.store == P32 && c->vt == P32 && L.cg.n2 % 2 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
     return launch_coarse_apply_tma(L.cg, L.M, x, out, R, c->dev_err, c->s);
   return launch_coarse_apply(L.store, L.cg, L.M, x, out, R, c->s);
@@ -921,6 +924,7 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   c->dc_prec = p->precision == MG_FP64 ? P64 : P32;
   c->coarse_reorth = std::getenv("SAPMG_COARSE_REORTH") ? std::atoi(std::getenv("SAPMG_COARSE_REORTH")) : 0;
   c->generic_coarse = std::getenv("SAPMG_GENERIC_COARSE") ? std::atoi(std::getenv("SAPMG_GENERIC_COARSE")) : 0;
+  c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
   c->m0 = m0;
   c->csw = c_sw;
   const int rc = do_setup(c, U);

@@ -241,3 +241,42 @@ def test_fp32_coarse_stencil_batched_parity():
     s.close()
     ref = c.apply(x.astype(np.complex128)).reshape(17, 16, 12)
     assert rel(host(out), ref) < 2e-6
+
+
+def _tf32(x):
+    """Round float32 values to TF32 (10-bit mantissa, to nearest with ties away
+    from zero), as the tensor-core coarse stencil rounds its inputs."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    b = f.view(np.uint32)
+    b = ((b.astype(np.uint64) + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return b.view(np.float32).astype(np.float64)
+
+
+def _tf32c(z):
+    return _tf32(np.real(z)) + 1j * _tf32(np.imag(z))
+
+
+@pytest.mark.parametrize("tf32", [1, 0])
+def test_coarse_stencil_tensor_core_parity(tf32, monkeypatch):
+    """n2 = 16 takes the tensor-core stencil (TF32 inputs, FP32 accumulation):
+    compared with the oracle's stencil on TF32-rounded operator entries and
+    vectors.  With SAPMG_COARSE_TF32=0 the FP32 bulk-copy stencil runs and is
+    compared with FP32-rounded entries."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    monkeypatch.setenv("SAPMG_COARSE_TF32", str(tf32))
+    u = synth.random_gauge_field(DIMS, 0.4, 49)
+    iv = synth.test_vector_draw(DIMS, 8, 50)
+    s = _solver(torch, u, n_levels=2, n_vec=(8,), setup_iters=0, precision="fp32", init_vectors=dev(torch, iv))
+    op = WilsonClover(u, M0, CSW)
+    c = CoarseOperator(op, Aggregation(DIMS, (4, 4, 4, 4), (4, 3)).build(iv))
+    rnd = _tf32c if tf32 else (lambda a: round_storage(a, "fp32"))
+    for name in ("self_", "fwd", "bwd"):
+        setattr(c, name, rnd(getattr(c, name)))
+    x = synth.random_spinor((2, 2, 2, 2), 51, nvec=13).reshape(13, 2, 2, 2, 2, 12)
+    x = np.concatenate([x, x[:, ..., :4] * 0.5], axis=-1).astype(np.complex64)     # 16 dof per site
+    out = torch.zeros((13, 16, 16), dtype=torch.complex64, device="cuda")
+    G.mg_coarse_apply_batch(s.ctx, 1, dev(torch, x), out, G.MG_FP32, 13)
+    s.close()
+    ref = c.apply(rnd(x.astype(np.complex128))).reshape(13, 16, 16)
+    assert rel(host(out), ref) < 5e-6
