@@ -167,6 +167,14 @@ int mg_get_coarse_op(mg_ctx* ctx, int level, double* out);
 int mg_restrict(mg_ctx* ctx, int level, const void* in, void* out, int prec);
 int mg_prolong(mg_ctx* ctx, int level, const void* in, void* out, int prec);
 int mg_coarse_apply(mg_ctx* ctx, int level, const void* in, void* out, int prec);
+/* Restriction and interpolation of nrhs <= nrhs_max vectors stored back to
+ * back (fine side [nrhs][field], coarse side [nrhs][sites][2N]), the batched
+ * form the cycle uses.  In the mixed form with nrhs > 1 the level-0
+ * restriction runs on the tensor cores: the FP32 fine vectors and the stored
+ * P enter as TF32 (10-bit mantissa, rounded to nearest), sums are FP32
+ * (environment SAPMG_RESTRICT_TF32=0 selects the FP32 form).  Asynchronous. */
+int mg_restrict_batch(mg_ctx* ctx, int level, const void* in, void* out, int prec, int nrhs);
+int mg_prolong_batch(mg_ctx* ctx, int level, const void* in, void* out, int prec, int nrhs);
 /* The same for nrhs coarse vectors stored back to back ([nrhs][sites][2N]);
  * synchronises (it checks the device error flag of the bounded waits). */
 int mg_coarse_apply_batch(mg_ctx* ctx, int level, const void* in, void* out, int prec, int nrhs);

@@ -85,6 +85,8 @@ _SIGNATURES = {
     "mg_prolong": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_coarse_apply": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_coarse_apply_batch": (_I, [_VP, _I, _VP, _VP, _I, _I]),
+    "mg_restrict_batch": (_I, [_VP, _I, _VP, _VP, _I, _I]),
+    "mg_prolong_batch": (_I, [_VP, _I, _VP, _VP, _I, _I]),
     "mg_coarse_solve": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_coarse_solve_noalloc": (_I, [_VP, _I, _VP, _VP, _I]),
     "mg_precondition": (_I, [_VP, _VP, _VP, _I]),
@@ -198,6 +200,14 @@ def mg_prolong(ctx, level, inp, out, prec):
 
 def mg_coarse_apply(ctx, level, inp, out, prec):
     return _check(lib().mg_coarse_apply(ctx, level, _ptr(inp), _ptr(out), prec), "mg_coarse_apply")
+
+
+def mg_restrict_batch(ctx, level, inp, out, prec, nrhs):
+    return _check(lib().mg_restrict_batch(ctx, level, _ptr(inp), _ptr(out), prec, nrhs), "mg_restrict_batch")
+
+
+def mg_prolong_batch(ctx, level, inp, out, prec, nrhs):
+    return _check(lib().mg_prolong_batch(ctx, level, _ptr(inp), _ptr(out), prec, nrhs), "mg_prolong_batch")
 
 
 def mg_coarse_apply_batch(ctx, level, inp, out, prec, nrhs):

@@ -177,9 +177,126 @@ __global__ void __launch_bounds__(256) prolong0_mrhs_kernel(const float2* __rest
   }
 }
 
+// K3'' (tensor cores): CTA (block, chirality), all right-hand sides (<= 16).
+// With K' = 2K + (0 re, 1 im) over the 1536 complex entries of the chiral
+// half-block, C = A B with A[k][K'] = the stored v_k (re/im interleaved, as P
+// is stored) and B[2K][2r] = Re x_r(K), B[2K+1][2r] = Im x_r(K),
+// B[2K][2r+1] = Im x_r(K), B[2K+1][2r+1] = -Re x_r(K) gives
+// C[k][2r] = Re <v_k, x_r>, C[k][2r+1] = Im <v_k, x_r>.  mma.sync m16n8k8 TF32
+// (FP16-stored P converts exactly); warp w takes the K steps w, w+8, ...;
+// the warps' partial products are added in shared memory.
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                                 uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int NT, class TV>
+__global__ void __launch_bounds__(256) restrict0_mma_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                            const TV* __restrict__ Pv, int N, int nrhs,
+                                                            int nblocks) {
+  __shared__ float red[8][2][NT][4][32];                       // [warp][M tile][N tile][fragment][lane]
+  const int blk = blockIdx.x >> 1, chi = blockIdx.x & 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tig = lane & 3;
+  const size_t fs = (size_t)nblocks * 12 * 256;
+  const size_t off = ((size_t)blk * 12 + 6 * chi) * 256;      // start of the chiral half-block
+  float acc[2][NT][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < NT; ++q) acc[m][q][0] = acc[m][q][1] = acc[m][q][2] = acc[m][q][3] = 0.f;
+  const int p1 = tig & 1;
+  for (int ks = warp; ks < 384; ks += 8) {                    // 3072 real K over steps of 8
+    const int K1 = ks * 4 + (tig >> 1);                       // complex entry of columns k'0+tig (and +4: K1+2)
+    uint32_t a[2][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int r0 = 16 * m + g, r1 = r0 + 8;
+      float v00 = 0.f, v01 = 0.f, v10 = 0.f, v11 = 0.f;
+      if (r0 < N) {
+        const Cplx<float> x = Io<float, TV>::ld(Pv + ((size_t)(blk * N + r0) * 12 + 6 * chi) * 256 + K1);
+        const Cplx<float> y = Io<float, TV>::ld(Pv + ((size_t)(blk * N + r0) * 12 + 6 * chi) * 256 + K1 + 2);
+        v00 = p1 ? x.im : x.re;
+        v01 = p1 ? y.im : y.re;
+      }
+      if (r1 < N) {
+        const Cplx<float> x = Io<float, TV>::ld(Pv + ((size_t)(blk * N + r1) * 12 + 6 * chi) * 256 + K1);
+        const Cplx<float> y = Io<float, TV>::ld(Pv + ((size_t)(blk * N + r1) * 12 + 6 * chi) * 256 + K1 + 2);
+        v10 = p1 ? x.im : x.re;
+        v11 = p1 ? y.im : y.re;
+      }
+      a[m][0] = f32_to_tf32(v00);
+      a[m][1] = f32_to_tf32(v10);
+      a[m][2] = f32_to_tf32(v01);
+      a[m][3] = f32_to_tf32(v11);
+    }
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+      const int col = 8 * q + g, r = col >> 1, pc = col & 1;
+      float b0 = 0.f, b1 = 0.f;
+      if (r < nrhs) {
+        const float2 x = in[(size_t)r * fs + off + K1];
+        const float2 y = in[(size_t)r * fs + off + K1 + 2];
+        // B[2K+p1][2r+pc]: (pc, p1) = (0,0) re, (0,1) im, (1,0) im, (1,1) -re
+        b0 = pc ? (p1 ? -x.x : x.y) : (p1 ? x.y : x.x);
+        b1 = pc ? (p1 ? -y.x : y.y) : (p1 ? y.y : y.x);
+      }
+      const uint32_t tb0 = f32_to_tf32(b0), tb1 = f32_to_tf32(b1);
+#pragma unroll
+      for (int m = 0; m < 2; ++m) mma_m16n8k8_tf32(acc[m][q], a[m][0], a[m][1], a[m][2], a[m][3], tb0, tb1);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int q = 0; q < NT; ++q)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) red[warp][m][q][f][lane] = acc[m][q][f];
+  __syncthreads();
+  // warp 0 adds the eight partial products and writes C[k][2r], C[k][2r+1]
+  if (warp == 0) {
+    const int n2 = 2 * N;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int q = 0; q < NT; ++q) {
+        float s[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int w = 0; w < 8; ++w)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) s[f] += red[w][m][q][f][lane];
+        const int r = (8 * q + 2 * tig) >> 1;                  // columns 2 tig (re) and 2 tig + 1 (im)
+        const int k0 = 16 * m + g, k1 = k0 + 8;
+        if (r < nrhs) {
+          float2* o = out + (size_t)r * nblocks * n2 + (size_t)blk * n2 + chi * N;
+          if (k0 < N) o[k0] = make_float2(s[0], s[1]);
+          if (k1 < N) o[k1] = make_float2(s[2], s[3]);
+        }
+      }
+  }
+}
+
 template <class TV>
 static int transfer0_mrhs(bool restrict_, const Geom& g, const void* in, void* out, const void* Pv, int N, int nrhs,
-                          cudaStream_t s) {
+                          bool tf32, cudaStream_t s) {
+  if (restrict_ && tf32 && nrhs <= 16 && N <= 32) {
+    const unsigned grid = (unsigned)(g.nblocks * 2);
+    if (nrhs <= 4) { restrict0_mma_kernel<1, TV><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs, g.nblocks); count_launches(1); }
+    else if (nrhs <= 8) { restrict0_mma_kernel<2, TV><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs, g.nblocks); count_launches(1); }
+    else if (nrhs <= 12) { restrict0_mma_kernel<3, TV><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs, g.nblocks); count_launches(1); }
+    else { restrict0_mma_kernel<4, TV><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs, g.nblocks); count_launches(1); }
+    SAPMG_CUDA_TRY(cudaGetLastError());
+    return MG_OK;
+  }
   if (restrict_) {
     constexpr int RG = 4;
     const size_t smem = sizeof(float2) * RG * 1536;
@@ -214,13 +331,13 @@ static int transfer0_run(bool restrict_, const Geom& g, const void* in, void* ou
 }
 
 int launch_transfer0(bool restrict_, int prec, const Geom& g, const void* in, void* out, const void* Pv, int N,
-                     int nrhs, cudaStream_t s) {
+                     int nrhs, bool tf32, cudaStream_t s) {
   // several right-hand sides in the mixed form: the forms that read P once
   if (nrhs > 1 && prec != P64 && N <= 24) {
     switch (prec) {
-      case P32: return transfer0_mrhs<float2>(restrict_, g, in, out, Pv, N, nrhs, s);
-      case P16: return transfer0_mrhs<__half2>(restrict_, g, in, out, Pv, N, nrhs, s);
-      case PBF: return transfer0_mrhs<__nv_bfloat162>(restrict_, g, in, out, Pv, N, nrhs, s);
+      case P32: return transfer0_mrhs<float2>(restrict_, g, in, out, Pv, N, nrhs, tf32, s);
+      case P16: return transfer0_mrhs<__half2>(restrict_, g, in, out, Pv, N, nrhs, tf32, s);
+      case PBF: return transfer0_mrhs<__nv_bfloat162>(restrict_, g, in, out, Pv, N, nrhs, tf32, s);
       default: break;
     }
   }

@@ -31,9 +31,10 @@ inline Box4 make_box(const CGeom& c, const int b[4]) {
   return x;
 }
 
-// Level 0 -> 1 (4^4 aggregates = the fine blocks).
+// Level 0 -> 1 (4^4 aggregates = the fine blocks).  tf32: several FP32
+// right-hand sides are restricted on the tensor cores (TF32 inputs, FP32 sums).
 int launch_transfer0(bool restrict_, int prec, const Geom& g, const void* in, void* out, const void* Pv, int N,
-                     int nrhs, cudaStream_t s);
+                     int nrhs, bool tf32, cudaStream_t s);
 int launch_block_gs0(const Geom& g, void* V64, int N, cudaStream_t s);
 int launch_store_p0(int prec, const Geom& g, const void* V64, void* Pv, int N, cudaStream_t s);
 int launch_assemble0(const Geom& g, const void* V64, const void* U64, const void* A64, void* M64, int N,

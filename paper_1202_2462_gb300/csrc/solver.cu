@@ -127,6 +127,7 @@ struct mg_ctx {
   int coarse_reorth = 0;  // second Gram-Schmidt pass in the coarse GMRES (SAPMG_COARSE_REORTH=1)
   int generic_coarse = 0; // use the generic coarse stencil kernel (SAPMG_GENERIC_COARSE=1)
   int coarse_tf32 = 1;    // tensor-core (TF32) coarse stencil in the mixed form (SAPMG_COARSE_TF32=0 disables)
+  int restrict_tf32 = 1;  // tensor-core (TF32) multi-RHS restriction in the mixed form (SAPMG_RESTRICT_TF32=0 disables)
   int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
   double m0 = 0, csw = 0;
   std::vector<void*> allocs;
@@ -354,12 +355,12 @@ static int cycle(mg_ctx* c, const void* v, void* z, int R) {
   }
   {
     ProfScope ps(c->prof, FAM_RESTRICT, c->s);
-    TRY(launch_transfer0(true, c->pv_prec, c->g, v, c->c1.b, c->Pv, c->N0, R, c->s));
+    TRY(launch_transfer0(true, c->pv_prec, c->g, v, c->c1.b, c->Pv, c->N0, R, c->restrict_tf32, c->s));
   }
   TRY(coarse_solve(c, 1, R));
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
-    TRY(launch_transfer0(false, c->pv_prec, c->g, c->c1.x, z, c->Pv, c->N0, R, c->s));
+    TRY(launch_transfer0(false, c->pv_prec, c->g, c->c1.x, z, c->Pv, c->N0, R, c->restrict_tf32, c->s));
   }
   return smoother_sweeps(c, v, z, c->p.nu_post, R);
 }
@@ -658,7 +659,7 @@ static int setup_level1(mg_ctx* c) {
   TRY(launch_store_p0(P64, c->g, c->V64, p0buf, N0, c->s));
   for (int k = 0; k < N1; ++k)
     TRY(launch_transfer0(true, P64, c->g, (char*)c->Vs64 + (size_t)k * nf * 16, (char*)c->W64 + (size_t)k * n1 * 16,
-                         p0buf, N0, 1, c->s));
+                         p0buf, N0, 1, false, c->s));
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
   c->release(p0buf);
   c->release(c->Vs64);
@@ -925,6 +926,7 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   c->coarse_reorth = std::getenv("SAPMG_COARSE_REORTH") ? std::atoi(std::getenv("SAPMG_COARSE_REORTH")) : 0;
   c->generic_coarse = std::getenv("SAPMG_GENERIC_COARSE") ? std::atoi(std::getenv("SAPMG_GENERIC_COARSE")) : 0;
   c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
+  c->restrict_tf32 = std::getenv("SAPMG_RESTRICT_TF32") ? std::atoi(std::getenv("SAPMG_RESTRICT_TF32")) : 1;
   c->m0 = m0;
   c->csw = c_sw;
   const int rc = do_setup(c, U);
@@ -1043,39 +1045,49 @@ int mg_get_coarse_op(mg_ctx* c, int level, double* out) {
 }
 
 int mg_restrict(mg_ctx* c, int level, const void* in, void* out, int prec) {
-  if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
+  return mg_restrict_batch(c, level, in, out, prec, 1);
+}
+
+int mg_prolong(mg_ctx* c, int level, const void* in, void* out, int prec) {
+  return mg_prolong_batch(c, level, in, out, prec, 1);
+}
+
+int mg_restrict_batch(mg_ctx* c, int level, const void* in, void* out, int prec, int nrhs) {
+  if (!c || !in || !out || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
+  if (nrhs > c->p.nrhs_max) return fail(MG_ERR_ARG, "more right-hand sides than nrhs_max");
   const bool blocked = (prec & MG_BLOCKED) != 0;
   prec &= 0xff;
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
   if (level == 1 && c->W) {
     ProfScope ps(c->prof, FAM_RESTRICT, c->s);
-    return launch_transfer1(true, c->vt, c->c1.cg, c->agg1, in, out, c->W, c->N1, 1, c->s);
+    return launch_transfer1(true, c->vt, c->c1.cg, c->agg1, in, out, c->W, c->N1, nrhs, c->s);
   }
   if (level != 0 || !c->Pv) return fail(MG_ERR_STATE, "no interpolation on that level");
   const void* src;
-  TRY(stage_in(c, in, prec, blocked, 1, &src));
+  TRY(stage_in(c, in, prec, blocked, nrhs, &src));
   ProfScope ps(c->prof, FAM_RESTRICT, c->s);
-  return launch_transfer0(true, c->pv_prec, c->g, src, out, c->Pv, c->N0, 1, c->s);
+  return launch_transfer0(true, c->pv_prec, c->g, src, out, c->Pv, c->N0, nrhs, c->restrict_tf32, c->s);
 }
 
-int mg_prolong(mg_ctx* c, int level, const void* in, void* out, int prec) {
-  if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
+int mg_prolong_batch(mg_ctx* c, int level, const void* in, void* out, int prec, int nrhs) {
+  if (!c || !in || !out || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
+  if (nrhs > c->p.nrhs_max) return fail(MG_ERR_ARG, "more right-hand sides than nrhs_max");
   const bool blocked = (prec & MG_BLOCKED) != 0;
   prec &= 0xff;
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
   if (level == 1 && c->W) {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
-    return launch_transfer1(false, c->vt, c->c1.cg, c->agg1, in, out, c->W, c->N1, 1, c->s);
+    return launch_transfer1(false, c->vt, c->c1.cg, c->agg1, in, out, c->W, c->N1, nrhs, c->s);
   }
   if (level != 0 || !c->Pv) return fail(MG_ERR_STATE, "no interpolation on that level");
   void* dst = blocked ? out : c->io_b;
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
-    TRY(launch_transfer0(false, c->pv_prec, c->g, in, dst, c->Pv, c->N0, 1, c->s));
+    TRY(launch_transfer0(false, c->pv_prec, c->g, in, dst, c->Pv, c->N0, nrhs, c->restrict_tf32, c->s));
   }
   if (!blocked) {
     const int t = prec == P64 ? P64 : P32;
-    TRY(launch_unpack_spinor(t, dst, t, out, c->g, 1, c->s));
+    TRY(launch_unpack_spinor(t, dst, t, out, c->g, nrhs, c->s));
   }
   return MG_OK;
 }

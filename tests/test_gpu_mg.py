@@ -161,6 +161,53 @@ def test_mixed_transfer_parity():
     assert rel(host(rc), agg.restrict(r.astype(np.complex128)).reshape(16, 8)) < 2e-6
 
 
+def _tf32(x):
+    """Round float32 values to TF32 (10-bit mantissa, to nearest with ties away
+    from zero), as the tensor-core kernels round their inputs."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    b = f.view(np.uint32)
+    b = ((b.astype(np.uint64) + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return b.view(np.float32).astype(np.float64)
+
+
+def _tf32c(z):
+    return _tf32(np.real(z)) + 1j * _tf32(np.imag(z))
+
+
+@pytest.mark.parametrize("nrhs,tf32", [(13, 1), (3, 1), (13, 0)])
+def test_batched_transfer_parity(nrhs, tf32, monkeypatch):
+    """Restriction and interpolation of several FP32 vectors at once (the form
+    the cycle uses), FP16-stored P with N = 8, against the oracle's P^dagger
+    and P with the same rounded P.  The tensor-core restriction takes TF32
+    inputs (FP16 values are exact in TF32), so the oracle restricts the
+    TF32-rounded vectors; SAPMG_RESTRICT_TF32=0 selects the FP32 kernel."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    monkeypatch.setenv("SAPMG_RESTRICT_TF32", str(tf32))
+    u = synth.random_gauge_field(DIMS, 0.4, 52)
+    iv = synth.test_vector_draw(DIMS, 8, 53)
+    s = _solver(torch, u, n_levels=2, n_vec=(8,), setup_iters=0, precision="fp16", init_vectors=dev(torch, iv),
+                nrhs_max=16)
+    agg = Aggregation(DIMS, (4, 4, 4, 4), (4, 3)).build(iv)
+    agg.q = round_storage(agg.q, "fp16")
+    r = synth.random_spinor(DIMS, 54, nvec=nrhs).astype(np.complex64)
+    rc = torch.zeros((nrhs, 16, 16), dtype=torch.complex64, device="cuda")
+    G.mg_restrict_batch(s.ctx, 0, dev(torch, r), rc, G.MG_FP16, nrhs)
+    e = synth.random_spinor((2, 2, 2, 2), 55, nvec=nrhs).reshape(nrhs, 2, 2, 2, 2, 12)
+    e = np.concatenate([e, e[..., :4] * 0.5], axis=-1).astype(np.complex64)         # 16 dof per site
+    f = torch.zeros((nrhs,) + DIMS[::-1] + (4, 3), dtype=torch.complex64, device="cuda")
+    G.mg_prolong_batch(s.ctx, 0, dev(torch, e), f, G.MG_FP16, nrhs)
+    torch.cuda.synchronize()
+    s.close()
+    rin = _tf32c(r) if tf32 else r.astype(np.complex128)
+    ref = agg.restrict(rin).reshape(nrhs, 16, 16)
+    for k in range(nrhs):
+        assert rel(host(rc)[k], ref[k]) < (1e-5 if tf32 else 2e-6), k
+    fref = agg.prolong(e.astype(np.complex128))
+    for k in range(nrhs):
+        assert rel(host(f)[k], fref[k]) < 2e-6, k
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
 def test_solve_reaches_tolerance(field, prec):
     """Outer solve: the oracle's own D confirms ||b - D z|| <= 1e-10 ||b||."""
@@ -241,19 +288,6 @@ def test_fp32_coarse_stencil_batched_parity():
     s.close()
     ref = c.apply(x.astype(np.complex128)).reshape(17, 16, 12)
     assert rel(host(out), ref) < 2e-6
-
-
-def _tf32(x):
-    """Round float32 values to TF32 (10-bit mantissa, to nearest with ties away
-    from zero), as the tensor-core coarse stencil rounds its inputs."""
-    f = np.ascontiguousarray(x, dtype=np.float32)
-    b = f.view(np.uint32)
-    b = ((b.astype(np.uint64) + 0x1000) & 0xFFFFE000).astype(np.uint32)
-    return b.view(np.float32).astype(np.float64)
-
-
-def _tf32c(z):
-    return _tf32(np.real(z)) + 1j * _tf32(np.imag(z))
 
 
 @pytest.mark.parametrize("tf32", [1, 0])
