@@ -6,15 +6,20 @@ relative residual of 1e-10 (verified in FP64 by the library), with the set-up
 done once before the timed region and reported separately (as the paper's
 tables do).  The default workload is the 32^3 x 64 lattice with the 12
 spin-colour point sources, solved by the mixed-precision form (FP32
-arithmetic, BF16-stored links, clover, test vectors and coarse operators; FP64
-defect correction).  Prints one JSON line.
+arithmetic, BF16-stored links and clover, FP16-stored test vectors, FP32
+coarse operator; FP64 defect correction).  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 
+import os
+
+# the CPU legs time the oracle on one core: keep numpy's BLAS single-threaded
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
-import os
 import statistics
 import subprocess
 import sys
@@ -58,6 +63,15 @@ def bytes_dirac_site(prec):
     spinor = 2 * 12 * (16 if prec == "fp64" else 8)
     store = {"fp64": 16, "fp32": 8, "fp16": 4, "bf16": 4}[prec]
     return spinor + 2 * 36 * store
+
+
+# the kernels behind each timed family (a family call may issue several launches)
+FAMILY_KERNELS = {
+    "dirac": "dirac_kernel", "sap": "sap_colour_kernel", "coarse": "coarse_apply_mma_kernel",
+    "restrict": "restrict0_mma_kernel", "prolong": "prolong0_mrhs_kernel",
+    "blas": "multidot_partial_f4 + multiaxpy_kernel (outer flexible GMRES, fine vectors)",
+    "coarse_blas": "multidot/multiaxpy/normalize on coarse vectors",
+}
 
 
 def load_peaks():
@@ -241,7 +255,13 @@ def run_ours(a, wl):
     for _ in range(a.warmup):
         z, info, code = s.solve(b)
         infos.append((info.iterations, info.relres, code))
-    fam_ms = {f: G.mg_get_profile(s.ctx, i)[1] for f, i in G.PROFILE_FAMILIES.items()}
+    fam = {}
+    for f, i in G.PROFILE_FAMILIES.items():
+        n_f, ms_f = G.mg_get_profile(s.ctx, i)
+        b_f = G.mg_get_profile_bytes(s.ctx, i)
+        fam[f] = {"ms_per_step": ms_f / max(a.warmup, 1), "calls_per_step": n_f / max(a.warmup, 1),
+                  "alg_gbs": (b_f / (ms_f / 1e3) / 1e9) if ms_f > 0 and b_f > 0 else None}
+    fam_ms = {f: v["ms_per_step"] for f, v in fam.items()}
     dominant = max(fam_ms, key=fam_ms.get)
     G.mg_reset_profile(s.ctx)
     G.mg_set_profiling(s.ctx, G.profile_mask(dominant))
@@ -272,6 +292,7 @@ def run_ours(a, wl):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / a.steps
     n_prof, ms_prof = G.mg_get_profile(s.ctx, G.PROFILE_FAMILIES[dominant])
+    bytes_prof = G.mg_get_profile_bytes(s.ctx, G.PROFILE_FAMILIES[dominant])
     G.mg_set_profiling(s.ctx, 0)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -324,8 +345,10 @@ def run_ours(a, wl):
                 "flop_per_site": flops_sap_site(wl["n_mr"]), "alg_bytes_per_launch": alg_bytes}
     else:
         avg_s = ms_prof / max(n_prof, 1) / 1e3
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-                "traffic": None, "launches": n_prof, "avg_launch_ms": avg_s * 1e3}
+        gbs = bytes_prof / (ms_prof / 1e3) / 1e9 if ms_prof > 0 and bytes_prof > 0 else None
+        roof = {"kernel": FAMILY_KERNELS.get(dominant, dominant), "bound": "hbm", "achieved": gbs, "peak": hbm,
+                "unit": "GB/s", "frac": gbs / hbm if gbs else None, "traffic": None, "launches": n_prof,
+                "avg_launch_ms": avg_s * 1e3, "alg_bytes_per_launch": bytes_prof / max(n_prof, 1)}
 
     iters = [c[0] for c in codes]
     line = {
@@ -337,7 +360,7 @@ def run_ours(a, wl):
         "setup_s": setup_s, "input_generation_s": gen_s,
         "dirac_apply": {"storage": prec, "gbs": dirac_gbs, "frac_of_measured_hbm": dirac_gbs / hbm,
                         "frac_of_8tbs": dirac_gbs / 8000.0, "us": dirac_s * 1e6},
-        "family_ms_warmup": fam_ms, "roofline": roof, "peak_hbm_gbs": hbm, "peak_kind": peak_kind,
+        "families_warmup": fam, "roofline": roof, "peak_hbm_gbs": hbm, "peak_kind": peak_kind,
         "clocks": clk, "gpu_launches": launches,
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(b_pinned.numel() * 16),
                 "d2h_bytes_per_step": int(z_pinned.numel() * 16)},

@@ -210,11 +210,19 @@ int mg_precondition(mg_ctx* ctx, const void* v, void* z, int prec);
 /* Per-kernel device timing with CUDA events recorded on the context's stream
  * around every launch of the selected kernel families.  mask: 0 = off, 1 = all
  * families, otherwise bit (f + 1) selects family f (0 dirac, 1 Schwarz colour
- * pass, 2 coarse apply, 3 restrict, 4 prolong, 5 BLAS).  mg_get_profile
+ * pass, 2 coarse apply, 3 restrict, 4 prolong, 5 fine-level vector kernels
+ * of the outer solver, 6 vector kernels of the coarse-level solves).  mg_get_profile
  * returns a family's timed launch count and summed milliseconds (it
  * synchronises on the pending events). */
 int mg_set_profiling(mg_ctx* ctx, int mask);
 int mg_get_profile(mg_ctx* ctx, int family, long long* launches, double* ms);
+/* The algorithmic bytes of the timed launches of a level-0 family (every
+ * operand read once and every result written once: fields in storage
+ * precision, the right-hand sides' vectors, P, the coarse operator), summed
+ * like mg_get_profile's milliseconds; their ratio is the family's achieved
+ * bandwidth.  The level-1 Schwarz sweeps and transfers of a three-level
+ * hierarchy add no bytes. */
+int mg_get_profile_bytes(mg_ctx* ctx, int family, double* bytes);
 int mg_reset_profile(mg_ctx* ctx);
 
 /* Number of kernel launches the library has issued in this process. */

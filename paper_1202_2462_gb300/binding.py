@@ -92,6 +92,7 @@ _SIGNATURES = {
     "mg_precondition": (_I, [_VP, _VP, _VP, _I]),
     "mg_set_profiling": (_I, [_VP, _I]),
     "mg_get_profile": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+    "mg_get_profile_bytes": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double)]),
     "mg_reset_profile": (_I, [_VP]),
     "mg_launch_count": (ctypes.c_longlong, []),
 }
@@ -237,6 +238,12 @@ def mg_get_profile(ctx, family):
     return n.value, ms.value
 
 
+def mg_get_profile_bytes(ctx, family):
+    b = ctypes.c_double()
+    _check(lib().mg_get_profile_bytes(ctx, family, ctypes.byref(b)), "mg_get_profile_bytes")
+    return b.value
+
+
 def mg_reset_profile(ctx):
     return _check(lib().mg_reset_profile(ctx), "mg_reset_profile")
 
@@ -253,4 +260,4 @@ def profile_mask(*families):
     return m
 
 
-PROFILE_FAMILIES = {"dirac": 0, "sap": 1, "coarse": 2, "restrict": 3, "prolong": 4, "blas": 5}
+PROFILE_FAMILIES = {"dirac": 0, "sap": 1, "coarse": 2, "restrict": 3, "prolong": 4, "blas": 5, "coarse_blas": 6}

@@ -185,6 +185,7 @@ static int multidot_t(const BVec& b, const void* const* v, int k, const void* w,
 int blas_multidot(int type, const BVec& b, const void* const* v, int k, const void* w, double2* out, int ldo,
                   int mode, double2* out2, double2* partial, cudaStream_t s) {
   if (k <= 0 || b.R <= 0) return MG_OK;
+  count_bytes((double)(k + (v[k - 1] == w ? 0 : 1)) * b.n * b.R * (type == P64 ? 16 : 8));
   if (type == P64) return multidot_t<double2>(b, v, k, w, out, ldo, mode, out2, partial, s);
   if (type == P32) return multidot_t<float2>(b, v, k, w, out, ldo, mode, out2, partial, s);
   return MG_ERR_ARG;
@@ -274,6 +275,7 @@ static int multiaxpy_t(const BVec& b, void* w, const void* const* v, int k, cons
 int blas_multiaxpy(int type, const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc,
                    double sign, cudaStream_t s) {
   if (k <= 0 || b.R <= 0) return MG_OK;
+  count_bytes((double)(k + 2) * b.n * b.R * (type == P64 ? 16 : 8));
   if (type == P64) return multiaxpy_t<double2>(b, w, v, k, coeff, ldc, sign, nullptr, 0, nullptr, s);
   if (type == P32) return multiaxpy_t<float2>(b, w, v, k, coeff, ldc, sign, nullptr, 0, nullptr, s);
   return MG_ERR_ARG;
@@ -282,6 +284,7 @@ int blas_multiaxpy(int type, const BVec& b, void* w, const void* const* v, int k
 int blas_multiaxpy_norm(int type, const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc,
                         double sign, double2* nrm2, int ldn, double2* partial, cudaStream_t s) {
   if (k <= 0 || b.R <= 0) return MG_OK;
+  count_bytes((double)(k + 2) * b.n * b.R * (type == P64 ? 16 : 8));
   if (type == P64) return multiaxpy_t<double2>(b, w, v, k, coeff, ldc, sign, nrm2, ldn, partial, s);
   if (type == P32) return multiaxpy_t<float2>(b, w, v, k, coeff, ldc, sign, nrm2, ldn, partial, s);
   return MG_ERR_ARG;
@@ -318,6 +321,9 @@ int blas_axpby2(int tx, const Scal32& a, const void* x, size_t xs, int ty, const
                 size_t n, int R, cudaStream_t s) {
   if (n == 0 || R == 0) return MG_OK;
   if (R > 32) return MG_ERR_ARG;
+  bool yread = false;
+  for (int r = 0; r < R; ++r) yread = yread || b.v[r].x != 0.0 || b.v[r].y != 0.0;
+  count_bytes((double)n * R * ((tx == P64 ? 16 : 8) + (ty == P64 ? 16 : 8) * (yread ? 2 : 1)));
   const dim3 g = stream_grid(n, R);
   if (tx == P64 && ty == P64) { axpby_kernel<double2, double2><<<g, 256, 0, s>>>(a, (const double2*)x, b, (double2*)y, n, xs, ys); count_launches(1); }
   else if (tx == P32 && ty == P32) { axpby_kernel<float2, float2><<<g, 256, 0, s>>>(a, (const float2*)x, b, (float2*)y, n, xs, ys); count_launches(1); }
@@ -350,6 +356,7 @@ __global__ void normalize_kernel(const T2* __restrict__ x, T2* __restrict__ out,
 
 int blas_normalize(int type, const BVec& b, const void* x, void* out, const double2* nrm2, int ldn, double2* store,
                    int lds, cudaStream_t s) {
+  count_bytes(2.0 * b.n * b.R * (type == P64 ? 16 : 8));
   const dim3 g = stream_grid(b.n, b.R);
   if (type == P64) { normalize_kernel<double2><<<g, 256, 0, s>>>((const double2*)x, (double2*)out, nrm2, ldn, store, lds, b.n, b.wstride); count_launches(1); }
   else if (type == P32) { normalize_kernel<float2><<<g, 256, 0, s>>>((const float2*)x, (float2*)out, nrm2, ldn, store, lds, b.n, b.wstride); count_launches(1); }

@@ -182,4 +182,8 @@ namespace sapmg {
 void set_last_error(const char* msg, const char* file, int line);
 // Count of kernel launches issued by the library (diagnostics).
 void count_launches(int n);
+// Running total of the algorithmic bytes (distinct operands read + results
+// written) of the vector kernels, for their roofline.
+void count_bytes(double bytes);
+long long bytes_counted();
 }

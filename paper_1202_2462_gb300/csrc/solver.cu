@@ -21,6 +21,9 @@ namespace sapmg {
 static thread_local std::string g_err;
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static std::atomic<long long> g_bytes{0};
+void count_bytes(double bytes) { g_bytes.fetch_add((long long)bytes, std::memory_order_relaxed); }
+long long bytes_counted() { return g_bytes.load(std::memory_order_relaxed); }
 void set_last_error(const char* msg, const char* file, int line) {
   g_err = std::string(msg) + " (" + file + ":" + std::to_string(line) + ")";
 }
@@ -35,24 +38,35 @@ static int fail(int code, const std::string& m) {
     if (rc__ < 0) return rc__;  \
   } while (0)
 
-// TRY for a vector-kernel call, timed as the BLAS family when profiling is on
+// TRY for a vector-kernel call, timed as the fine-level (BLAS) or coarse-level
+// (CBLAS) vector family when profiling is on
 #define BLAS(x)                                     \
   do {                                              \
     ProfScope ps__(c->prof, FAM_BLAS, c->s);        \
     int rc__ = (x);                                 \
     if (rc__ < 0) return rc__;                      \
   } while (0)
+#define CBLAS(x)                                    \
+  do {                                              \
+    ProfScope ps__(c->prof, FAM_CBLAS, c->s);       \
+    int rc__ = (x);                                 \
+    if (rc__ < 0) return rc__;                      \
+  } while (0)
 
-enum { FAM_DIRAC = 0, FAM_SAP = 1, FAM_COARSE = 2, FAM_RESTRICT = 3, FAM_PROLONG = 4, FAM_BLAS = 5, FAM_N = 6 };
+enum {
+  FAM_DIRAC = 0, FAM_SAP = 1, FAM_COARSE = 2, FAM_RESTRICT = 3, FAM_PROLONG = 4, FAM_BLAS = 5, FAM_CBLAS = 6,
+  FAM_N = 7
+};
 
 struct Prof {
   bool on = false;
   unsigned mask = 0;   // families timed (bit f = family f)
-  struct Rec { int fam; cudaEvent_t a, b; };
+  struct Rec { int fam; cudaEvent_t a, b; long long bytes; };
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> pending;
   long long launches[FAM_N] = {};
   double ms[FAM_N] = {};
+  double bytes[FAM_N] = {};
   cudaEvent_t get() {
     if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
     cudaEvent_t e;
@@ -66,6 +80,7 @@ struct Prof {
       cudaEventElapsedTime(&t, r.a, r.b);
       ms[r.fam] += t;
       launches[r.fam] += 1;
+      bytes[r.fam] += (double)r.bytes;
       pool.push_back(r.a);
       pool.push_back(r.b);
     }
@@ -82,15 +97,16 @@ struct ProfScope {
   int fam;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
+  long long b0 = 0;
   bool act;
   ProfScope(Prof& p_, int f, cudaStream_t s_) : p(p_), fam(f), s(s_), act(p_.on && ((p_.mask >> f) & 1u)) {
-    if (act) { a = p.get(); cudaEventRecord(a, s); }
+    if (act) { a = p.get(); cudaEventRecord(a, s); b0 = bytes_counted(); }
   }
   ~ProfScope() {
     if (act) {
       cudaEvent_t b = p.get();
       cudaEventRecord(b, s);
-      p.pending.push_back({fam, a, b});
+      p.pending.push_back({fam, a, b, bytes_counted() - b0});
       if (p.pending.size() > 4096) p.drain();
     }
   }
@@ -189,10 +205,18 @@ struct mg_ctx {
 namespace sapmg {
 
 // ------------------------------------------------------------ helpers
+// Algorithmic bytes of the level-0 kernels (each operand read once, each
+// result written once): links (4 x 9 complex) and clover (2 x 36 real) per
+// site in storage precision, spinors (12 complex per site and system).
+static double fields_bytes(int store) { return 72.0 * complex_bytes(store); }
+static double vec_bytes(int prec) { return prec == P64 ? 16.0 : 8.0; }
+
 static int smoother_sweeps(mg_ctx* c, const void* b, void* z, int n_sweeps, int nrhs) {
   for (int it = 0; it < n_sweeps; ++it)
     for (int col = 0; col < 2; ++col) {
       ProfScope ps(c->prof, FAM_SAP, c->s);
+      // one colour: half the sites; b and z read, z written, z read across the block faces
+      count_bytes(0.5 * c->g.V * (nrhs * 4 * 12 * vec_bytes(c->prec) + fields_bytes(c->prec)));
       TRY(launch_sap_colour(c->prec, c->g, z, b, c->Us, c->As, col, c->p.n_mr, nrhs, c->s));
     }
   return MG_OK;
@@ -203,6 +227,7 @@ static int fine_dirac(mg_ctx* c, int prec, void* out, const void* in, int nrhs) 
   const void* A = prec == P64 ? c->A64 : (prec == P32 ? c->A32 : c->As);
   if (!U || !A) return fail(MG_ERR_STATE, "requested precision not set up in this context");
   ProfScope ps(c->prof, FAM_DIRAC, c->s);
+  count_bytes((double)c->g.V * (nrhs * 2 * 12 * vec_bytes(prec) + fields_bytes(prec)));
   return launch_dirac(prec, c->g, out, in, U, A, nrhs, c->s);
 }
 
@@ -214,6 +239,8 @@ static int dot_to(mg_ctx* c, int type, const BVec& b, const void* x, const void*
 // D_c x on a coarse level: the bulk-copy kernel for an FP32 operator, else the generic one.
 static int coarse_apply(mg_ctx* c, CoarseLevel& L, const void* x, void* out, int R) {
   ProfScope ps(c->prof, FAM_COARSE, c->s);
+  count_bytes((double)L.cg.nsites * (9.0 * L.cg.n2 * L.cg.n2 * complex_bytes(L.store) +
+                                     2.0 * R * L.cg.n2 * complex_bytes(c->vt)));
   if (L.store == P32 && c->vt == P32 && c->coarse_tf32 && L.cg.n2 % 8 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
     return launch_coarse_apply_mma(L.cg, L.M, x, out, R, c->dev_err, c->s);
   if (L.store == P32 && c->vt == P32 && L.cg.n2 % 2 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
@@ -248,28 +275,28 @@ static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k, int R) {
   const size_t eb = complex_bytes(vt);
   const BVec bv = bvec(n, R, n);
   auto Vj = [&](int j) { return (void*)((char*)L.V + (size_t)j * R * n * eb); };
-  BLAS(dot_to(c, vt, bv, L.b, L.b, L.beta2, 1));
-  BLAS(blas_normalize(vt, bv, L.b, Vj(0), L.beta2, 1, nullptr, 0, c->s));
+  CBLAS(dot_to(c, vt, bv, L.b, L.b, L.beta2, 1));
+  CBLAS(blas_normalize(vt, bv, L.b, Vj(0), L.beta2, 1, nullptr, 0, c->s));
   std::vector<const void*> vl;
   for (int j = 0; j < k; ++j) {
     TRY(coarse_apply(c, L, Vj(j), L.w, R));
     vl.push_back(Vj(j));
     double2* hcol = L.H + (size_t)j * 33;
-    BLAS(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
+    CBLAS(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
     if (c->coarse_reorth) {
-      BLAS(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
-      BLAS(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 1, L.tmp, c->partial, c->s));
-      BLAS(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
+      CBLAS(blas_multiaxpy(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
+      CBLAS(blas_multidot(vt, bv, vl.data(), j + 1, L.w, hcol, 33 * 33, 1, L.tmp, c->partial, c->s));
+      CBLAS(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, L.tmp, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
                               c->s));
     } else {
-      BLAS(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
+      CBLAS(blas_multiaxpy_norm(vt, bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial,
                               c->s));
     }
-    BLAS(blas_normalize(vt, bv, L.w, Vj(j + 1), L.tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
+    CBLAS(blas_normalize(vt, bv, L.w, Vj(j + 1), L.tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
   }
-  BLAS(blas_hessenberg_solve(L.H, 33, 33 * 33, k, L.beta2, L.y, 33, R, c->s));
+  CBLAS(blas_hessenberg_solve(L.H, 33, 33 * 33, k, L.beta2, L.y, 33, R, c->s));
   SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, (size_t)R * n * eb, c->s));
-  BLAS(blas_multiaxpy(vt, bv, L.x, vl.data(), k, L.y, 33, 1.0, c->s));
+  CBLAS(blas_multiaxpy(vt, bv, L.x, vl.data(), k, L.y, 33, 1.0, c->s));
   return MG_OK;
 }
 
@@ -286,8 +313,8 @@ static int fgmres_fixed1(mg_ctx* c, int k, int R) {
   const BVec bv = bvec(n, R, n);
   auto Vj = [&](int j) { return (void*)((char*)c->f1V + (size_t)j * R * n * eb); };
   auto Zj = [&](int j) { return (void*)((char*)c->f1Z + (size_t)j * R * n * eb); };
-  BLAS(dot_to(c, vt, bv, L.b, L.b, c->f1beta2, 1));
-  BLAS(blas_normalize(vt, bv, L.b, Vj(0), c->f1beta2, 1, nullptr, 0, c->s));
+  CBLAS(dot_to(c, vt, bv, L.b, L.b, c->f1beta2, 1));
+  CBLAS(blas_normalize(vt, bv, L.b, Vj(0), c->f1beta2, 1, nullptr, 0, c->s));
   std::vector<const void*> vl, zl;
   for (int j = 0; j < k; ++j) {
     TRY(cycle1(c, Vj(j), Zj(j), R));
@@ -295,21 +322,21 @@ static int fgmres_fixed1(mg_ctx* c, int k, int R) {
     vl.push_back(Vj(j));
     zl.push_back(Zj(j));
     double2* hcol = c->f1H + (size_t)j * 33;
-    BLAS(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
+    CBLAS(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 0, nullptr, c->partial, c->s));
     if (c->coarse_reorth) {
-      BLAS(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
-      BLAS(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 1, c->f1tmp, c->partial, c->s));
-      BLAS(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, c->f1tmp, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
+      CBLAS(blas_multiaxpy(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->s));
+      CBLAS(blas_multidot(vt, bv, vl.data(), j + 1, c->f1w, hcol, 33 * 33, 1, c->f1tmp, c->partial, c->s));
+      CBLAS(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, c->f1tmp, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
                               c->partial, c->s));
     } else {
-      BLAS(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
+      CBLAS(blas_multiaxpy_norm(vt, bv, c->f1w, vl.data(), j + 1, hcol, 33 * 33, -1.0, c->f1tmp + 40, 33 * 33,
                               c->partial, c->s));
     }
-    BLAS(blas_normalize(vt, bv, c->f1w, Vj(j + 1), c->f1tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
+    CBLAS(blas_normalize(vt, bv, c->f1w, Vj(j + 1), c->f1tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
   }
-  BLAS(blas_hessenberg_solve(c->f1H, 33, 33 * 33, k, c->f1beta2, c->f1y, 33, R, c->s));
+  CBLAS(blas_hessenberg_solve(c->f1H, 33, 33 * 33, k, c->f1beta2, c->f1y, 33, R, c->s));
   SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, (size_t)R * n * eb, c->s));
-  BLAS(blas_multiaxpy(vt, bv, L.x, zl.data(), k, c->f1y, 33, 1.0, c->s));
+  CBLAS(blas_multiaxpy(vt, bv, L.x, zl.data(), k, c->f1y, 33, 1.0, c->s));
   return MG_OK;
 }
 
@@ -353,13 +380,18 @@ static int cycle(mg_ctx* c, const void* v, void* z, int R) {
     SAPMG_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)R * n * complex_bytes(c->vt), c->s));
     return smoother_sweeps(c, v, z, c->p.nu_post, R);
   }
+  // P (N vectors of 12 complex per site), the fine and the coarse vectors
+  const double tbytes = (double)c->g.V * (c->N0 * 12.0 * complex_bytes(c->pv_prec) + R * 12.0 * complex_bytes(c->vt)) +
+                        (double)c->g.nblocks * 2 * c->N0 * R * complex_bytes(c->vt);
   {
     ProfScope ps(c->prof, FAM_RESTRICT, c->s);
+    count_bytes(tbytes);
     TRY(launch_transfer0(true, c->pv_prec, c->g, v, c->c1.b, c->Pv, c->N0, R, c->restrict_tf32, c->s));
   }
   TRY(coarse_solve(c, 1, R));
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
+    count_bytes(tbytes);
     TRY(launch_transfer0(false, c->pv_prec, c->g, c->c1.x, z, c->Pv, c->N0, R, c->restrict_tf32, c->s));
   }
   return smoother_sweeps(c, v, z, c->p.nu_post, R);
@@ -1214,10 +1246,17 @@ int mg_get_profile(mg_ctx* c, int family, long long* launches, double* ms) {
   return MG_OK;
 }
 
+int mg_get_profile_bytes(mg_ctx* c, int family, double* bytes) {
+  if (!c || !bytes || family < 0 || family >= FAM_N) return fail(MG_ERR_ARG, "bad argument");
+  c->prof.drain();
+  *bytes = c->prof.bytes[family];
+  return MG_OK;
+}
+
 int mg_reset_profile(mg_ctx* c) {
   if (!c) return fail(MG_ERR_ARG, "bad argument");
   c->prof.drain();
-  for (int f = 0; f < FAM_N; ++f) { c->prof.launches[f] = 0; c->prof.ms[f] = 0; }
+  for (int f = 0; f < FAM_N; ++f) { c->prof.launches[f] = 0; c->prof.ms[f] = 0; c->prof.bytes[f] = 0; }
   return MG_OK;
 }
 
