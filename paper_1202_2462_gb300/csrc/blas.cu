@@ -430,6 +430,313 @@ __global__ void hessenberg_solve_kernel(const double2* __restrict__ Hall, int ld
   }
 }
 
+// ------------------------------------------------------------ delayed reorthogonalisation
+// One Arnoldi step with classical Gram-Schmidt whose second pass is delayed by
+// one step (low-synchronisation CGS2, Bielich, Langou, Thomas, Swirydowicz,
+// Yamazaki, Boman, Parallel Computing 2022): the previous basis vector u (one
+// pass done) is reorthogonalised in the same sweeps that orthogonalise the new
+// vector w, so each step reads the basis twice instead of four times.
+//   pass 1: A_i = <v_i, u>, B_i = <v_i, w> (i < j), d = <u, u>, c = <u, w>, <w, w>;
+//   coefficients: beta = sqrt(d - sum |A_i|^2), v_j = (u - sum A_i v_i) / beta,
+//                 h_j = (c - sum conj(A_i) B_i) / beta;
+//   pass 2: u <- v_j, w <- w - sum_i B_i v_i - h_j v_j (and both norms).
+
+// A load unit: two FP32 complex numbers (float4) or one FP64 complex (double2).
+template <class T2> struct Unit;
+template <> struct Unit<float2> { typedef float4 V; typedef float R; static constexpr int C = 2; };
+template <> struct Unit<double2> { typedef double2 V; typedef double R; static constexpr int C = 1; };
+
+__device__ __forceinline__ void cdot_acc(const float4& a, const float4& x, float& re, float& im) {
+  re = fmaf(a.x, x.x, fmaf(a.y, x.y, fmaf(a.z, x.z, fmaf(a.w, x.w, re))));
+  im = fmaf(a.x, x.y, fmaf(-a.y, x.x, fmaf(a.z, x.w, fmaf(-a.w, x.z, im))));
+}
+__device__ __forceinline__ void cdot_acc(const double2& a, const double2& x, double& re, double& im) {
+  re = fma(a.x, x.x, fma(a.y, x.y, re));
+  im = fma(a.x, x.y, fma(-a.y, x.x, im));
+}
+__device__ __forceinline__ void caxpy(float cr, float ci, const float4& a, float4& y) {
+  y.x = fmaf(cr, a.x, fmaf(-ci, a.y, y.x));
+  y.y = fmaf(cr, a.y, fmaf(ci, a.x, y.y));
+  y.z = fmaf(cr, a.z, fmaf(-ci, a.w, y.z));
+  y.w = fmaf(cr, a.w, fmaf(ci, a.z, y.w));
+}
+__device__ __forceinline__ void caxpy(double cr, double ci, const double2& a, double2& y) {
+  y.x = fma(cr, a.x, fma(-ci, a.y, y.x));
+  y.y = fma(cr, a.y, fma(ci, a.x, y.y));
+}
+__device__ __forceinline__ float nrm_of(const float4& y) { return y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w; }
+__device__ __forceinline__ double nrm_of(const double2& y) { return y.x * y.x + y.y * y.y; }
+template <class V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+
+constexpr int kDots2Max = 12;      // basis vectors per pass-1 launch
+constexpr int kDots2Slots = 32;    // partial slots per (right-hand side, CTA)
+template <class V> struct PtrsV { const V* p[16]; };
+
+// slots: [i] = <v_i, u>, [K + i] = <v_i, w>, [2K + 0..2] = <u,u>, <u,w>, <w,w> (EXTRA only)
+template <class T2, int K, bool EXTRA>
+__global__ void __launch_bounds__(256) dots2_partial(PtrsV<typename Unit<T2>::V> v,
+                                                     const typename Unit<T2>::V* __restrict__ u,
+                                                     const typename Unit<T2>::V* __restrict__ w, size_t nu,
+                                                     size_t stride, double2* __restrict__ partial) {
+  typedef typename Unit<T2>::V V;
+  typedef typename Unit<T2>::R R;
+  constexpr int NS = 2 * K + (EXTRA ? 3 : 0);
+  const int r = blockIdx.y;
+  const V* ur = u + r * stride;
+  const V* wr = w + r * stride;
+  R re[NS > 0 ? NS : 1], im[NS > 0 ? NS : 1];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) re[q] = im[q] = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += (size_t)gridDim.x * blockDim.x) {
+    V a[K > 0 ? K : 1];
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] = __ldg(v.p[q] + r * stride + i);
+    const V x = __ldg(ur + i);
+    const V y = __ldg(wr + i);
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      cdot_acc(a[q], x, re[q], im[q]);
+      cdot_acc(a[q], y, re[K + q], im[K + q]);
+    }
+    if (EXTRA) {
+      cdot_acc(x, x, re[2 * K], im[2 * K]);
+      cdot_acc(x, y, re[2 * K + 1], im[2 * K + 1]);
+      cdot_acc(y, y, re[2 * K + 2], im[2 * K + 2]);
+    }
+  }
+  __shared__ double red[8][2 * kDots2Slots];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    const R s = warp_sum(re[q]);
+    const R m = warp_sum(im[q]);
+    if (lane == 0) { red[wid][2 * q] = (double)s; red[wid][2 * q + 1] = (double)m; }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < NS) {
+    double s = 0, m = 0;
+    for (int q = 0; q < 8; ++q) { s += red[q][2 * threadIdx.x]; m += red[q][2 * threadIdx.x + 1]; }
+    partial[((size_t)r * gridDim.x + blockIdx.x) * kDots2Slots + threadIdx.x] = make_double2(s, m);
+  }
+}
+
+// Sums the CTAs' slots: A[r*ld + j0 + i], B[r*ld + j0 + i] (i < K), X[r*4 + e].
+__global__ void dots2_finalize(const double2* __restrict__ partial, int ncta, int K, bool extra, double2* A,
+                               double2* B, double2* X, int ld, int j0) {
+  __shared__ double red[8][2];
+  const int r = blockIdx.x;
+  const int ns = 2 * K + (extra ? 3 : 0);
+  for (int q = 0; q < ns; ++q) {
+    double s = 0, m = 0;
+    for (int c = threadIdx.x; c < ncta; c += blockDim.x) {
+      const double2 v = partial[((size_t)r * ncta + c) * kDots2Slots + q];
+      s += v.x;
+      m += v.y;
+    }
+    s = warp_sum(s);
+    m = warp_sum(m);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[wid][0] = s; red[wid][1] = m; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double ss = 0, sm = 0;
+      for (int k = 0; k < 8; ++k) { ss += red[k][0]; sm += red[k][1]; }
+      const double2 o = make_double2(ss, sm);
+      if (q < K) A[(size_t)r * ld + j0 + q] = o;
+      else if (q < 2 * K) B[(size_t)r * ld + j0 + q - K] = o;
+      else X[(size_t)r * 4 + q - 2 * K] = o;
+    }
+    __syncthreads();
+  }
+}
+
+// Per right-hand side (one thread): beta, h_j and the pass-2 coefficients for
+// the vector list [u, w, v_0 .. v_{j-1}]: c1 makes v_j, c2 makes the new w.
+// hcol[0..j] = (B_0 .. B_{j-1}, h_j); acol[0..j] = (A_0 .. A_{j-1}, beta).  A
+// vanishing beta (u in the span of the basis: a zero or invariant direction)
+// gives zero coefficients.
+__global__ void dcgs2_coeff_kernel(int j, const double2* __restrict__ A, const double2* __restrict__ B,
+                                   const double2* __restrict__ X, int ld, double2* c1, double2* c2, int ldc,
+                                   double2* hcol, double2* acol) {
+  if (threadIdx.x != 0) return;
+  const int r = blockIdx.x;
+  const double2* a = A + (size_t)r * ld;
+  const double2* b = B + (size_t)r * ld;
+  const double2* x = X + (size_t)r * 4;
+  double2* o1 = c1 + (size_t)r * ldc;
+  double2* o2 = c2 + (size_t)r * ldc;
+  double2* hc = hcol + (size_t)r * ld;
+  double2* ac = acol + (size_t)r * ld;
+  double na = 0;
+  for (int i = 0; i < j; ++i) na += a[i].x * a[i].x + a[i].y * a[i].y;
+  const double d = x[0].x;
+  const double beta2 = d - na;
+  if (!(beta2 > 1e-24 * d) || !(d > 0)) {
+    for (int i = 0; i < j + 2; ++i) { o1[i] = make_double2(0, 0); o2[i] = make_double2(0, 0); }
+    for (int i = 0; i <= j; ++i) { hc[i] = make_double2(0, 0); ac[i] = make_double2(0, 0); }
+    return;
+  }
+  const double beta = sqrt(beta2), ib = 1.0 / beta;
+  double sr = x[1].x, si = x[1].y;                          // c - sum conj(a_i) b_i
+  for (int i = 0; i < j; ++i) {
+    sr -= a[i].x * b[i].x + a[i].y * b[i].y;
+    si -= a[i].x * b[i].y - a[i].y * b[i].x;
+  }
+  const double hr = sr * ib, hi = si * ib;                  // h_j
+  const double gr = hr * ib, gi = hi * ib;                  // h_j / beta
+  o1[0] = make_double2(ib, 0);
+  o1[1] = make_double2(0, 0);
+  o2[0] = make_double2(-gr, -gi);
+  o2[1] = make_double2(1, 0);
+  for (int i = 0; i < j; ++i) {
+    o1[2 + i] = make_double2(-a[i].x * ib, -a[i].y * ib);
+    // -(b_i - (h_j / beta) a_i)
+    o2[2 + i] = make_double2(-(b[i].x - (gr * a[i].x - gi * a[i].y)), -(b[i].y - (gr * a[i].y + gi * a[i].x)));
+    hc[i] = b[i];
+    ac[i] = a[i];
+  }
+  hc[j] = make_double2(hr, hi);
+  ac[j] = make_double2(beta, 0);
+}
+
+// y1 = (acc ? y1 : 0) + sum c1_q v_q, y2 likewise; y1 and y2 may be v_0, v_1
+// (every element is read before it is written, by the same thread).  With
+// partial != nullptr the CTA writes its parts of ||y1||^2 and ||y2||^2.
+template <class T2, int K>
+__global__ void __launch_bounds__(256) axpy2_kernel(PtrsV<typename Unit<T2>::V> v, const double2* __restrict__ c1,
+                                                    const double2* __restrict__ c2, int ldc, int j0,
+                                                    typename Unit<T2>::V* y1, typename Unit<T2>::V* y2, size_t nu,
+                                                    size_t stride, int acc, double2* __restrict__ partial) {
+  typedef typename Unit<T2>::V V;
+  typedef typename Unit<T2>::R R;
+  __shared__ R cf[4][16];
+  const int r = blockIdx.y;
+  if (threadIdx.x < K) {
+    const double2 p = c1[(size_t)r * ldc + j0 + threadIdx.x], q = c2[(size_t)r * ldc + j0 + threadIdx.x];
+    cf[0][threadIdx.x] = (R)p.x;
+    cf[1][threadIdx.x] = (R)p.y;
+    cf[2][threadIdx.x] = (R)q.x;
+    cf[3][threadIdx.x] = (R)q.y;
+  }
+  __syncthreads();
+  V* o1 = y1 + r * stride;
+  V* o2 = y2 + r * stride;
+  R n1 = 0, n2 = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += (size_t)gridDim.x * blockDim.x) {
+    V a[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] = v.p[q][r * stride + i];
+    V s1 = acc ? o1[i] : vzero<V>();
+    V s2 = acc ? o2[i] : vzero<V>();
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      caxpy(cf[0][q], cf[1][q], a[q], s1);
+      caxpy(cf[2][q], cf[3][q], a[q], s2);
+    }
+    o1[i] = s1;
+    o2[i] = s2;
+    n1 += nrm_of(s1);
+    n2 += nrm_of(s2);
+  }
+  if (partial) {
+    __shared__ double red[8][2];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const R t1 = warp_sum(n1), t2 = warp_sum(n2);
+    if (lane == 0) { red[wid][0] = (double)t1; red[wid][1] = (double)t2; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double sum = 0;
+      for (int q = 0; q < 8; ++q) sum += red[q][threadIdx.x];
+      partial[((size_t)r * gridDim.x + blockIdx.x) * kChunk + threadIdx.x] = make_double2(sum, 0.0);
+    }
+  }
+}
+
+template <class T2>
+static int dcgs2_step_t(const BVec& b, const void* const* v, int j, void* u, void* w, const DcgsWork& ws,
+                        cudaStream_t s) {
+  typedef typename Unit<T2>::V V;
+  constexpr int C = Unit<T2>::C;
+  const size_t nu = b.n / C, stride = b.vstride / C;
+  const int R = b.R;
+  // pass 1: dots of u and w with the basis (chunks of kDots2Max) and with each other
+  const int ncta1 = std::max(1, std::min(reduce_ctas(nu, R), (int)(kPartialDouble2 / kDots2Slots / (size_t)R)));
+  const dim3 g1(ncta1, R);
+  int j0 = 0;
+  do {
+    const int kk = std::min(kDots2Max, j - j0);
+    const bool extra = (j0 == 0);
+    PtrsV<V> p;
+    for (int q = 0; q < 16; ++q) p.p[q] = j > 0 ? (const V*)v[std::max(0, std::min(j0 + q, j - 1))] : (const V*)u;
+#define SAPMG_D2(K)                                                                                          \
+  case K:                                                                                                    \
+    if (extra) { dots2_partial<T2, K, true><<<g1, 256, 0, s>>>(p, (const V*)u, (const V*)w, nu, stride, ws.partial); } \
+    else { dots2_partial<T2, K, false><<<g1, 256, 0, s>>>(p, (const V*)u, (const V*)w, nu, stride, ws.partial); } \
+    count_launches(1);                                                                                       \
+    break;
+    switch (kk) {
+      SAPMG_D2(0) SAPMG_D2(1) SAPMG_D2(2) SAPMG_D2(3) SAPMG_D2(4) SAPMG_D2(5) SAPMG_D2(6)
+      SAPMG_D2(7) SAPMG_D2(8) SAPMG_D2(9) SAPMG_D2(10) SAPMG_D2(11) SAPMG_D2(12)
+      default: return MG_ERR_ARG;
+    }
+#undef SAPMG_D2
+    dots2_finalize<<<R, 256, 0, s>>>(ws.partial, ncta1, kk, extra, ws.A, ws.B, ws.X, ws.ld, j0); count_launches(1);
+    j0 += kk;
+  } while (j0 < j);
+  dcgs2_coeff_kernel<<<R, 32, 0, s>>>(j, ws.A, ws.B, ws.X, ws.ld, ws.c1, ws.c2, ws.ld, ws.hcol, ws.acol);
+  count_launches(1);
+  // pass 2 over the list [u, w, v_0 .. v_{j-1}] in chunks of 16
+  const dim3 g2(reduce_ctas(nu, R), R);
+  const int total = j + 2;
+  for (int q0 = 0; q0 < total; q0 += 16) {
+    const int kk = std::min(16, total - q0);
+    const bool last = q0 + 16 >= total;
+    PtrsV<V> p;
+    for (int q = 0; q < 16; ++q) {
+      const int t = q0 + std::min(q, kk - 1);
+      p.p[q] = (const V*)(t == 0 ? u : (t == 1 ? w : v[t - 2]));
+    }
+    double2* part = last ? ws.partial : nullptr;
+    const int acc = q0 > 0;
+#define SAPMG_A2(K)                                                                                            \
+  case K:                                                                                                      \
+    axpy2_kernel<T2, K><<<g2, 256, 0, s>>>(p, ws.c1, ws.c2, ws.ld, q0, (V*)u, (V*)w, nu, stride, acc, part); \
+    count_launches(1);                                                                                         \
+    break;
+    switch (kk) {
+      SAPMG_A2(1) SAPMG_A2(2) SAPMG_A2(3) SAPMG_A2(4) SAPMG_A2(5) SAPMG_A2(6) SAPMG_A2(7) SAPMG_A2(8)
+      SAPMG_A2(9) SAPMG_A2(10) SAPMG_A2(11) SAPMG_A2(12) SAPMG_A2(13) SAPMG_A2(14) SAPMG_A2(15) SAPMG_A2(16)
+      default: return MG_ERR_ARG;
+    }
+#undef SAPMG_A2
+  }
+  multidot_finalize<<<R, 256, 0, s>>>(ws.partial, (int)g2.x, 2, ws.nrm, ws.ld, 0, nullptr); count_launches(1);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+int blas_dcgs2_step(int type, const BVec& b, const void* const* v, int j, void* u, void* w, const DcgsWork& ws,
+                    cudaStream_t s) {
+  if (b.R <= 0) return MG_OK;
+  if (j < 0 || j + 2 > ws.ld || b.R > 32) return MG_ERR_ARG;
+  // pass 1 reads the j basis vectors, u and w; pass 2 reads them again and writes u and w
+  count_bytes((double)(2 * j + 6) * b.n * b.R * (type == P64 ? 16 : 8));
+  if (type == P32) {
+    bool al = (b.n % 2 == 0) && (b.vstride == b.n) && ((reinterpret_cast<uintptr_t>(u) & 15) == 0) &&
+              ((reinterpret_cast<uintptr_t>(w) & 15) == 0);
+    for (int q = 0; q < j; ++q) al = al && ((reinterpret_cast<uintptr_t>(v[q]) & 15) == 0);
+    if (!al) return MG_ERR_ARG;
+    return dcgs2_step_t<float2>(b, v, j, u, w, ws, s);
+  }
+  if (type == P64) {
+    if (b.vstride != b.n) return MG_ERR_ARG;
+    return dcgs2_step_t<double2>(b, v, j, u, w, ws, s);
+  }
+  return MG_ERR_ARG;
+}
+
 int blas_hessenberg_solve(const double2* H, int ldh, int ldr, int m, const double2* beta2, double2* y, int ldy,
                           int R, cudaStream_t s) {
   if (m > 32) return MG_ERR_ARG;

@@ -37,6 +37,20 @@ int blas_axpby2(int tx, const Scal32& a, const void* x, size_t xs, int ty, const
 // out[r] = x[r] / sqrt(nrm2[r*ldn]); store[r*lds] = sqrt(nrm2[r*ldn]) if store != nullptr.
 int blas_normalize(int type, const BVec& b, const void* x, void* out, const double2* nrm2, int ldn, double2* store,
                    int lds, cudaStream_t s);
+// Work areas of one delayed-reorthogonalisation Arnoldi step (device, each [R][ld]
+// double2 except X = [R][4]): dot products A, B, X, pass-2 coefficients c1, c2,
+// and the results hcol (Hessenberg column: <v_i, w> for i < j, h_j), acol
+// (<v_i, u> for i < j, beta) and nrm (||v_j||^2, ||w_new||^2).
+struct DcgsWork {
+  double2 *A, *B, *X, *c1, *c2, *hcol, *acol, *nrm;
+  int ld;
+  double2* partial;
+};
+// One Arnoldi step with the second Gram-Schmidt pass delayed by one step: u (the
+// last basis vector, one pass done) becomes v_j, w (the operator image of the
+// step) becomes w - sum_{i<=j} <v_i, w> v_i; v = the j finished basis vectors.
+int blas_dcgs2_step(int type, const BVec& b, const void* const* v, int j, void* u, void* w, const DcgsWork& ws,
+                    cudaStream_t s);
 // y[r] = argmin || sqrt(beta2[r]) e1 - H_r y || for (m+1) x m Hessenberg H_r (column-major, ldh; H_r at H + r*ldr).
 int blas_hessenberg_solve(const double2* H, int ldh, int ldr, int m, const double2* beta2, double2* y, int ldy,
                           int R, cudaStream_t s);

@@ -200,86 +200,148 @@ __device__ __forceinline__ void mma_m16n8k8_tf32(float (&d)[4], uint32_t a0, uin
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Operands are staged in shared memory by asynchronous 16-byte copies
+// (cp.async, kRStages-deep ring over K chunks of kRKC complex entries), so
+// every global load is a coalesced 16-byte piece and the fragments come from
+// shared memory.  Rows N..31 of P and R..15 of x stay zero in every stage.
+constexpr int kRKC = 128;
+constexpr int kRStages = 3;
+template <class TV> struct RPad { static constexpr int sp = 132; };           // 4-byte P entries
+template <> struct RPad<float2> { static constexpr int sp = 130; };           // 8-byte P entries
+constexpr int kRSX = 132;                                                      // x row stride (float2)
+
+template <class TV> __device__ __forceinline__ float2 p_ld(const TV* p) {
+  const Cplx<float> v = Io<float, TV>::ldc(p);
+  return make_float2(v.re, v.im);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <class TV>
+__host__ __device__ constexpr size_t restrict_stage_bytes() {
+  return (size_t)32 * RPad<TV>::sp * sizeof(TV) + (size_t)16 * kRSX * sizeof(float2);
+}
+
 template <int NT, class TV>
 __global__ void __launch_bounds__(256) restrict0_mma_kernel(const float2* __restrict__ in, float2* __restrict__ out,
                                                             const TV* __restrict__ Pv, int N, int nrhs,
                                                             int nblocks) {
-  __shared__ float red[8][2][NT][4][32];                       // [warp][M tile][N tile][fragment][lane]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int SP = RPad<TV>::sp;
+  constexpr size_t PB = (size_t)32 * SP * sizeof(TV);
+  constexpr size_t STAGE = restrict_stage_bytes<TV>();
+  auto sP = [&](int st) { return reinterpret_cast<TV*>(smem_raw + st * STAGE); };
+  auto sX = [&](int st) { return reinterpret_cast<float2*>(smem_raw + st * STAGE + PB); };
   const int blk = blockIdx.x >> 1, chi = blockIdx.x & 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, tig = lane & 3;
+  const int g = lane >> 2, tig = lane & 3, p1 = tig & 1;
   const size_t fs = (size_t)nblocks * 12 * 256;
   const size_t off = ((size_t)blk * 12 + 6 * chi) * 256;      // start of the chiral half-block
+  // zero rows of P (>= N) and of x (>= nrhs) in every stage
+  for (int st = 0; st < kRStages; ++st) {
+    TV* P = sP(st);
+    float2* X = sX(st);
+    uint32_t* pz = reinterpret_cast<uint32_t*>(P + N * SP);
+    for (int e = tid; e < (32 - N) * SP * (int)sizeof(TV) / 4; e += 256) pz[e] = 0u;
+    for (int e = tid; e < (16 - nrhs) * kRSX; e += 256) X[nrhs * kRSX + e] = make_float2(0.f, 0.f);
+  }
+  constexpr int PP = kRKC * (int)sizeof(TV) / 16;             // 16-byte pieces per P row chunk
+  constexpr int XP = kRKC * 8 / 16;                           // per x row chunk
+  auto load = [&](int st, int kc0) {
+    TV* P = sP(st);
+    float2* X = sX(st);
+    const int np = N * PP, total = np + nrhs * XP;
+    for (int e = tid; e < total; e += 256) {
+      if (e < np) {
+        const int row = e / PP, pc = e % PP;
+        const TV* src = Pv + ((size_t)(blk * N + row) * 12 + 6 * chi) * 256 + kc0;
+        cp_async16(reinterpret_cast<unsigned char*>(P + row * SP) + pc * 16,
+                   reinterpret_cast<const unsigned char*>(src) + pc * 16);
+      } else {
+        const int f = e - np, row = f / XP, pc = f % XP;
+        const float2* src = in + (size_t)row * fs + off + kc0;
+        cp_async16(reinterpret_cast<unsigned char*>(X + row * kRSX) + pc * 16,
+                   reinterpret_cast<const unsigned char*>(src) + pc * 16);
+      }
+    }
+  };
+  constexpr int NC = 1536 / kRKC;
+#pragma unroll
+  for (int st = 0; st < kRStages - 1; ++st) {
+    load(st, st * kRKC);
+    cp_async_commit();
+  }
   float acc[2][NT][4];
 #pragma unroll
   for (int m = 0; m < 2; ++m)
 #pragma unroll
     for (int q = 0; q < NT; ++q) acc[m][q][0] = acc[m][q][1] = acc[m][q][2] = acc[m][q][3] = 0.f;
-  const int p1 = tig & 1;
-  for (int ks = warp; ks < 384; ks += 8) {                    // 3072 real K over steps of 8
-    const int K1 = ks * 4 + (tig >> 1);                       // complex entry of columns k'0+tig (and +4: K1+2)
-    uint32_t a[2][4];
+  for (int c = 0; c < NC; ++c) {
+    cp_async_wait<kRStages - 2>();
+    __syncthreads();
+    if (c + kRStages - 1 < NC) load((c + kRStages - 1) % kRStages, (c + kRStages - 1) * kRKC);
+    cp_async_commit();
+    const TV* P = sP(c % kRStages);
+    const float2* X = sX(c % kRStages);
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const int r0 = 16 * m + g, r1 = r0 + 8;
-      float v00 = 0.f, v01 = 0.f, v10 = 0.f, v11 = 0.f;
-      if (r0 < N) {
-        const Cplx<float> x = Io<float, TV>::ld(Pv + ((size_t)(blk * N + r0) * 12 + 6 * chi) * 256 + K1);
-        const Cplx<float> y = Io<float, TV>::ld(Pv + ((size_t)(blk * N + r0) * 12 + 6 * chi) * 256 + K1 + 2);
-        v00 = p1 ? x.im : x.re;
-        v01 = p1 ? y.im : y.re;
-      }
-      if (r1 < N) {
-        const Cplx<float> x = Io<float, TV>::ld(Pv + ((size_t)(blk * N + r1) * 12 + 6 * chi) * 256 + K1);
-        const Cplx<float> y = Io<float, TV>::ld(Pv + ((size_t)(blk * N + r1) * 12 + 6 * chi) * 256 + K1 + 2);
-        v10 = p1 ? x.im : x.re;
-        v11 = p1 ? y.im : y.re;
-      }
-      a[m][0] = f32_to_tf32(v00);
-      a[m][1] = f32_to_tf32(v10);
-      a[m][2] = f32_to_tf32(v01);
-      a[m][3] = f32_to_tf32(v11);
-    }
+    for (int i = 0; i < kRKC / 32; ++i) {                     // this warp's k8 steps: warp + 8 i
+      const int K = 4 * (warp + 8 * i) + (tig >> 1);          // complex entry of columns tig (and tig + 4: K + 2)
+      uint32_t a[2][4];
 #pragma unroll
-    for (int q = 0; q < NT; ++q) {
-      const int col = 8 * q + g, r = col >> 1, pc = col & 1;
-      float b0 = 0.f, b1 = 0.f;
-      if (r < nrhs) {
-        const float2 x = in[(size_t)r * fs + off + K1];
-        const float2 y = in[(size_t)r * fs + off + K1 + 2];
+      for (int m = 0; m < 2; ++m) {
+        const int r0 = 16 * m + g, r1 = r0 + 8;
+        const float2 x00 = p_ld(P + r0 * SP + K), x01 = p_ld(P + r0 * SP + K + 2);
+        const float2 x10 = p_ld(P + r1 * SP + K), x11 = p_ld(P + r1 * SP + K + 2);
+        a[m][0] = f32_to_tf32(p1 ? x00.y : x00.x);
+        a[m][1] = f32_to_tf32(p1 ? x10.y : x10.x);
+        a[m][2] = f32_to_tf32(p1 ? x01.y : x01.x);
+        a[m][3] = f32_to_tf32(p1 ? x11.y : x11.x);
+      }
+#pragma unroll
+      for (int q = 0; q < NT; ++q) {
+        const int col = 8 * q + g, r = col >> 1, pc = col & 1;
+        const float2 x = X[r * kRSX + K], y = X[r * kRSX + K + 2];
         // B[2K+p1][2r+pc]: (pc, p1) = (0,0) re, (0,1) im, (1,0) im, (1,1) -re
-        b0 = pc ? (p1 ? -x.x : x.y) : (p1 ? x.y : x.x);
-        b1 = pc ? (p1 ? -y.x : y.y) : (p1 ? y.y : y.x);
-      }
-      const uint32_t tb0 = f32_to_tf32(b0), tb1 = f32_to_tf32(b1);
+        const float b0 = pc ? (p1 ? -x.x : x.y) : (p1 ? x.y : x.x);
+        const float b1 = pc ? (p1 ? -y.x : y.y) : (p1 ? y.y : y.x);
+        const uint32_t tb0 = f32_to_tf32(b0), tb1 = f32_to_tf32(b1);
 #pragma unroll
-      for (int m = 0; m < 2; ++m) mma_m16n8k8_tf32(acc[m][q], a[m][0], a[m][1], a[m][2], a[m][3], tb0, tb1);
+        for (int m = 0; m < 2; ++m) mma_m16n8k8_tf32(acc[m][q], a[m][0], a[m][1], a[m][2], a[m][3], tb0, tb1);
+      }
     }
   }
+  cp_async_wait<0>();
+  __syncthreads();
+  // the warps' partial products, added by warp 0 in a fixed order
+  float* red = reinterpret_cast<float*>(smem_raw);            // [8][2][NT][4][32]
 #pragma unroll
   for (int m = 0; m < 2; ++m)
 #pragma unroll
     for (int q = 0; q < NT; ++q)
 #pragma unroll
-      for (int f = 0; f < 4; ++f) red[warp][m][q][f][lane] = acc[m][q][f];
+      for (int f = 0; f < 4; ++f) red[(((warp * 2 + m) * NT + q) * 4 + f) * 32 + lane] = acc[m][q][f];
   __syncthreads();
-  // warp 0 adds the eight partial products and writes C[k][2r], C[k][2r+1]
   if (warp == 0) {
     const int n2 = 2 * N;
 #pragma unroll
     for (int m = 0; m < 2; ++m)
 #pragma unroll
       for (int q = 0; q < NT; ++q) {
-        float s[4] = {0.f, 0.f, 0.f, 0.f};
+        float sum[4] = {0.f, 0.f, 0.f, 0.f};
         for (int w = 0; w < 8; ++w)
 #pragma unroll
-          for (int f = 0; f < 4; ++f) s[f] += red[w][m][q][f][lane];
+          for (int f = 0; f < 4; ++f) sum[f] += red[(((w * 2 + m) * NT + q) * 4 + f) * 32 + lane];
         const int r = (8 * q + 2 * tig) >> 1;                  // columns 2 tig (re) and 2 tig + 1 (im)
         const int k0 = 16 * m + g, k1 = k0 + 8;
         if (r < nrhs) {
           float2* o = out + (size_t)r * nblocks * n2 + (size_t)blk * n2 + chi * N;
-          if (k0 < N) o[k0] = make_float2(s[0], s[1]);
-          if (k1 < N) o[k1] = make_float2(s[2], s[3]);
+          if (k0 < N) o[k0] = make_float2(sum[0], sum[1]);
+          if (k1 < N) o[k1] = make_float2(sum[2], sum[3]);
         }
       }
   }
@@ -290,10 +352,22 @@ static int transfer0_mrhs(bool restrict_, const Geom& g, const void* in, void* o
                           bool tf32, cudaStream_t s) {
   if (restrict_ && tf32 && nrhs <= 16 && N <= 32) {
     const unsigned grid = (unsigned)(g.nblocks * 2);
-    if (nrhs <= 4) { restrict0_mma_kernel<1, TV><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs, g.nblocks); count_launches(1); }
-    else if (nrhs <= 8) { restrict0_mma_kernel<2, TV><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs, g.nblocks); count_launches(1); }
-    else if (nrhs <= 12) { restrict0_mma_kernel<3, TV><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs, g.nblocks); count_launches(1); }
-    else { restrict0_mma_kernel<4, TV><<<grid, 256, 0, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs, g.nblocks); count_launches(1); }
+    const size_t smem = kRStages * restrict_stage_bytes<TV>();
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(restrict0_mma_kernel<1, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(restrict0_mma_kernel<2, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(restrict0_mma_kernel<3, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(restrict0_mma_kernel<4, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    const float2* xi = (const float2*)in;
+    float2* xo = (float2*)out;
+    const TV* pv = (const TV*)Pv;
+    if (nrhs <= 4) { restrict0_mma_kernel<1, TV><<<grid, 256, smem, s>>>(xi, xo, pv, N, nrhs, g.nblocks); count_launches(1); }
+    else if (nrhs <= 8) { restrict0_mma_kernel<2, TV><<<grid, 256, smem, s>>>(xi, xo, pv, N, nrhs, g.nblocks); count_launches(1); }
+    else if (nrhs <= 12) { restrict0_mma_kernel<3, TV><<<grid, 256, smem, s>>>(xi, xo, pv, N, nrhs, g.nblocks); count_launches(1); }
+    else { restrict0_mma_kernel<4, TV><<<grid, 256, smem, s>>>(xi, xo, pv, N, nrhs, g.nblocks); count_launches(1); }
     SAPMG_CUDA_TRY(cudaGetLastError());
     return MG_OK;
   }

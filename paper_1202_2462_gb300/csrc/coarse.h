@@ -48,8 +48,8 @@ int launch_coarse_export(int prec, const CGeom& c, const void* M, double* out, c
 int launch_coarse_apply_tma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
                             cudaStream_t s);
 // The same stencil with the block products on tensor cores (TF32 inputs, FP32
-// accumulation; n2 % 8 == 0, n2 <= 64).
-int launch_coarse_apply_mma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
+// accumulation; n2 % 8 == 0, n2 <= 64); operator stored in FP32 (P32) or FP16 (P16).
+int launch_coarse_apply_mma(const CGeom& c, int store, const void* M, const void* x, void* out, int nrhs, int* err,
                             cudaStream_t s);
 
 // Intermediate level of a three-level hierarchy (coarse1.cu).

@@ -117,6 +117,7 @@ struct CoarseLevel {
   int store = P64;           // storage precision of M
   void* M64 = nullptr;       // FP64 operator (set-up result, export)
   void* M = nullptr;         // operator used by the solver (== M64 in FP64)
+  void* Mh = nullptr;        // FP16 copy for the tensor-core stencil (mixed form, SAPMG_COARSE_FP16=0: none)
   // fixed-step GMRES workspace for R right-hand sides (vector type = the cycle's)
   void* V = nullptr;         // (kmax + 1) batched vectors, vector j at V + j*R*n
   void* w = nullptr;         // batched [R][n]
@@ -144,6 +145,7 @@ struct mg_ctx {
   int generic_coarse = 0; // use the generic coarse stencil kernel (SAPMG_GENERIC_COARSE=1)
   int coarse_tf32 = 1;    // tensor-core (TF32) coarse stencil in the mixed form (SAPMG_COARSE_TF32=0 disables)
   int restrict_tf32 = 1;  // tensor-core (TF32) multi-RHS restriction in the mixed form (SAPMG_RESTRICT_TF32=0 disables)
+  int coarse_fp16 = 1;    // FP16-stored operator for the tensor-core coarse stencil (SAPMG_COARSE_FP16=0: FP32)
   int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
   double m0 = 0, csw = 0;
   std::vector<void*> allocs;
@@ -178,6 +180,9 @@ struct mg_ctx {
   int ldh = 0;                             // per-RHS stride of the scalar buffers
   double2* hd = nullptr;                   // device scalars [nrhs_max][ldh]
   double2* hh = nullptr;                   // pinned host mirror
+  double2* dcg = nullptr;                  // delayed-reorthogonalisation work [8][nrhs_max][ldh] (device)
+  double2* dch = nullptr;                  // pinned mirror of its hcol, acol, nrm parts [3][nrhs_max][ldh]
+  int outer_dcgs2 = 1;                     // outer Arnoldi with the delayed second pass (SAPMG_DCGS2=0: two passes)
   Prof prof;
 
   void release(void* ptr) {
@@ -198,6 +203,7 @@ struct mg_ctx {
     for (void* q : allocs)
       if (q) cudaFree(q);
     if (hh) cudaFreeHost(hh);
+    if (dch) cudaFreeHost(dch);
   }
   size_t fine_n() const { return (size_t)g.V * 12; }
 };
@@ -239,10 +245,12 @@ static int dot_to(mg_ctx* c, int type, const BVec& b, const void* x, const void*
 // D_c x on a coarse level: the bulk-copy kernel for an FP32 operator, else the generic one.
 static int coarse_apply(mg_ctx* c, CoarseLevel& L, const void* x, void* out, int R) {
   ProfScope ps(c->prof, FAM_COARSE, c->s);
-  count_bytes((double)L.cg.nsites * (9.0 * L.cg.n2 * L.cg.n2 * complex_bytes(L.store) +
+  const bool mma = L.store == P32 && c->vt == P32 && c->coarse_tf32 && L.cg.n2 % 8 == 0 && L.cg.n2 <= 64 &&
+                   !c->generic_coarse;
+  const int store = (mma && L.Mh) ? P16 : L.store;
+  count_bytes((double)L.cg.nsites * (9.0 * L.cg.n2 * L.cg.n2 * complex_bytes(store) +
                                      2.0 * R * L.cg.n2 * complex_bytes(c->vt)));
-  if (L.store == P32 && c->vt == P32 && c->coarse_tf32 && L.cg.n2 % 8 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
-    return launch_coarse_apply_mma(L.cg, L.M, x, out, R, c->dev_err, c->s);
+  if (mma) return launch_coarse_apply_mma(L.cg, store, store == P16 ? L.Mh : L.M, x, out, R, c->dev_err, c->s);
   if (L.store == P32 && c->vt == P32 && L.cg.n2 % 2 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
     return launch_coarse_apply_tma(L.cg, L.M, x, out, R, c->dev_err, c->s);
   return launch_coarse_apply(L.store, L.cg, L.M, x, out, R, c->s);
@@ -397,6 +405,134 @@ static int cycle(mg_ctx* c, const void* v, void* z, int R) {
   return smoother_sweeps(c, v, z, c->p.nu_post, R);
 }
 
+// Least squares min || g0 e1 - H y || for the (n+1) x n upper Hessenberg H
+// (column-major, leading dimension ld) by Givens rotations applied from
+// scratch; returns the residual norm and, if y != nullptr, the solution.
+static double hessenberg_lsq(const std::complex<double>* H, int ld, int n, double g0, std::complex<double>* y) {
+  typedef std::complex<double> cd;
+  std::vector<cd> h(H, H + (size_t)ld * n), g(n + 1, 0.0);
+  g[0] = g0;
+  for (int j = 0; j < n; ++j) {
+    const cd u = h[j + (size_t)j * ld], v = h[j + 1 + (size_t)j * ld];
+    const double na = std::abs(u), nb = std::abs(v), den = std::sqrt(na * na + nb * nb);
+    double cs;
+    cd sn;
+    if (den == 0.0) { cs = 1; sn = 0; }
+    else if (na == 0.0) { cs = 0; sn = 1; }
+    else { cs = na / den; sn = (u / na) * std::conj(v) / den; }
+    for (int k = j; k < n; ++k) {
+      cd& p = h[j + (size_t)k * ld];
+      cd& q = h[j + 1 + (size_t)k * ld];
+      const cd t = cs * p + sn * q;
+      q = -std::conj(sn) * p + cs * q;
+      p = t;
+    }
+    g[j + 1] = -std::conj(sn) * g[j];
+    g[j] = cs * g[j];
+  }
+  if (y) {
+    for (int i = n - 1; i >= 0; --i) {
+      cd acc = g[i];
+      for (int k = i + 1; k < n; ++k) acc -= h[i + (size_t)k * ld] * y[k];
+      const cd d = h[i + (size_t)i * ld];
+      y[i] = std::abs(d) > 0 ? acc / d : 0.0;
+    }
+  }
+  return std::abs(g[n]);
+}
+
+// The same cycle as fgmres_cycle with the delayed second Gram-Schmidt pass
+// (blas_dcgs2_step): step j reorthogonalises v_j and orthogonalises w = A z_j
+// in one dot pass and one update pass over the basis.  The second pass of v_j
+// rewrites column j-1 of the Hessenberg matrix (A z_{j-1} was expanded in the
+// once-orthogonalised v_j); the least-squares problem is re-solved from the
+// stored columns at every step.
+static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r, const std::vector<double>& rnorm,
+                              void* x, const std::vector<double>& abs_tol, int iters_left, std::vector<int>& done,
+                              std::vector<double>& est) {
+  typedef std::complex<double> cd;
+  const size_t n = c->fine_n();
+  const size_t eb = complex_bytes(ft);
+  const int m = std::min(c->m, std::max(1, iters_left));
+  const int ld = c->ldh;
+  const int lh = m + 1;
+  const BVec bv = bvec(n, R, n);
+  auto Vj = [&](int j) { return (void*)((char*)c->V + (size_t)j * R * n * eb); };
+  auto Zj = [&](int j) { return (void*)((char*)c->Z + (size_t)j * R * n * eb); };
+  std::vector<cd> H((size_t)R * lh * m, 0.0);
+  auto Hq = [&](int q, int i, int j) -> cd& { return H[(size_t)q * lh * m + i + (size_t)j * lh]; };
+  std::vector<char> active(R, 0);
+  done.assign(R, 0);
+  est.assign(R, 0.0);
+  Scal32 a = scal_all(0, R), zero = scal_all(0, R);
+  int n_active = 0;
+  for (int q = 0; q < R; ++q) {
+    est[q] = rnorm[q];
+    if (rnorm[q] > 0 && rnorm[q] > abs_tol[q]) { active[q] = 1; ++n_active; a.v[q].x = 1.0 / rnorm[q]; }
+  }
+  if (n_active == 0) return MG_OK;
+  BLAS(blas_axpby2(ft, a, r, n, ft, zero, Vj(0), n, n, R, c->s));
+  const size_t rl = (size_t)R * ld;
+  DcgsWork ws;
+  ws.A = c->dcg;
+  ws.B = c->dcg + rl;
+  ws.X = c->dcg + 2 * rl;
+  ws.c1 = c->dcg + 3 * rl;
+  ws.c2 = c->dcg + 4 * rl;
+  ws.hcol = c->dcg + 5 * rl;
+  ws.acol = c->dcg + 6 * rl;
+  ws.nrm = c->dcg + 7 * rl;
+  ws.ld = ld;
+  ws.partial = c->partial;
+  std::vector<const void*> vl;   // finished basis vectors v_0 .. v_{j-1}
+  for (int j = 0; j < m; ++j) {
+    TRY(cycle(c, Vj(j), Zj(j), R));
+    TRY(fine_dirac(c, aprec, c->w, Zj(j), R));
+    BLAS(blas_dcgs2_step(ft, bv, vl.data(), j, Vj(j), c->w, ws, c->s));
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->dch, ws.hcol, sizeof(double2) * 3 * rl, cudaMemcpyDeviceToHost, c->s));
+    SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+    n_active = 0;
+    for (int q = 0; q < R; ++q) {
+      a.v[q] = make_double2(0, 0);
+      if (!active[q]) continue;
+      const double2* hc = c->dch + (size_t)q * ld;
+      const double2* ac = c->dch + rl + (size_t)q * ld;
+      const double2* nr = c->dch + 2 * rl + (size_t)q * ld;
+      if (j > 0) {
+        const cd hs = Hq(q, j, j - 1);
+        for (int i = 0; i < j; ++i) Hq(q, i, j - 1) += hs * cd(ac[i].x, ac[i].y);
+        Hq(q, j, j - 1) = hs * ac[j].x;
+      }
+      for (int i = 0; i <= j; ++i) Hq(q, i, j) = cd(hc[i].x, hc[i].y);
+      const double hn = std::sqrt(std::max(nr[1].x, 0.0));
+      Hq(q, j + 1, j) = hn;
+      done[q] = j + 1;
+      est[q] = hessenberg_lsq(&Hq(q, 0, 0), lh, j + 1, rnorm[q], nullptr);
+      if (est[q] <= abs_tol[q] || hn == 0.0 || ac[j].x == 0.0) { active[q] = 0; continue; }
+      a.v[q].x = 1.0 / hn;
+      ++n_active;
+    }
+    if (n_active == 0 || j + 1 == m) break;
+    BLAS(blas_axpby2(ft, a, c->w, n, ft, zero, Vj(j + 1), n, n, R, c->s));
+    vl.push_back(Vj(j));
+  }
+  // least squares per system and x += Z y
+  int jmax = 0;
+  for (int q = 0; q < R; ++q) {
+    jmax = std::max(jmax, done[q]);
+    std::vector<cd> y(std::max(done[q], 1));
+    if (done[q] > 0) hessenberg_lsq(&Hq(q, 0, 0), lh, done[q], rnorm[q], y.data());
+    double2* hq = c->hh + (size_t)q * ld;
+    for (int i = 0; i < ld; ++i) hq[i] = i < done[q] ? make_double2(y[i].real(), y[i].imag()) : make_double2(0, 0);
+  }
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hd, c->hh, sizeof(double2) * R * ld, cudaMemcpyHostToDevice, c->s));
+  std::vector<const void*> zl;
+  for (int i = 0; i < jmax; ++i) zl.push_back(Zj(i));
+  BLAS(blas_multiaxpy(ft, bv, x, zl.data(), jmax, c->hd, ld, 1.0, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));   // hh is reused by the next cycle
+  return MG_OK;
+}
+
 // One cycle of flexible GMRES(m) for R systems in lockstep, A e = r from e = x
 // (x updated in place, x += Z y).  r: current residuals (type ft); rnorm[r]
 // their norms (0 = system inactive).  System r stops when its least-squares
@@ -407,6 +543,7 @@ static int cycle(mg_ctx* c, const void* v, void* z, int R) {
 static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, const std::vector<double>& rnorm,
                         void* x, const std::vector<double>& abs_tol, int iters_left, std::vector<int>& done,
                         std::vector<double>& est) {
+  if (c->outer_dcgs2) return fgmres_cycle_dcgs2(c, ft, aprec, R, r, rnorm, x, abs_tol, iters_left, done, est);
   typedef std::complex<double> cd;
   const size_t n = c->fine_n();
   const size_t eb = complex_bytes(ft);
@@ -667,6 +804,11 @@ static int setup_level0(mg_ctx* c) {
     L.M = c->alloc(msz * complex_bytes(c->dc_prec));
     if (!L.M) return fail(MG_ERR_OOM, "coarse operator");
     TRY(launch_convert(P64, L.M64, c->dc_prec, L.M, msz, c->s));
+    if (c->dc_prec == P32 && c->coarse_fp16 && L.cg.n2 % 8 == 0 && L.cg.n2 <= 64) {
+      L.Mh = c->alloc(msz * complex_bytes(P16));
+      if (!L.Mh) return fail(MG_ERR_OOM, "coarse operator");
+      TRY(launch_convert(P64, L.M64, P16, L.Mh, msz, c->s));
+    }
   }
   return MG_OK;
 }
@@ -742,6 +884,11 @@ static int setup_level1(mg_ctx* c) {
     L2.M = c->alloc(msz * complex_bytes(c->dc_prec));
     if (!L2.M) return fail(MG_ERR_OOM, "level-2 operator");
     TRY(launch_convert(P64, L2.M64, c->dc_prec, L2.M, msz, c->s));
+    if (c->dc_prec == P32 && c->coarse_fp16 && L2.cg.n2 % 8 == 0 && L2.cg.n2 <= 64) {
+      L2.Mh = c->alloc(msz * complex_bytes(P16));
+      if (!L2.Mh) return fail(MG_ERR_OOM, "level-2 operator");
+      TRY(launch_convert(P64, L2.M64, P16, L2.Mh, msz, c->s));
+    }
   }
   return MG_OK;
 }
@@ -860,10 +1007,12 @@ static int do_setup(mg_ctx* c, const double* U) {
   c->b64 = c->alloc((size_t)R * n * 16);
   c->e32 = c->vt == P64 ? c->t64 : c->alloc((size_t)R * n * 8);
   c->hd = (double2*)c->alloc(sizeof(double2) * R * c->ldh);
+  c->dcg = (double2*)c->alloc(sizeof(double2) * 8 * R * c->ldh);
   if (!c->partial || !c->zero_f || !c->io_a || !c->io_b || !c->V || !c->Z || !c->w || !c->x64 || !c->r64 ||
-      !c->t64 || !c->b64 || !c->hd || !c->e32)
+      !c->t64 || !c->b64 || !c->hd || !c->e32 || !c->dcg)
     return fail(MG_ERR_OOM, "workspace");
   if (cudaMallocHost((void**)&c->hh, sizeof(double2) * R * c->ldh) != cudaSuccess) return fail(MG_ERR_OOM, "host");
+  if (cudaMallocHost((void**)&c->dch, sizeof(double2) * 3 * R * c->ldh) != cudaSuccess) return fail(MG_ERR_OOM, "host");
   SAPMG_CUDA_TRY(cudaMemsetAsync(c->zero_f, 0, n * eb, c->s));
   if (p.n_levels >= 2) {
     c->N0 = p.n_vec[0];
@@ -959,6 +1108,8 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   c->generic_coarse = std::getenv("SAPMG_GENERIC_COARSE") ? std::atoi(std::getenv("SAPMG_GENERIC_COARSE")) : 0;
   c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
   c->restrict_tf32 = std::getenv("SAPMG_RESTRICT_TF32") ? std::atoi(std::getenv("SAPMG_RESTRICT_TF32")) : 1;
+  c->outer_dcgs2 = std::getenv("SAPMG_DCGS2") ? std::atoi(std::getenv("SAPMG_DCGS2")) : 1;
+  c->coarse_fp16 = std::getenv("SAPMG_COARSE_FP16") ? std::atoi(std::getenv("SAPMG_COARSE_FP16")) : 1;
   c->m0 = m0;
   c->csw = c_sw;
   const int rc = do_setup(c, U);

@@ -224,6 +224,30 @@ def test_solve_reaches_tolerance(field, prec):
     assert info.relres <= 1e-10
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_two_pass_and_delayed_orthogonalisation_agree(field, prec, monkeypatch):
+    """The outer Arnoldi with the delayed second Gram-Schmidt pass (default)
+    and with two passes per step (SAPMG_DCGS2=0) both reach the tolerance under
+    the oracle's D, on four right-hand sides of which one converges early
+    (a multiple of another plus a small change), and give the same solution."""
+    torch = torch_cuda()
+    u, op = field
+    b = synth.random_spinor(DIMS, 44, nvec=4)
+    b[3] = 2.0 * b[0]
+    zs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SAPMG_DCGS2", flag)
+        s = _solver(torch, u, n_levels=2, n_vec=(8,), precision=prec, nrhs_max=4, seed=6, fgmres_m=8)
+        z, info, code = s.solve(dev(torch, b))
+        s.close()
+        assert code == 0
+        z = host(z)
+        for k in range(4):
+            assert np.linalg.norm(b[k] - op.apply(z[k])) <= 1e-10 * np.linalg.norm(b[k]), (flag, k)
+        zs.append(z)
+    assert rel(zs[0], zs[1]) < 1e-7
+
+
 def test_fp64_and_mixed_solutions_agree(field):
     torch = torch_cuda()
     u, op = field
@@ -290,27 +314,38 @@ def test_fp32_coarse_stencil_batched_parity():
     assert rel(host(out), ref) < 2e-6
 
 
-@pytest.mark.parametrize("tf32", [1, 0])
-def test_coarse_stencil_tensor_core_parity(tf32, monkeypatch):
-    """n2 = 16 takes the tensor-core stencil (TF32 inputs, FP32 accumulation):
-    compared with the oracle's stencil on TF32-rounded operator entries and
-    vectors.  With SAPMG_COARSE_TF32=0 the FP32 bulk-copy stencil runs and is
-    compared with FP32-rounded entries."""
+@pytest.mark.parametrize("tf32,fp16", [(1, 1), (1, 0), (0, 0)])
+def test_coarse_stencil_tensor_core_parity(tf32, fp16, monkeypatch):
+    """n2 = 16 takes the tensor-core stencil: with the operator stored in FP16
+    (default) the products are FP16 x FP16 with FP32 accumulation, so the
+    oracle's stencil gets FP16-rounded entries and vectors; with
+    SAPMG_COARSE_FP16=0 the FP32 operator and the vectors enter as TF32.  For
+    13, 7, 3 and 1 right-hand sides (each batch width of the kernel).  With
+    SAPMG_COARSE_TF32=0 the FP32 bulk-copy stencil runs and is compared with
+    FP32-rounded entries."""
     torch = torch_cuda()
     import paper_1202_2462_gb300 as G
     monkeypatch.setenv("SAPMG_COARSE_TF32", str(tf32))
+    monkeypatch.setenv("SAPMG_COARSE_FP16", str(fp16))
     u = synth.random_gauge_field(DIMS, 0.4, 49)
     iv = synth.test_vector_draw(DIMS, 8, 50)
     s = _solver(torch, u, n_levels=2, n_vec=(8,), setup_iters=0, precision="fp32", init_vectors=dev(torch, iv))
     op = WilsonClover(u, M0, CSW)
     c = CoarseOperator(op, Aggregation(DIMS, (4, 4, 4, 4), (4, 3)).build(iv))
-    rnd = _tf32c if tf32 else (lambda a: round_storage(a, "fp32"))
+    if not tf32:
+        rnd_m = rnd_x = lambda a: round_storage(a, "fp32")
+    elif fp16:
+        rnd_m = rnd_x = lambda a: round_storage(a, "fp16")        # FP16 operator and FP16 fragments
+    else:
+        rnd_m = rnd_x = _tf32c
     for name in ("self_", "fwd", "bwd"):
-        setattr(c, name, rnd(getattr(c, name)))
+        setattr(c, name, rnd_m(getattr(c, name)))
     x = synth.random_spinor((2, 2, 2, 2), 51, nvec=13).reshape(13, 2, 2, 2, 2, 12)
     x = np.concatenate([x, x[:, ..., :4] * 0.5], axis=-1).astype(np.complex64)     # 16 dof per site
-    out = torch.zeros((13, 16, 16), dtype=torch.complex64, device="cuda")
-    G.mg_coarse_apply_batch(s.ctx, 1, dev(torch, x), out, G.MG_FP32, 13)
+    xd = dev(torch, x)
+    for nr in (13, 7, 3, 1):
+        out = torch.zeros((nr, 16, 16), dtype=torch.complex64, device="cuda")
+        G.mg_coarse_apply_batch(s.ctx, 1, xd[:nr].contiguous(), out, G.MG_FP32, nr)
+        ref = c.apply(rnd_x(x[:nr].astype(np.complex128))).reshape(nr, 16, 16)
+        assert rel(host(out), ref) < 5e-6, nr
     s.close()
-    ref = c.apply(rnd(x.astype(np.complex128))).reshape(13, 16, 16)
-    assert rel(host(out), ref) < 5e-6
