@@ -366,28 +366,36 @@ int blas_normalize(int type, const BVec& b, const void* x, void* out, const doub
 }
 
 // Least-squares solve of the (m+1) x m Hessenberg system min ||beta e1 - H y||
-// of fixed-step GMRES, one right-hand side per thread block (thread 0): Givens
-// rotations and back substitution.  H for RHS r at H + r*ldr, column-major with
-// leading dimension ldh; beta2[r].x = ||b_r||^2; y[r*ldy + j].  Columns after a
-// zero subdiagonal entry are unused.  m <= 32.
-__global__ void hessenberg_solve_kernel(const double2* __restrict__ Hall, int ldh, int ldr, int m,
-                                        const double2* __restrict__ beta2, double2* __restrict__ yall, int ldy) {
-  if (threadIdx.x != 0) return;
-  const int r = blockIdx.x;
+// of fixed-step GMRES, one warp per right-hand side: H in shared memory, each
+// Givens rotation computed by every lane (same values) and applied to the
+// columns in parallel, back substitution with warp-reduced row sums.  H for
+// RHS r at H + r*ldr, column-major with leading dimension ldh; beta2[r].x =
+// ||b_r||^2; y[r*ldy + j].  Columns after a zero subdiagonal entry are
+// unused.  m <= 32.
+__global__ void __launch_bounds__(32) hessenberg_solve_kernel(const double2* __restrict__ Hall, int ldh, int ldr,
+                                                              int m, const double2* __restrict__ beta2,
+                                                              double2* __restrict__ yall, int ldy) {
+  __shared__ double hr[33 * 32], hi[33 * 32];
+  __shared__ double gr[33], gi[33], yr[32], yi[32];
+  const int r = blockIdx.x, lane = threadIdx.x;
   const double2* Hin = Hall + (size_t)r * ldr;
   double2* y = yall + (size_t)r * ldy;
-  double hr[33 * 32], hi[33 * 32];
-  double gr[33], gi[33];
-  for (int j = 0; j < m; ++j) y[j] = make_double2(0, 0);
   const double beta = sqrt(fmax(beta2[r].x, 0.0));
-  if (beta == 0.0) return;
+  if (beta == 0.0) {
+    for (int j = lane; j < m; j += 32) y[j] = make_double2(0, 0);
+    return;
+  }
   int mm = m;
   for (int j = 0; j < m; ++j)
     if (Hin[(j + 1) + j * ldh].x == 0.0) { mm = j + 1; break; }
-  for (int j = 0; j < mm; ++j)
-    for (int i = 0; i <= j + 1; ++i) { hr[i + j * 33] = Hin[i + j * ldh].x; hi[i + j * 33] = Hin[i + j * ldh].y; }
-  for (int i = 0; i <= mm; ++i) gr[i] = gi[i] = 0;
-  gr[0] = beta;
+  for (int idx = lane; idx < 33 * mm; idx += 32) {
+    const int k = idx / 33, i = idx % 33;
+    const bool in = i <= k + 1;
+    hr[idx] = in ? Hin[i + k * ldh].x : 0.0;
+    hi[idx] = in ? Hin[i + k * ldh].y : 0.0;
+  }
+  for (int i = lane; i <= mm; i += 32) { gr[i] = i == 0 ? beta : 0.0; gi[i] = 0.0; }
+  __syncwarp();
   for (int j = 0; j < mm; ++j) {
     const double ar = hr[j + j * 33], ai = hi[j + j * 33];
     const double br = hr[j + 1 + j * 33], bi = hi[j + 1 + j * 33];
@@ -402,7 +410,8 @@ __global__ void hessenberg_solve_kernel(const double2* __restrict__ Hall, int ld
       sr = (pr * br + pi * bi) / den;
       si = (pi * br - pr * bi) / den;
     }
-    for (int k = j; k < mm; ++k) {                  // rotate rows j, j+1
+    __syncwarp();                                   // every lane has read column j
+    for (int k = j + lane; k < mm; k += 32) {       // rotate rows j, j+1 of column k
       const double xr = hr[j + k * 33], xi = hi[j + k * 33];
       const double zr = hr[j + 1 + k * 33], zi = hi[j + 1 + k * 33];
       hr[j + k * 33] = c * xr + (sr * zr - si * zi);
@@ -410,24 +419,34 @@ __global__ void hessenberg_solve_kernel(const double2* __restrict__ Hall, int ld
       hr[j + 1 + k * 33] = -(sr * xr + si * xi) + c * zr;
       hi[j + 1 + k * 33] = -(sr * xi - si * xr) + c * zi;
     }
-    const double xr = gr[j], xi = gi[j];
-    gr[j] = c * xr;
-    gi[j] = c * xi;
-    gr[j + 1] = -(sr * xr + si * xi);
-    gi[j + 1] = -(sr * xi - si * xr);
+    if (lane == 0) {
+      const double xr = gr[j], xi = gi[j];
+      gr[j] = c * xr;
+      gi[j] = c * xi;
+      gr[j + 1] = -(sr * xr + si * xi);
+      gi[j + 1] = -(sr * xi - si * xr);
+    }
+    __syncwarp();
   }
   for (int i = mm - 1; i >= 0; --i) {
-    double sr = gr[i], si = gi[i];
-    for (int k = i + 1; k < mm; ++k) {
+    double sr = 0, si = 0;
+    for (int k = i + 1 + lane; k < mm; k += 32) {
       const double hr_ = hr[i + k * 33], hi_ = hi[i + k * 33];
-      const double yr = y[k].x, yi = y[k].y;
-      sr -= hr_ * yr - hi_ * yi;
-      si -= hr_ * yi + hi_ * yr;
+      sr += hr_ * yr[k] - hi_ * yi[k];
+      si += hr_ * yi[k] + hi_ * yr[k];
     }
-    const double dr = hr[i + i * 33], di = hi[i + i * 33];
-    const double d2 = dr * dr + di * di;
-    y[i] = d2 > 0 ? make_double2((sr * dr + si * di) / d2, (si * dr - sr * di) / d2) : make_double2(0, 0);
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) {
+      const double tr = gr[i] - sr, ti = gi[i] - si;
+      const double dr = hr[i + i * 33], di = hi[i + i * 33];
+      const double d2 = dr * dr + di * di;
+      yr[i] = d2 > 0 ? (tr * dr + ti * di) / d2 : 0.0;
+      yi[i] = d2 > 0 ? (ti * dr - tr * di) / d2 : 0.0;
+    }
+    __syncwarp();
   }
+  for (int j = lane; j < m; j += 32) y[j] = j < mm ? make_double2(yr[j], yi[j]) : make_double2(0, 0);
 }
 
 // ------------------------------------------------------------ delayed reorthogonalisation

@@ -12,51 +12,10 @@
 // the host turns into MG_ERR_TIMEOUT.
 #include "internal.h"
 #include "coarse.h"
+#include "async.cuh"
 
 namespace sapmg {
 
-namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: true when the phase completed, false after kMaxSpins tries.
-constexpr int kMaxSpins = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kMaxSpins; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-}  // namespace
 
 template <int RB, int APT>
 __global__ void __launch_bounds__(256) coarse_apply_tma_kernel(const float2* __restrict__ M,
@@ -215,11 +174,13 @@ __device__ __forceinline__ float2 tile_ld(const __half2* t, int k) { return __ha
 
 // Pipeline: a ring of kStages stages, each holding one operator block (FP32
 // or FP16 entries; FP16 converts exactly to TF32) and the RB neighbour
-// vectors it multiplies.  One thread issues all bulk copies of block t+3
-// (block + RB vector rows, one transaction count on that stage's mbarrier)
-// while the warps multiply block t; a block's stage is refilled only after the
-// CTA-wide barrier that ends its use.
-constexpr int kStages = 4;
+// vectors it multiplies.  One thread issues all bulk copies of block
+// t + kStages - 1 (block + RB vector rows, one transaction count on that
+// stage's mbarrier) while the warps multiply block t; a block's stage is
+// refilled only after the CTA-wide barrier that ends its use.  Two stages keep
+// a CTA's shared memory small, so that many CTAs share an SM (measured faster
+// than deeper rings with fewer CTAs).
+constexpr int kStages = 2;
 
 template <int RB, class TM>
 __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restrict__ M,
@@ -366,14 +327,14 @@ __device__ __forceinline__ uint32_t pack16(float2 v) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int RB>
+template <int RB, int N2, int ST>
 __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* __restrict__ M,
                                                                  const float2* __restrict__ x,
                                                                  float2* __restrict__ out, CGeom c, int r0,
                                                                  int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[kStages];
-  const int n2 = c.n2;
+  __shared__ __align__(8) uint64_t bar[ST];
+  const int n2 = N2 > 0 ? N2 : c.n2;                         // N2 > 0: block size fixed at compile time
   const int xst = n2 + 4;                                     // padded row stride (conflict-free fragment loads)
   const int tile = n2 * n2;
   const uint32_t tile_bytes = (uint32_t)tile * sizeof(__half2);
@@ -388,10 +349,10 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
   const int nsite_cta = (c.nsites - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int T = 9 * nsite_cta;
   if (T <= 0) return;
-  for (int st = 0; st < kStages; ++st)
+  for (int st = 0; st < ST; ++st)
     for (int e = tid; e < (16 - RB) * xst; e += blockDim.x) stage_x(st)[RB * xst + e] = make_float2(0.f, 0.f);
   if (tid == 0) {
-    for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
+    for (int st = 0; st < ST; ++st) mbar_init(&bar[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -405,7 +366,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
     return site + (((xc + step + c.L[mu]) % c.L[mu]) - xc) * stride;
   };
   auto issue = [&](int t) {
-    const int st = t % kStages;
+    const int st = t % ST;
     const int site = site_of(t), d = t % 9;
     uint64_t* b = &bar[st];
     mbar_expect_tx(b, tile_bytes + RB * row_bytes);
@@ -417,7 +378,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
   };
   if (tid == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int t = 0; t < kStages - 1 && t < T; ++t) issue(t);
+    for (int t = 0; t < ST - 1 && t < T; ++t) issue(t);
   }
   const int m0 = warp * 16;
   const int i0 = (m0 >> 1) + (g >> 1), a = g & 1;            // output rows i0 (fragment row g) and i0 + 4 (g + 8)
@@ -430,12 +391,12 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
 #pragma unroll
       for (int q = 0; q < 2; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
     }
-    if (tid == 0 && t + kStages - 1 < T) {
+    if (tid == 0 && t + ST - 1 < T) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(t + kStages - 1);
+      issue(t + ST - 1);
     }
-    const int st = t % kStages;
-    const bool waited = mbar_wait(&bar[st], (uint32_t)((t / kStages) & 1));
+    const int st = t % ST;
+    const bool waited = mbar_wait(&bar[st], (uint32_t)((t / ST) & 1));
     if (__syncthreads_or(!waited)) {
       tfail = t;
       break;
@@ -443,6 +404,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
     const uint32_t* mt = stage_tile(st);
     const float2* xs = stage_x(st);
     if (m0 < 2 * n2) {
+#pragma unroll
       for (int k0 = 0; k0 < 2 * n2; k0 += 16) {
         const int j = (k0 >> 1) + tig;                        // input columns j (k pair 2 tig) and j + 4
         const uint32_t a0 = emb16(mt[j * n2 + i0], a);
@@ -476,26 +438,38 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
   if (tfail >= 0) {
     if (tid == 0) {
       atomicExch(err, 1);
-      for (int u = tfail; u < T && u < tfail + kStages - 1; ++u) mbar_wait(&bar[u % kStages], (uint32_t)((u / kStages) & 1));
+      for (int u = tfail; u < T && u < tfail + ST - 1; ++u) mbar_wait(&bar[u % ST], (uint32_t)((u / ST) & 1));
     }
     __syncthreads();
   }
 }
 
-template <int RB>
-static void launch_mma16(const CGeom& c, const __half2* M, const float2* x, float2* out, int r0, int* err,
-                         cudaStream_t s) {
+template <int RB, int N2, int ST>
+static void launch_mma16_t(const CGeom& c, const __half2* M, const float2* x, float2* out, int r0, int* err,
+                           cudaStream_t s) {
   const size_t stage = (size_t)c.n2 * c.n2 * sizeof(__half2) + (size_t)16 * (c.n2 + 4) * sizeof(float2);
-  const size_t smem = kStages * stage;
+  const size_t smem = ST * stage;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(coarse_apply_mma16_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(coarse_apply_mma16_kernel<RB, N2, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     attr = true;
   }
   const int threads = 32 * (c.n2 / 8);
   const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / (smem + 1024)));
   const int grid = std::min(c.nsites, 152 * per_sm);
-  coarse_apply_mma16_kernel<RB><<<grid, threads, smem, s>>>(M, x, out, c, r0, err); count_launches(1);
+  coarse_apply_mma16_kernel<RB, N2, ST><<<grid, threads, smem, s>>>(M, x, out, c, r0, err); count_launches(1);
+}
+
+// Two stages (one block in flight while the previous is multiplied) keep the
+// shared memory per CTA small enough for eight CTAs per SM, which measured
+// faster than deeper rings with fewer CTAs; 2N = 40 has a specialised
+// instance with the k loop unrolled.
+template <int RB>
+static void launch_mma16(const CGeom& c, const __half2* M, const float2* x, float2* out, int r0, int* err,
+                         cudaStream_t s) {
+  if (c.n2 == 40) launch_mma16_t<RB, 40, 2>(c, M, x, out, r0, err, s);
+  else launch_mma16_t<RB, 0, 2>(c, M, x, out, r0, err, s);
 }
 
 template <int RB, class TM>

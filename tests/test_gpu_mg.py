@@ -314,6 +314,31 @@ def test_fp32_coarse_stencil_batched_parity():
     assert rel(host(out), ref) < 2e-6
 
 
+def test_coarse_stencil_fp16_n2_40_parity():
+    """The tensor-core stencil specialised for 2N = 40 (N = 20 test vectors, the
+    benchmark's size), against the oracle's stencil on FP16-rounded entries and
+    vectors, for 12 and 5 right-hand sides."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u = synth.random_gauge_field(DIMS, 0.4, 56)
+    iv = synth.test_vector_draw(DIMS, 20, 57)
+    s = _solver(torch, u, n_levels=2, n_vec=(20,), setup_iters=0, precision="bf16", init_vectors=dev(torch, iv),
+                nrhs_max=12)
+    op = WilsonClover(u, M0, CSW)
+    c = CoarseOperator(op, Aggregation(DIMS, (4, 4, 4, 4), (4, 3)).build(iv))
+    for name in ("self_", "fwd", "bwd"):
+        setattr(c, name, round_storage(getattr(c, name), "fp16"))
+    x = synth.random_spinor((2, 2, 2, 2), 58, nvec=12).reshape(12, 2, 2, 2, 2, 12)
+    x = np.concatenate([x, 0.5 * x, -x, x[..., :4]], axis=-1).astype(np.complex64)   # 40 dof per site
+    xd = dev(torch, x)
+    for nr in (12, 5):
+        out = torch.zeros((nr, 16, 40), dtype=torch.complex64, device="cuda")
+        G.mg_coarse_apply_batch(s.ctx, 1, xd[:nr].contiguous(), out, G.MG_FP32, nr)
+        ref = c.apply(round_storage(x[:nr].astype(np.complex128), "fp16")).reshape(nr, 16, 40)
+        assert rel(host(out), ref) < 5e-6, nr
+    s.close()
+
+
 @pytest.mark.parametrize("tf32,fp16", [(1, 1), (1, 0), (0, 0)])
 def test_coarse_stencil_tensor_core_parity(tf32, fp16, monkeypatch):
     """n2 = 16 takes the tensor-core stencil: with the operator stored in FP16
