@@ -756,6 +756,216 @@ int blas_dcgs2_step(int type, const BVec& b, const void* const* v, int j, void* 
   return MG_ERR_ARG;
 }
 
+// ------------------------------------------------------------ FP16 basis
+// The finished basis vectors of the mixed form's outer Arnoldi may be kept in
+// FP16, scaled by kBasisScale = 2^10 (a unit vector's entries stay below 1, so
+// the scaled values stay in FP16's normal range and the scaling is exact).
+// Eight bytes = two complex numbers per load unit.
+constexpr float kBasisScale = 1024.f;
+
+__device__ __forceinline__ float4 h4_to_f4(uint2 u) {
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  constexpr float is = 1.f / kBasisScale;
+  return make_float4(a.x * is, a.y * is, b.x * is, b.y * is);
+}
+
+__device__ __forceinline__ uint2 f4_to_h4(float4 v) {
+  const __half2 a = __floats2half2_rn(v.x * kBasisScale, v.y * kBasisScale);
+  const __half2 b = __floats2half2_rn(v.z * kBasisScale, v.w * kBasisScale);
+  uint2 u;
+  u.x = *reinterpret_cast<const unsigned int*>(&a);
+  u.y = *reinterpret_cast<const unsigned int*>(&b);
+  return u;
+}
+
+// pass 1 with an FP16 basis: slots as dots2_partial
+template <int K, bool EXTRA>
+__global__ void __launch_bounds__(256) dots2h_partial(PtrsV<uint2> v, const float4* __restrict__ u,
+                                                      const float4* __restrict__ w, size_t nu, size_t stride,
+                                                      double2* __restrict__ partial) {
+  constexpr int NS = 2 * K + (EXTRA ? 3 : 0);
+  const int r = blockIdx.y;
+  const float4* ur = u + r * stride;
+  const float4* wr = w + r * stride;
+  float re[NS > 0 ? NS : 1], im[NS > 0 ? NS : 1];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) re[q] = im[q] = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += (size_t)gridDim.x * blockDim.x) {
+    uint2 a[K > 0 ? K : 1];
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] = __ldg(v.p[q] + r * stride + i);
+    const float4 x = __ldg(ur + i);
+    const float4 y = __ldg(wr + i);
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const float4 av = h4_to_f4(a[q]);
+      cdot_acc(av, x, re[q], im[q]);
+      cdot_acc(av, y, re[K + q], im[K + q]);
+    }
+    if (EXTRA) {
+      cdot_acc(x, x, re[2 * K], im[2 * K]);
+      cdot_acc(x, y, re[2 * K + 1], im[2 * K + 1]);
+      cdot_acc(y, y, re[2 * K + 2], im[2 * K + 2]);
+    }
+  }
+  __shared__ double red[8][2 * kDots2Slots];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    const float a = warp_sum(re[q]);
+    const float b = warp_sum(im[q]);
+    if (lane == 0) { red[wid][2 * q] = (double)a; red[wid][2 * q + 1] = (double)b; }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < NS) {
+    double a = 0, b = 0;
+    for (int q = 0; q < 8; ++q) { a += red[q][2 * threadIdx.x]; b += red[q][2 * threadIdx.x + 1]; }
+    partial[((size_t)r * gridDim.x + blockIdx.x) * kDots2Slots + threadIdx.x] = make_double2(a, b);
+  }
+}
+
+// pass 2 with an FP16 basis.  Coefficient q of c1/c2 belongs to [u, w, v_0, ...].
+// first: y1 = c1_u u + c1_w w + sum, y2 likewise; otherwise y1 += sum (y1 kept
+// in u), y2 += sum (in w).  vout != nullptr (last chunk): v_j = y1 is also
+// written to the FP16 basis; partial: ||y1||^2, ||y2||^2.
+template <int K>
+__global__ void __launch_bounds__(256) axpy2h_kernel(PtrsV<uint2> v, const double2* __restrict__ c1,
+                                                     const double2* __restrict__ c2, int ldc, int q0, float4* u,
+                                                     float4* w, uint2* __restrict__ vout, size_t nu, size_t stride,
+                                                     int first, double2* __restrict__ partial) {
+  __shared__ float cf[4][18];
+  const int r = blockIdx.y;
+  if ((int)threadIdx.x < K + 2) {
+    const int q = threadIdx.x;                       // 0, 1: u, w (first chunk); 2..: basis entries
+    const int ci = q < 2 ? q : 2 + q0 + (q - 2);
+    const double2 p = c1[(size_t)r * ldc + ci], t = c2[(size_t)r * ldc + ci];
+    cf[0][q] = (float)p.x;
+    cf[1][q] = (float)p.y;
+    cf[2][q] = (float)t.x;
+    cf[3][q] = (float)t.y;
+  }
+  __syncthreads();
+  float4* o1 = u + r * stride;
+  float4* o2 = w + r * stride;
+  uint2* ov = vout ? vout + r * stride : nullptr;
+  float n1 = 0.f, n2 = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += (size_t)gridDim.x * blockDim.x) {
+    uint2 a[K > 0 ? K : 1];
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] = __ldg(v.p[q] + r * stride + i);
+    const float4 uu = o1[i], ww = o2[i];
+    float4 s1, s2;
+    if (first) {
+      s1 = vzero<float4>();
+      s2 = vzero<float4>();
+      caxpy(cf[0][0], cf[1][0], uu, s1);
+      caxpy(cf[0][1], cf[1][1], ww, s1);
+      caxpy(cf[2][0], cf[3][0], uu, s2);
+      caxpy(cf[2][1], cf[3][1], ww, s2);
+    } else {
+      s1 = uu;
+      s2 = ww;
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const float4 av = h4_to_f4(a[q]);
+      caxpy(cf[0][2 + q], cf[1][2 + q], av, s1);
+      caxpy(cf[2][2 + q], cf[3][2 + q], av, s2);
+    }
+    o1[i] = s1;
+    o2[i] = s2;
+    if (ov) ov[i] = f4_to_h4(s1);
+    n1 += nrm_of(s1);
+    n2 += nrm_of(s2);
+  }
+  if (partial) {
+    __shared__ double red[8][2];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float t1 = warp_sum(n1), t2 = warp_sum(n2);
+    if (lane == 0) { red[wid][0] = (double)t1; red[wid][1] = (double)t2; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double sum = 0;
+      for (int q = 0; q < 8; ++q) sum += red[q][threadIdx.x];
+      partial[((size_t)r * gridDim.x + blockIdx.x) * kChunk + threadIdx.x] = make_double2(sum, 0.0);
+    }
+  }
+}
+
+int blas_dcgs2_step_h(const BVec& b, const void* const* vh, int j, void* u, void* w, void* vout, const DcgsWork& ws,
+                      cudaStream_t s) {
+  if (b.R <= 0) return MG_OK;
+  if (j < 0 || j + 2 > ws.ld || b.R > 32 || b.n % 2 != 0 || b.vstride != b.n) return MG_ERR_ARG;
+  bool al = ((reinterpret_cast<uintptr_t>(u) & 15) == 0) && ((reinterpret_cast<uintptr_t>(w) & 15) == 0) &&
+            ((reinterpret_cast<uintptr_t>(vout) & 7) == 0);
+  for (int q = 0; q < j; ++q) al = al && ((reinterpret_cast<uintptr_t>(vh[q]) & 7) == 0);
+  if (!al) return MG_ERR_ARG;
+  // pass 1: j FP16 basis vectors + u, w; pass 2: the same + u, w written + v_j in FP16
+  count_bytes(((double)2 * j * 4 + 6 * 8 + 4) * b.n * b.R);
+  const size_t nu = b.n / 2, stride = b.vstride / 2;
+  const int R = b.R;
+  const int ncta1 = std::max(1, std::min(reduce_ctas(nu, R), (int)(kPartialDouble2 / kDots2Slots / (size_t)R)));
+  const dim3 g1(ncta1, R);
+  const float4* uf = (const float4*)u;
+  const float4* wf = (const float4*)w;
+  int j0 = 0;
+  do {
+    const int kk = std::min(kDots2Max, j - j0);
+    const bool extra = (j0 == 0);
+    PtrsV<uint2> p;
+    for (int q = 0; q < 16; ++q) p.p[q] = j > 0 ? (const uint2*)vh[std::max(0, std::min(j0 + q, j - 1))] : (const uint2*)vout;
+#define SAPMG_D2H(K)                                                                                              \
+  case K:                                                                                                         \
+    if (extra) { dots2h_partial<K, true><<<g1, 256, 0, s>>>(p, uf, wf, nu, stride, ws.partial); }                \
+    else { dots2h_partial<K, false><<<g1, 256, 0, s>>>(p, uf, wf, nu, stride, ws.partial); }                     \
+    count_launches(1);                                                                                            \
+    break;
+    switch (kk) {
+      SAPMG_D2H(0) SAPMG_D2H(1) SAPMG_D2H(2) SAPMG_D2H(3) SAPMG_D2H(4) SAPMG_D2H(5) SAPMG_D2H(6)
+      SAPMG_D2H(7) SAPMG_D2H(8) SAPMG_D2H(9) SAPMG_D2H(10) SAPMG_D2H(11) SAPMG_D2H(12)
+      default: return MG_ERR_ARG;
+    }
+#undef SAPMG_D2H
+    dots2_finalize<<<R, 256, 0, s>>>(ws.partial, ncta1, kk, extra, ws.A, ws.B, ws.X, ws.ld, j0); count_launches(1);
+    j0 += kk;
+  } while (j0 < j);
+  dcgs2_coeff_kernel<<<R, 32, 0, s>>>(j, ws.A, ws.B, ws.X, ws.ld, ws.c1, ws.c2, ws.ld, ws.hcol, ws.acol);
+  count_launches(1);
+  const dim3 g2(reduce_ctas(nu, R), R);
+  int q0 = 0;
+  bool first = true;
+  do {
+    const int kk = std::min(16, j - q0);
+    const bool last = q0 + kk >= j;
+    PtrsV<uint2> p;
+    for (int q = 0; q < 16; ++q) p.p[q] = j > 0 ? (const uint2*)vh[std::max(0, std::min(q0 + q, j - 1))] : (const uint2*)vout;
+    double2* part = last ? ws.partial : nullptr;
+    uint2* vo = last ? (uint2*)vout : nullptr;
+#define SAPMG_A2H(K)                                                                                                \
+  case K:                                                                                                           \
+    axpy2h_kernel<K><<<g2, 256, 0, s>>>(p, ws.c1, ws.c2, ws.ld, q0, (float4*)u, (float4*)w, vo, nu, stride, first, \
+                                        part);                                                                      \
+    count_launches(1);                                                                                              \
+    break;
+    switch (kk) {
+      SAPMG_A2H(0) SAPMG_A2H(1) SAPMG_A2H(2) SAPMG_A2H(3) SAPMG_A2H(4) SAPMG_A2H(5) SAPMG_A2H(6) SAPMG_A2H(7)
+      SAPMG_A2H(8) SAPMG_A2H(9) SAPMG_A2H(10) SAPMG_A2H(11) SAPMG_A2H(12) SAPMG_A2H(13) SAPMG_A2H(14)
+      SAPMG_A2H(15) SAPMG_A2H(16)
+      default: return MG_ERR_ARG;
+    }
+#undef SAPMG_A2H
+    q0 += kk;
+    first = false;
+  } while (q0 < j);
+  multidot_finalize<<<R, 256, 0, s>>>(ws.partial, (int)g2.x, 2, ws.nrm, ws.ld, 0, nullptr); count_launches(1);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+// x[r] += sum_j coeff[r*ldc + j] z_j[r] is blas_multiaxpy; with an FP16 basis the
+// outer solve needs no other FP16 kernel (the solution uses the FP32 Z vectors).
+
 int blas_hessenberg_solve(const double2* H, int ldh, int ldr, int m, const double2* beta2, double2* y, int ldy,
                           int R, cudaStream_t s) {
   if (m > 32) return MG_ERR_ARG;

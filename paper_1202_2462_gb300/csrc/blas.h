@@ -51,6 +51,11 @@ struct DcgsWork {
 // step) becomes w - sum_{i<=j} <v_i, w> v_i; v = the j finished basis vectors.
 int blas_dcgs2_step(int type, const BVec& b, const void* const* v, int j, void* u, void* w, const DcgsWork& ws,
                     cudaStream_t s);
+// The same step (FP32 u and w) with the finished basis vectors stored in FP16,
+// scaled by 2^10: vh = v_0 .. v_{j-1}; the new v_j is written to vout in the
+// same format (and stays in u in FP32).
+int blas_dcgs2_step_h(const BVec& b, const void* const* vh, int j, void* u, void* w, void* vout, const DcgsWork& ws,
+                      cudaStream_t s);
 // y[r] = argmin || sqrt(beta2[r]) e1 - H_r y || for (m+1) x m Hessenberg H_r (column-major, ldh; H_r at H + r*ldr).
 int blas_hessenberg_solve(const double2* H, int ldh, int ldr, int m, const double2* beta2, double2* y, int ldy,
                           int R, cudaStream_t s);

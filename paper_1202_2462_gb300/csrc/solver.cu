@@ -183,6 +183,8 @@ struct mg_ctx {
   double2* dcg = nullptr;                  // delayed-reorthogonalisation work [8][nrhs_max][ldh] (device)
   double2* dch = nullptr;                  // pinned mirror of its hcol, acol, nrm parts [3][nrhs_max][ldh]
   int outer_dcgs2 = 1;                     // outer Arnoldi with the delayed second pass (SAPMG_DCGS2=0: two passes)
+  int outer_half = 0;                      // mixed form: finished outer basis vectors in FP16 (SAPMG_OUTER_FP16=0: FP32)
+  void* Vh = nullptr;                      // the FP16 basis [m][nrhs_max][fine field] (V then holds only the newest vector)
   Prof prof;
 
   void release(void* ptr) {
@@ -471,7 +473,12 @@ static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r
     if (rnorm[q] > 0 && rnorm[q] > abs_tol[q]) { active[q] = 1; ++n_active; a.v[q].x = 1.0 / rnorm[q]; }
   }
   if (n_active == 0) return MG_OK;
-  BLAS(blas_axpby2(ft, a, r, n, ft, zero, Vj(0), n, n, R, c->s));
+  // with an FP16 basis the newest (once-orthogonalised) vector lives in V in
+  // FP32 and the finished ones in Vh
+  const bool hb = c->outer_half != 0;
+  auto Uj = [&](int j) { return hb ? c->V : Vj(j); };
+  auto Vhj = [&](int j) { return (void*)((char*)c->Vh + (size_t)j * R * n * 4); };
+  BLAS(blas_axpby2(ft, a, r, n, ft, zero, Uj(0), n, n, R, c->s));
   const size_t rl = (size_t)R * ld;
   DcgsWork ws;
   ws.A = c->dcg;
@@ -486,9 +493,10 @@ static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r
   ws.partial = c->partial;
   std::vector<const void*> vl;   // finished basis vectors v_0 .. v_{j-1}
   for (int j = 0; j < m; ++j) {
-    TRY(cycle(c, Vj(j), Zj(j), R));
+    TRY(cycle(c, Uj(j), Zj(j), R));
     TRY(fine_dirac(c, aprec, c->w, Zj(j), R));
-    BLAS(blas_dcgs2_step(ft, bv, vl.data(), j, Vj(j), c->w, ws, c->s));
+    if (hb) BLAS(blas_dcgs2_step_h(bv, vl.data(), j, Uj(j), c->w, Vhj(j), ws, c->s));
+    else BLAS(blas_dcgs2_step(ft, bv, vl.data(), j, Vj(j), c->w, ws, c->s));
     SAPMG_CUDA_TRY(cudaMemcpyAsync(c->dch, ws.hcol, sizeof(double2) * 3 * rl, cudaMemcpyDeviceToHost, c->s));
     SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
     n_active = 0;
@@ -513,8 +521,8 @@ static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r
       ++n_active;
     }
     if (n_active == 0 || j + 1 == m) break;
-    BLAS(blas_axpby2(ft, a, c->w, n, ft, zero, Vj(j + 1), n, n, R, c->s));
-    vl.push_back(Vj(j));
+    BLAS(blas_axpby2(ft, a, c->w, n, ft, zero, Uj(j + 1), n, n, R, c->s));
+    vl.push_back(hb ? Vhj(j) : Vj(j));
   }
   // least squares per system and x += Z y
   int jmax = 0;
@@ -998,7 +1006,15 @@ static int do_setup(mg_ctx* c, const double* U) {
   c->m = p.fgmres_m;
   c->ldh = std::max(c->m, 32) + 8;
   const size_t ft = complex_bytes(c->vt);
-  c->V = c->alloc((size_t)(c->m + 1) * R * n * ft);
+  const char* oh = std::getenv("SAPMG_OUTER_FP16");
+  c->outer_half = c->vt == P32 && c->outer_dcgs2 && (oh ? std::atoi(oh) : 1);
+  if (c->outer_half) {
+    c->V = c->alloc((size_t)R * n * ft);
+    c->Vh = c->alloc((size_t)c->m * R * n * 4);
+    if (!c->Vh) return fail(MG_ERR_OOM, "workspace");
+  } else {
+    c->V = c->alloc((size_t)(c->m + 1) * R * n * ft);
+  }
   c->Z = c->alloc((size_t)c->m * R * n * ft);
   c->w = c->alloc((size_t)R * n * ft);
   c->x64 = c->alloc((size_t)R * n * 16);
