@@ -125,7 +125,9 @@ int sap_smooth(mg_ctx* ctx, const void* b, void* z, int n_sweeps, int prec, int 
  * with the FP64 multilevel cycle as right preconditioner.  Mixed form: FP64
  * defect correction (r = b - D z recomputed in FP64) around FP32 FGMRES(m)
  * whose preconditioner is the FP32/FP16/BF16 cycle.  Synchronises.
- * info may be NULL.  Returns MG_OK, MG_NOT_CONVERGED or an error. */
+ * info may be NULL.  Returns MG_OK, MG_NOT_CONVERGED or an error;
+ * MG_ERR_NONFINITE if the recomputed residual is not finite (NaN or Inf in b,
+ * or a breakdown of the reduced-precision iteration). */
 int mg_solve(mg_ctx* ctx, const double* b, double* z, int nrhs, mg_solve_info* info);
 
 /* Free every device buffer the context owns. */

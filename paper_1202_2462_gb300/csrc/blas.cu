@@ -761,7 +761,6 @@ int blas_dcgs2_step(int type, const BVec& b, const void* const* v, int j, void* 
 // FP16, scaled by kBasisScale = 2^10 (a unit vector's entries stay below 1, so
 // the scaled values stay in FP16's normal range and the scaling is exact).
 // Eight bytes = two complex numbers per load unit.
-constexpr float kBasisScale = 1024.f;
 
 __device__ __forceinline__ float4 h4_to_f4(uint2 u) {
   const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
@@ -963,8 +962,170 @@ int blas_dcgs2_step_h(const BVec& b, const void* const* vh, int j, void* u, void
   return MG_OK;
 }
 
-// x[r] += sum_j coeff[r*ldc + j] z_j[r] is blas_multiaxpy; with an FP16 basis the
-// outer solve needs no other FP16 kernel (the solution uses the FP32 Z vectors).
+// The coarse-level GMRES with an FP16 basis (same format): <v_j, w> for a list
+// of FP16 vectors, w += sign sum c_j v_j (FP32 w, optional norm), and
+// out = x / ||x|| written in FP16.
+template <int K>
+__global__ void __launch_bounds__(256) multidot_h_partial(PtrsV<uint2> v, const float4* __restrict__ w, size_t nu,
+                                                          size_t stride, double2* __restrict__ partial) {
+  const int r = blockIdx.y;
+  const float4* wr = w + r * stride;
+  float re[K], im[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) re[q] = im[q] = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += (size_t)gridDim.x * blockDim.x) {
+    uint2 a[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] = __ldg(v.p[q] + r * stride + i);
+    const float4 x = __ldg(wr + i);
+#pragma unroll
+    for (int q = 0; q < K; ++q) cdot_acc(h4_to_f4(a[q]), x, re[q], im[q]);
+  }
+  __shared__ double red[8][2 * K];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const float a = warp_sum(re[q]);
+    const float b = warp_sum(im[q]);
+    if (lane == 0) { red[wid][2 * q] = (double)a; red[wid][2 * q + 1] = (double)b; }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < K) {
+    double a = 0, b = 0;
+    for (int q = 0; q < 8; ++q) { a += red[q][2 * threadIdx.x]; b += red[q][2 * threadIdx.x + 1]; }
+    partial[((size_t)r * gridDim.x + blockIdx.x) * kChunk + threadIdx.x] = make_double2(a, b);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) multiaxpy_h_kernel(float4* __restrict__ w, PtrsV<uint2> v,
+                                                          const double2* __restrict__ coeff, int ldc, double sign,
+                                                          size_t nu, size_t stride, double2* __restrict__ partial) {
+  __shared__ float cf[2][16];
+  const int r = blockIdx.y;
+  if ((int)threadIdx.x < K) {
+    const double2 c = coeff[(size_t)r * ldc + threadIdx.x];
+    cf[0][threadIdx.x] = (float)(sign * c.x);
+    cf[1][threadIdx.x] = (float)(sign * c.y);
+  }
+  __syncthreads();
+  float4* wr = w + r * stride;
+  float nn = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += (size_t)gridDim.x * blockDim.x) {
+    uint2 a[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) a[q] = __ldg(v.p[q] + r * stride + i);
+    float4 x = wr[i];
+#pragma unroll
+    for (int q = 0; q < K; ++q) caxpy(cf[0][q], cf[1][q], h4_to_f4(a[q]), x);
+    wr[i] = x;
+    nn += nrm_of(x);
+  }
+  if (partial) {
+    __shared__ double red[8];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float t = warp_sum(nn);
+    if (lane == 0) red[wid] = (double)t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0;
+      for (int q = 0; q < 8; ++q) sum += red[q];
+      partial[((size_t)r * gridDim.x + blockIdx.x) * kChunk] = make_double2(sum, 0.0);
+    }
+  }
+}
+
+__global__ void normalize_h_kernel(const float4* __restrict__ x, uint2* __restrict__ out,
+                                   const double2* __restrict__ nrm2, int ldn, double2* __restrict__ store, int lds,
+                                   size_t nu, size_t stride) {
+  const int r = blockIdx.y;
+  const double nn = sqrt(fmax(nrm2[(size_t)r * ldn].x, 0.0));
+  const float inv = nn > 0.0 ? (float)(1.0 / nn) : 0.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && store) store[(size_t)r * lds] = make_double2(nn, 0.0);
+  const float4* xr = x + r * stride;
+  uint2* o = out + r * stride;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += (size_t)gridDim.x * blockDim.x) {
+    float4 u = xr[i];
+    u.x *= inv;
+    u.y *= inv;
+    u.z *= inv;
+    u.w *= inv;
+    o[i] = f4_to_h4(u);
+  }
+}
+
+static bool half_ok(const BVec& b, const void* w, const void* const* v, int k) {
+  bool al = (b.n % 2 == 0) && (b.vstride == b.n) && ((reinterpret_cast<uintptr_t>(w) & 15) == 0);
+  for (int q = 0; q < k; ++q) al = al && ((reinterpret_cast<uintptr_t>(v[q]) & 7) == 0);
+  return al;
+}
+
+int blas_multidot_h(const BVec& b, const void* const* v, int k, const void* w, double2* out, int ldo,
+                    double2* partial, cudaStream_t s) {
+  if (k <= 0 || b.R <= 0) return MG_OK;
+  if (!half_ok(b, w, v, k)) return MG_ERR_ARG;
+  count_bytes(((double)k * 4 + 8) * b.n * b.R);
+  const size_t nu = b.n / 2, stride = b.vstride / 2;
+  const int ncta = reduce_ctas(nu, b.R);
+  const dim3 grid(ncta, b.R);
+  for (int j0 = 0; j0 < k; j0 += kChunk) {
+    const int kk = std::min(kChunk, k - j0);
+    PtrsV<uint2> p;
+    for (int q = 0; q < 16; ++q) p.p[q] = (const uint2*)v[j0 + std::min(q, kk - 1)];
+#define SAPMG_MDH(K) case K: multidot_h_partial<K><<<grid, 256, 0, s>>>(p, (const float4*)w, nu, stride, partial); count_launches(1); break;
+    switch (kk) {
+      SAPMG_MDH(1) SAPMG_MDH(2) SAPMG_MDH(3) SAPMG_MDH(4) SAPMG_MDH(5) SAPMG_MDH(6) SAPMG_MDH(7) SAPMG_MDH(8)
+      SAPMG_MDH(9) SAPMG_MDH(10) SAPMG_MDH(11) SAPMG_MDH(12) SAPMG_MDH(13) SAPMG_MDH(14) SAPMG_MDH(15)
+      default: multidot_h_partial<16><<<grid, 256, 0, s>>>(p, (const float4*)w, nu, stride, partial); count_launches(1); break;
+    }
+#undef SAPMG_MDH
+    multidot_finalize<<<b.R, 256, 0, s>>>(partial, ncta, kk, out + j0, ldo, 0, nullptr); count_launches(1);
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+int blas_multiaxpy_h(const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc, double sign,
+                     double2* nrm2, int ldn, double2* partial, cudaStream_t s) {
+  if (k <= 0 || b.R <= 0) return MG_OK;
+  if (!half_ok(b, w, v, k)) return MG_ERR_ARG;
+  count_bytes(((double)k * 4 + 16) * b.n * b.R);
+  const size_t nu = b.n / 2, stride = b.vstride / 2;
+  const dim3 g = nrm2 ? dim3(reduce_ctas(nu, b.R), b.R) : stream_grid(nu, b.R);
+  for (int j0 = 0; j0 < k; j0 += kChunk) {
+    const int kk = std::min(kChunk, k - j0);
+    const bool last = j0 + kChunk >= k;
+    PtrsV<uint2> p;
+    for (int q = 0; q < 16; ++q) p.p[q] = (const uint2*)v[j0 + std::min(q, kk - 1)];
+    double2* part = (last && nrm2) ? partial : nullptr;
+    const double2* c = coeff + j0;
+#define SAPMG_MAH(K) case K: multiaxpy_h_kernel<K><<<g, 256, 0, s>>>((float4*)w, p, c, ldc, sign, nu, stride, part); count_launches(1); break;
+    switch (kk) {
+      SAPMG_MAH(1) SAPMG_MAH(2) SAPMG_MAH(3) SAPMG_MAH(4) SAPMG_MAH(5) SAPMG_MAH(6) SAPMG_MAH(7) SAPMG_MAH(8)
+      SAPMG_MAH(9) SAPMG_MAH(10) SAPMG_MAH(11) SAPMG_MAH(12) SAPMG_MAH(13) SAPMG_MAH(14) SAPMG_MAH(15)
+      default: multiaxpy_h_kernel<16><<<g, 256, 0, s>>>((float4*)w, p, c, ldc, sign, nu, stride, part); count_launches(1); break;
+    }
+#undef SAPMG_MAH
+  }
+  if (nrm2) {
+    multidot_finalize<<<b.R, 256, 0, s>>>(partial, (int)g.x, 1, nrm2, ldn, 0, nullptr); count_launches(1);
+  }
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+int blas_normalize_h(const BVec& b, const void* x, void* out, const double2* nrm2, int ldn, double2* store, int lds,
+                     cudaStream_t s) {
+  if (b.n % 2 != 0 || b.wstride != b.n) return MG_ERR_ARG;
+  count_bytes(12.0 * b.n * b.R);
+  const size_t nu = b.n / 2;
+  const dim3 g = stream_grid(nu, b.R);
+  normalize_h_kernel<<<g, 256, 0, s>>>((const float4*)x, (uint2*)out, nrm2, ldn, store, lds, nu, b.wstride / 2);
+  count_launches(1);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
 
 int blas_hessenberg_solve(const double2* H, int ldh, int ldr, int m, const double2* beta2, double2* y, int ldy,
                           int R, cudaStream_t s) {

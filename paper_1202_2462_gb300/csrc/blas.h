@@ -56,6 +56,15 @@ int blas_dcgs2_step(int type, const BVec& b, const void* const* v, int j, void* 
 // same format (and stays in u in FP32).
 int blas_dcgs2_step_h(const BVec& b, const void* const* vh, int j, void* u, void* w, void* vout, const DcgsWork& ws,
                       cudaStream_t s);
+// Kernels on FP16 basis vectors (scaled by 2^10, as blas_dcgs2_step_h stores
+// them) with FP32 w / x: <v_j, w>; w += sign sum c_j v_j (and ||w_new||^2 when
+// nrm2 != nullptr); out = x / ||x|| stored in the FP16 format.
+int blas_multidot_h(const BVec& b, const void* const* v, int k, const void* w, double2* out, int ldo,
+                    double2* partial, cudaStream_t s);
+int blas_multiaxpy_h(const BVec& b, void* w, const void* const* v, int k, const double2* coeff, int ldc, double sign,
+                     double2* nrm2, int ldn, double2* partial, cudaStream_t s);
+int blas_normalize_h(const BVec& b, const void* x, void* out, const double2* nrm2, int ldn, double2* store, int lds,
+                     cudaStream_t s);
 // y[r] = argmin || sqrt(beta2[r]) e1 - H_r y || for (m+1) x m Hessenberg H_r (column-major, ldh; H_r at H + r*ldr).
 int blas_hessenberg_solve(const double2* H, int ldh, int ldr, int m, const double2* beta2, double2* y, int ldy,
                           int R, cudaStream_t s);

@@ -49,8 +49,9 @@ int launch_coarse_apply_tma(const CGeom& c, const void* M, const void* x, void* 
                             cudaStream_t s);
 // The same stencil with the block products on tensor cores (TF32 inputs, FP32
 // accumulation; n2 % 8 == 0, n2 <= 64); operator stored in FP32 (P32) or FP16 (P16).
+// x_half (FP16 operator only): x holds FP16 basis vectors scaled by kBasisScale.
 int launch_coarse_apply_mma(const CGeom& c, int store, const void* M, const void* x, void* out, int nrhs, int* err,
-                            cudaStream_t s);
+                            bool x_half, cudaStream_t s);
 
 // Intermediate level of a three-level hierarchy (coarse1.cu).
 int launch_coarse_sap(int prec, const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,

@@ -185,7 +185,7 @@ constexpr int kStages = 2;
 template <int RB, class TM>
 __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restrict__ M,
                                                                const float2* __restrict__ x,
-                                                               float2* __restrict__ out, CGeom c, int r0,
+                                                               float2* __restrict__ out, CGeom c, int r0, int nr,
                                                                int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[kStages];
@@ -204,9 +204,9 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restr
   const int nsite_cta = (c.nsites - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int T = 9 * nsite_cta;
   if (T <= 0) return;
-  // rows RB..15 of every stage's vectors stay zero (the copies fill rows < RB only)
+  // rows nr..15 of every stage's vectors stay zero (the copies fill rows < nr only)
   for (int st = 0; st < kStages; ++st)
-    for (int e = tid; e < (16 - RB) * xst; e += blockDim.x) stage_x(st)[RB * xst + e] = make_float2(0.f, 0.f);
+    for (int e = tid; e < (16 - nr) * xst; e += blockDim.x) stage_x(st)[nr * xst + e] = make_float2(0.f, 0.f);
   if (tid == 0) {
     for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -226,12 +226,11 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restr
     const int st = t % kStages;
     const int site = site_of(t), d = t % 9;
     uint64_t* b = &bar[st];
-    mbar_expect_tx(b, tile_bytes + RB * row_bytes);
+    mbar_expect_tx(b, tile_bytes + nr * row_bytes);
     bulk_copy_g2s(stage_tile(st), M + ((size_t)site * 9 + d) * tile, tile_bytes, b);
     const int nb = neighbour(site, d);
     float2* xs = stage_x(st);
-#pragma unroll
-    for (int r = 0; r < RB; ++r) bulk_copy_g2s(xs + r * xst, xr + (size_t)r * fs + (size_t)nb * n2, row_bytes, b);
+    for (int r = 0; r < nr; ++r) bulk_copy_g2s(xs + r * xst, xr + (size_t)r * fs + (size_t)nb * n2, row_bytes, b);
   };
   if (tid == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -284,7 +283,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restr
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = 8 * q + 2 * tig + h;
-            if (r < RB) {
+            if (r < nr) {
               float* o = reinterpret_cast<float*>(out + (size_t)(r0 + r) * fs + (size_t)site * n2);
               o[2 * i0 + a] = acc[q][h];
               o[2 * (i0 + 4) + a] = acc[q][2 + h];
@@ -327,10 +326,10 @@ __device__ __forceinline__ uint32_t pack16(float2 v) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int RB, int N2, int ST>
+template <int RB, int N2, int ST, bool XH>
 __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* __restrict__ M,
-                                                                 const float2* __restrict__ x,
-                                                                 float2* __restrict__ out, CGeom c, int r0,
+                                                                 const void* __restrict__ xv,
+                                                                 float2* __restrict__ out, CGeom c, int r0, int nr,
                                                                  int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[ST];
@@ -338,19 +337,25 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
   const int xst = n2 + 4;                                     // padded row stride (conflict-free fragment loads)
   const int tile = n2 * n2;
   const uint32_t tile_bytes = (uint32_t)tile * sizeof(__half2);
-  const uint32_t row_bytes = (uint32_t)n2 * sizeof(float2);
-  const size_t stage_bytes = tile_bytes + (size_t)16 * xst * sizeof(float2);
+  // XH: the vectors are FP16 basis vectors (scaled by kBasisScale), staged as
+  // half2 and used as B fragments directly; otherwise FP32, packed per fragment
+  constexpr int xb = XH ? 4 : 8;                              // bytes per staged complex entry
+  const uint32_t row_bytes = (uint32_t)n2 * xb;
+  const size_t stage_bytes = tile_bytes + (size_t)16 * xst * xb;
   auto stage_tile = [&](int st) { return reinterpret_cast<const uint32_t*>(smem + st * stage_bytes); };
   auto stage_x = [&](int st) { return reinterpret_cast<float2*>(smem + st * stage_bytes + tile_bytes); };
+  auto stage_xh = [&](int st) { return reinterpret_cast<uint32_t*>(smem + st * stage_bytes + tile_bytes); };
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, tig = lane & 3;
   const size_t fs = (size_t)c.nsites * n2;
-  const float2* xr = x + (size_t)r0 * fs;
+  const unsigned char* xr = reinterpret_cast<const unsigned char*>(xv) + (size_t)r0 * fs * xb;
   const int nsite_cta = (c.nsites - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int T = 9 * nsite_cta;
   if (T <= 0) return;
-  for (int st = 0; st < ST; ++st)
-    for (int e = tid; e < (16 - RB) * xst; e += blockDim.x) stage_x(st)[RB * xst + e] = make_float2(0.f, 0.f);
+  for (int st = 0; st < ST; ++st) {
+    uint32_t* z = reinterpret_cast<uint32_t*>(smem + st * stage_bytes + tile_bytes + (size_t)nr * xst * xb);
+    for (int e = tid; e < (16 - nr) * xst * xb / 4; e += blockDim.x) z[e] = 0u;
+  }
   if (tid == 0) {
     for (int st = 0; st < ST; ++st) mbar_init(&bar[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -369,12 +374,12 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
     const int st = t % ST;
     const int site = site_of(t), d = t % 9;
     uint64_t* b = &bar[st];
-    mbar_expect_tx(b, tile_bytes + RB * row_bytes);
+    mbar_expect_tx(b, tile_bytes + nr * row_bytes);
     bulk_copy_g2s((void*)stage_tile(st), M + ((size_t)site * 9 + d) * tile, tile_bytes, b);
     const int nb = neighbour(site, d);
-    float2* xs = stage_x(st);
-#pragma unroll
-    for (int r = 0; r < RB; ++r) bulk_copy_g2s(xs + r * xst, xr + (size_t)r * fs + (size_t)nb * n2, row_bytes, b);
+    unsigned char* xs = smem + st * stage_bytes + tile_bytes;
+    for (int r = 0; r < nr; ++r)
+      bulk_copy_g2s(xs + (size_t)r * xst * xb, xr + ((size_t)r * fs + (size_t)nb * n2) * xb, row_bytes, b);
   };
   if (tid == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -403,6 +408,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
     }
     const uint32_t* mt = stage_tile(st);
     const float2* xs = stage_x(st);
+    const uint32_t* xsh = stage_xh(st);
     if (m0 < 2 * n2) {
 #pragma unroll
       for (int k0 = 0; k0 < 2 * n2; k0 += 16) {
@@ -414,8 +420,8 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           if (q == 1 && RB <= 8) continue;                    // columns 8..15 are zero
-          const uint32_t b0 = pack16(xs[(8 * q + g) * xst + j]);
-          const uint32_t b1 = pack16(xs[(8 * q + g) * xst + j + 4]);
+          const uint32_t b0 = XH ? xsh[(8 * q + g) * xst + j] : pack16(xs[(8 * q + g) * xst + j]);
+          const uint32_t b1 = XH ? xsh[(8 * q + g) * xst + j + 4] : pack16(xs[(8 * q + g) * xst + j + 4]);
           mma_f16(acc[q], a0, a1, a2, a3, b0, b1);
         }
       }
@@ -425,10 +431,11 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = 8 * q + 2 * tig + h;
-            if (r < RB) {
+            if (r < nr) {
               float* o = reinterpret_cast<float*>(out + (size_t)(r0 + r) * fs + (size_t)site * n2);
-              o[2 * i0 + a] = acc[q][h];
-              o[2 * (i0 + 4) + a] = acc[q][2 + h];
+              constexpr float os = XH ? 1.f / kBasisScale : 1.f;
+              o[2 * i0 + a] = os * acc[q][h];
+              o[2 * (i0 + 4) + a] = os * acc[q][2 + h];
             }
           }
       }
@@ -444,36 +451,37 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
   }
 }
 
-template <int RB, int N2, int ST>
-static void launch_mma16_t(const CGeom& c, const __half2* M, const float2* x, float2* out, int r0, int* err,
+template <int RB, int N2, int ST, bool XH>
+static void launch_mma16_t(const CGeom& c, const __half2* M, const void* x, float2* out, int r0, int nr, int* err,
                            cudaStream_t s) {
-  const size_t stage = (size_t)c.n2 * c.n2 * sizeof(__half2) + (size_t)16 * (c.n2 + 4) * sizeof(float2);
+  const size_t stage = (size_t)c.n2 * c.n2 * sizeof(__half2) + (size_t)16 * (c.n2 + 4) * (XH ? 4 : 8);
   const size_t smem = ST * stage;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(coarse_apply_mma16_kernel<RB, N2, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(coarse_apply_mma16_kernel<RB, N2, ST, XH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr = true;
   }
   const int threads = 32 * (c.n2 / 8);
   const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / (smem + 1024)));
   const int grid = std::min(c.nsites, 152 * per_sm);
-  coarse_apply_mma16_kernel<RB, N2, ST><<<grid, threads, smem, s>>>(M, x, out, c, r0, err); count_launches(1);
+  coarse_apply_mma16_kernel<RB, N2, ST, XH><<<grid, threads, smem, s>>>(M, x, out, c, r0, nr, err); count_launches(1);
 }
 
 // Two stages (one block in flight while the previous is multiplied) keep the
 // shared memory per CTA small enough for eight CTAs per SM, which measured
 // faster than deeper rings with fewer CTAs; 2N = 40 has a specialised
 // instance with the k loop unrolled.
-template <int RB>
-static void launch_mma16(const CGeom& c, const __half2* M, const float2* x, float2* out, int r0, int* err,
+template <int RB, bool XH>
+static void launch_mma16(const CGeom& c, const __half2* M, const void* x, float2* out, int r0, int nr, int* err,
                          cudaStream_t s) {
-  if (c.n2 == 40) launch_mma16_t<RB, 40, 2>(c, M, x, out, r0, err, s);
-  else launch_mma16_t<RB, 0, 2>(c, M, x, out, r0, err, s);
+  if (c.n2 == 40) launch_mma16_t<RB, 40, 2, XH>(c, M, x, out, r0, nr, err, s);
+  else launch_mma16_t<RB, 0, 2, XH>(c, M, x, out, r0, nr, err, s);
 }
 
 template <int RB, class TM>
-static void launch_mma(const CGeom& c, const TM* M, const float2* x, float2* out, int r0, int* err, cudaStream_t s) {
+static void launch_mma(const CGeom& c, const TM* M, const float2* x, float2* out, int r0, int nr, int* err,
+                       cudaStream_t s) {
   const size_t stage = (size_t)c.n2 * c.n2 * sizeof(TM) + (size_t)16 * (c.n2 + 2) * sizeof(float2);
   const size_t smem = kStages * stage;
   static bool attr = false;
@@ -484,7 +492,7 @@ static void launch_mma(const CGeom& c, const TM* M, const float2* x, float2* out
   const int threads = 32 * (c.n2 / 8);                        // one warp per 16 rows of the 2 n2 real rows
   const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / (smem + 1024)));
   const int grid = std::min(c.nsites, 152 * per_sm);
-  coarse_apply_mma_kernel<RB, TM><<<grid, threads, smem, s>>>(M, x, out, c, r0, err); count_launches(1);
+  coarse_apply_mma_kernel<RB, TM><<<grid, threads, smem, s>>>(M, x, out, c, r0, nr, err); count_launches(1);
 }
 
 template <class TM>
@@ -492,30 +500,40 @@ static void launch_mma_all(const CGeom& c, const TM* M, const float2* x, float2*
                            cudaStream_t s) {
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
     const int rb = std::min(16, nrhs - r0);
-    if (rb > 12) launch_mma<16, TM>(c, M, x, out, r0, err, s);
-    else if (rb > 8) launch_mma<12, TM>(c, M, x, out, r0, err, s);
-    else if (rb > 4) launch_mma<8, TM>(c, M, x, out, r0, err, s);
-    else if (rb > 1) launch_mma<4, TM>(c, M, x, out, r0, err, s);
-    else launch_mma<1, TM>(c, M, x, out, r0, err, s);
+    if (rb > 12) launch_mma<16, TM>(c, M, x, out, r0, rb, err, s);
+    else if (rb > 8) launch_mma<12, TM>(c, M, x, out, r0, rb, err, s);
+    else if (rb > 4) launch_mma<8, TM>(c, M, x, out, r0, rb, err, s);
+    else if (rb > 1) launch_mma<4, TM>(c, M, x, out, r0, rb, err, s);
+    else launch_mma<1, TM>(c, M, x, out, r0, rb, err, s);
   }
 }
 
 // Tensor-core form: n2 % 8 == 0 and n2 <= 64; up to 16 right-hand sides per
-// launch; the operator in FP32 (store P32) or FP16 (store P16).
+// launch (nr of them, the template width RB >= nr fixes the fragment count);
+// the operator in FP32 (store P32) or FP16 (store P16).
 int launch_coarse_apply_mma(const CGeom& c, int store, const void* M, const void* x, void* out, int nrhs, int* err,
-                            cudaStream_t s) {
+                            bool x_half, cudaStream_t s) {
+  if (x_half && store != P16) return MG_ERR_ARG;
   if (c.n2 % 8 != 0 || c.n2 > 64) return MG_ERR_ARG;
   if (store == P32) {
     launch_mma_all(c, (const float2*)M, (const float2*)x, (float2*)out, nrhs, err, s);
   } else if (store == P16) {
     const __half2* m = (const __half2*)M;
+    const size_t xe = x_half ? 4 : 8;                         // bytes per complex vector entry
     for (int r0 = 0; r0 < nrhs; r0 += 16) {
       const int rb = std::min(16, nrhs - r0);
-      if (rb > 12) launch_mma16<16>(c, m, (const float2*)x, (float2*)out, r0, err, s);
-      else if (rb > 8) launch_mma16<12>(c, m, (const float2*)x, (float2*)out, r0, err, s);
-      else if (rb > 4) launch_mma16<8>(c, m, (const float2*)x, (float2*)out, r0, err, s);
-      else if (rb > 1) launch_mma16<4>(c, m, (const float2*)x, (float2*)out, r0, err, s);
-      else launch_mma16<1>(c, m, (const float2*)x, (float2*)out, r0, err, s);
+      const void* xs = x;
+      float2* o = (float2*)out;
+      (void)xe;
+#define SAPMG_M16(RB_)                                                                       \
+  if (x_half) launch_mma16<RB_, true>(c, m, xs, o, r0, rb, err, s);                          \
+  else launch_mma16<RB_, false>(c, m, xs, o, r0, rb, err, s);
+      if (rb > 12) { SAPMG_M16(16) }
+      else if (rb > 8) { SAPMG_M16(12) }
+      else if (rb > 4) { SAPMG_M16(8) }
+      else if (rb > 1) { SAPMG_M16(4) }
+      else { SAPMG_M16(1) }
+#undef SAPMG_M16
     }
   } else {
     return MG_ERR_ARG;

@@ -13,6 +13,9 @@ namespace sapmg {
 enum { P64 = MG_FP64, P32 = MG_FP32, P16 = MG_FP16, PBF = MG_BF16 };
 
 inline size_t complex_bytes(int prec) { return prec == P64 ? 16 : (prec == P32 ? 8 : 4); }
+// Krylov basis vectors kept in FP16 are stored multiplied by this power of two
+// (unit vectors: entries below 1, so the scaled values stay normal in FP16).
+constexpr float kBasisScale = 1024.f;
 
 // layout.cu
 int launch_pack_gauge(int prec, const Geom& g, const double* Uc, void* Ub, int antiperiodic_t, cudaStream_t s);

@@ -118,6 +118,7 @@ struct CoarseLevel {
   void* M64 = nullptr;       // FP64 operator (set-up result, export)
   void* M = nullptr;         // operator used by the solver (== M64 in FP64)
   void* Mh = nullptr;        // FP16 copy for the tensor-core stencil (mixed form, SAPMG_COARSE_FP16=0: none)
+  void* Vh = nullptr;        // FP16 Krylov basis of the coarse GMRES (with Mh; SAPMG_COARSE_BASIS_FP16=0: none)
   // fixed-step GMRES workspace for R right-hand sides (vector type = the cycle's)
   void* V = nullptr;         // (kmax + 1) batched vectors, vector j at V + j*R*n
   void* w = nullptr;         // batched [R][n]
@@ -199,6 +200,10 @@ struct mg_ctx {
       return nullptr;
     }
     allocs.push_back(ptr);
+    // SAPMG_POISON=1: fill every workspace with NaN bytes (0xff), so that a read
+    // of memory no kernel has written shows up in the results (debugging aid)
+    static const bool poison = std::getenv("SAPMG_POISON") && std::atoi(std::getenv("SAPMG_POISON"));
+    if (poison) cudaMemset(ptr, 0xff, bytes);
     return ptr;
   }
   ~mg_ctx() {
@@ -244,15 +249,20 @@ static int dot_to(mg_ctx* c, int type, const BVec& b, const void* x, const void*
   return blas_multidot(type, b, v, 1, y, out, ldo, 0, nullptr, c->partial, c->s);
 }
 
-// D_c x on a coarse level: the bulk-copy kernel for an FP32 operator, else the generic one.
-static int coarse_apply(mg_ctx* c, CoarseLevel& L, const void* x, void* out, int R) {
+// D_c x on a coarse level: the tensor-core kernel (FP16 or FP32 operator) in
+// the mixed form, the bulk-copy kernel for an FP32 operator, else the generic
+// one.  xh: x holds FP16 basis vectors (scaled by kBasisScale); needs the FP16
+// operator copy.
+static int coarse_apply(mg_ctx* c, CoarseLevel& L, const void* x, void* out, int R, bool xh = false) {
   ProfScope ps(c->prof, FAM_COARSE, c->s);
   const bool mma = L.store == P32 && c->vt == P32 && c->coarse_tf32 && L.cg.n2 % 8 == 0 && L.cg.n2 <= 64 &&
                    !c->generic_coarse;
   const int store = (mma && L.Mh) ? P16 : L.store;
+  if (xh && store != P16) return fail(MG_ERR_STATE, "FP16 coarse vectors need the FP16 operator");
   count_bytes((double)L.cg.nsites * (9.0 * L.cg.n2 * L.cg.n2 * complex_bytes(store) +
-                                     2.0 * R * L.cg.n2 * complex_bytes(c->vt)));
-  if (mma) return launch_coarse_apply_mma(L.cg, store, store == P16 ? L.Mh : L.M, x, out, R, c->dev_err, c->s);
+                                     R * L.cg.n2 * (complex_bytes(c->vt) + (xh ? 4.0 : complex_bytes(c->vt)))));
+  if (mma)
+    return launch_coarse_apply_mma(L.cg, store, store == P16 ? L.Mh : L.M, x, out, R, c->dev_err, xh, c->s);
   if (L.store == P32 && c->vt == P32 && L.cg.n2 % 2 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
     return launch_coarse_apply_tma(L.cg, L.M, x, out, R, c->dev_err, c->s);
   return launch_coarse_apply(L.store, L.cg, L.M, x, out, R, c->s);
@@ -310,6 +320,30 @@ static int coarse_gmres(mg_ctx* c, CoarseLevel& L, int k, int R) {
   return MG_OK;
 }
 
+// The same fixed-step GMRES with the Krylov basis kept in FP16 (scaled by
+// kBasisScale; the mixed form's two-level coarse solve when the FP16 operator
+// copy exists): half the basis traffic of the orthogonalisation, FP32 w, x.
+static int coarse_gmres_h(mg_ctx* c, CoarseLevel& L, int k, int R) {
+  const size_t n = L.n();
+  const BVec bv = bvec(n, R, n);
+  auto Vj = [&](int j) { return (void*)((char*)L.Vh + (size_t)j * R * n * 4); };
+  CBLAS(dot_to(c, P32, bv, L.b, L.b, L.beta2, 1));
+  CBLAS(blas_normalize_h(bv, L.b, Vj(0), L.beta2, 1, nullptr, 0, c->s));
+  std::vector<const void*> vl;
+  for (int j = 0; j < k; ++j) {
+    TRY(coarse_apply(c, L, Vj(j), L.w, R, true));
+    vl.push_back(Vj(j));
+    double2* hcol = L.H + (size_t)j * 33;
+    CBLAS(blas_multidot_h(bv, vl.data(), j + 1, L.w, hcol, 33 * 33, c->partial, c->s));
+    CBLAS(blas_multiaxpy_h(bv, L.w, vl.data(), j + 1, hcol, 33 * 33, -1.0, L.tmp + 40, 33 * 33, c->partial, c->s));
+    CBLAS(blas_normalize_h(bv, L.w, Vj(j + 1), L.tmp + 40, 33 * 33, hcol + j + 1, 33 * 33, c->s));
+  }
+  CBLAS(blas_hessenberg_solve(L.H, 33, 33 * 33, k, L.beta2, L.y, 33, R, c->s));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(L.x, 0, (size_t)R * n * 8, c->s));
+  CBLAS(blas_multiaxpy_h(bv, L.x, vl.data(), k, L.y, 33, 1.0, nullptr, 0, c->partial, c->s));
+  return MG_OK;
+}
+
 static int cycle1(mg_ctx* c, const void* v, void* z, int R);
 
 // Fixed-step flexible GMRES from zero on level 1 of a three-level hierarchy,
@@ -351,8 +385,10 @@ static int fgmres_fixed1(mg_ctx* c, int k, int R) {
 }
 
 static int coarse_solve(mg_ctx* c, int level, int R) {
+  if (level == 1 && c->p.n_levels == 2 && c->c1.Vh) return coarse_gmres_h(c, c->c1, c->p.coarse_iters, R);
   if (level == 1 && c->p.n_levels == 2) return coarse_gmres(c, c->c1, c->p.coarse_iters, R);
   if (level == 1 && c->p.n_levels == 3) return fgmres_fixed1(c, c->p.inner_iters, R);
+  if (level == 2 && c->p.n_levels == 3 && c->c2.Vh) return coarse_gmres_h(c, c->c2, c->p.coarse_iters, R);
   if (level == 2 && c->p.n_levels == 3) return coarse_gmres(c, c->c2, c->p.coarse_iters, R);
   return fail(MG_ERR_ARG, "coarse level out of range");
 }
@@ -375,7 +411,7 @@ static int cycle1(mg_ctx* c, const void* v, void* z, int R) {
     ProfScope ps(c->prof, FAM_RESTRICT, c->s);
     TRY(launch_transfer1(true, c->vt, c->c1.cg, c->agg1, v, c->c2.b, c->W, c->N1, R, c->s));
   }
-  TRY(coarse_gmres(c, c->c2, c->p.coarse_iters, R));
+  TRY(coarse_solve(c, 2, R));
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
     TRY(launch_transfer1(false, c->vt, c->c1.cg, c->agg1, c->c2.x, z, c->W, c->N1, R, c->s));
@@ -689,6 +725,10 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
     relres = 0;
     bool all = true;
     for (int q = 0; q < R; ++q) {
+      if (!std::isfinite(rn[q])) {
+        relres = rn[q];
+        return fail(MG_ERR_NONFINITE, "the residual became non-finite");
+      }
       const double rel = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
       relres = std::max(relres, rel);
       if (rn[q] > tol[q]) all = false;
@@ -918,7 +958,12 @@ static int alloc_fgmres1_ws(mg_ctx* c, int k, int R) {
 
 static int alloc_coarse_ws(mg_ctx* c, CoarseLevel& L, int kmax, int R) {
   const size_t n = L.n(), eb = complex_bytes(c->vt);
-  L.V = c->alloc((size_t)(kmax + 1) * R * n * eb);
+  const char* hb = std::getenv("SAPMG_COARSE_BASIS_FP16");
+  if (L.Mh && c->vt == P32 && n % 2 == 0 && (hb ? std::atoi(hb) : 1)) {
+    L.Vh = c->alloc((size_t)(kmax + 1) * R * n * 4);
+    if (!L.Vh) return fail(MG_ERR_OOM, "coarse workspace");
+  }
+  if (!L.Vh) L.V = c->alloc((size_t)(kmax + 1) * R * n * eb);
   L.w = c->alloc((size_t)R * n * eb);
   L.x = c->alloc((size_t)R * n * eb);
   L.b = c->alloc((size_t)R * n * eb);
@@ -926,7 +971,8 @@ static int alloc_coarse_ws(mg_ctx* c, CoarseLevel& L, int kmax, int R) {
   L.tmp = (double2*)c->alloc(sizeof(double2) * 33 * 33 * R);
   L.beta2 = (double2*)c->alloc(sizeof(double2) * R);
   L.y = (double2*)c->alloc(sizeof(double2) * 33 * R);
-  if (!L.V || !L.w || !L.x || !L.b || !L.H || !L.tmp || !L.beta2 || !L.y) return fail(MG_ERR_OOM, "coarse workspace");
+  if ((!L.V && !L.Vh) || !L.w || !L.x || !L.b || !L.H || !L.tmp || !L.beta2 || !L.y)
+    return fail(MG_ERR_OOM, "coarse workspace");
   SAPMG_CUDA_TRY(cudaMemsetAsync(L.H, 0, sizeof(double2) * 33 * 33 * R, c->s));
   return MG_OK;
 }

@@ -130,6 +130,43 @@ def test_coarse_gmres_parity(fp64_ctx):
     assert rel(host(out), ref) < 1e-11
 
 
+@pytest.mark.parametrize("basis16", ["1", "0"])
+def test_coarse_gmres_mixed_parity(basis16, monkeypatch):
+    """Fixed-step GMRES in the mixed form (FP16 operator on the tensor cores),
+    with the Krylov basis in FP16 (default) or FP32 (SAPMG_COARSE_BASIS_FP16=0),
+    against the oracle's GMRES on the FP16-rounded operator (8^3 x 16 lattice,
+    32 coarse sites, m0 = -3.9 so that 12 steps are far from an exact solve):
+    the same Krylov minimiser up to the rounding of the basis and of the
+    vectors fed to the tensor cores (FP16, 2^-11 relative), and a residual
+    above the minimal one by no more than that rounding."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    monkeypatch.setenv("SAPMG_COARSE_BASIS_FP16", basis16)
+    dims = (8, 8, 8, 16)
+    u = synth.random_gauge_field(dims, 0.4, 59)
+    iv = synth.test_vector_draw(dims, 8, 60)
+    m0 = -3.9
+    s = G.Solver(dev(torch, u), CSW, m0, n_levels=2, n_vec=(8,), setup_iters=0, precision="bf16",
+                 init_vectors=dev(torch, iv), coarse_iters=12)
+    c = CoarseOperator(WilsonClover(u, m0, CSW), Aggregation(dims, (4, 4, 4, 4), (4, 3)).build(iv))
+    for name in ("self_", "fwd", "bwd"):
+        setattr(c, name, round_storage(getattr(c, name), "fp16"))
+    bc = synth.random_spinor((2, 2, 2, 4), 61).reshape(4, 2, 2, 2, 12)
+    bc = np.concatenate([bc, bc[..., :4]], axis=-1).astype(np.complex64).astype(np.complex128)   # 16 dof
+    out = torch.zeros((32, 16), dtype=torch.complex64, device="cuda")
+    G.mg_coarse_solve(s.ctx, 1, dev(torch, bc.reshape(32, 16), torch.complex64), out, G.MG_FP32)
+    torch.cuda.synchronize()
+    s.close()
+    ref = gmres_fixed(c.apply, bc, 12)
+    got = host(out).astype(np.complex128).reshape(bc.shape)
+    res_ref = np.linalg.norm(bc - c.apply(ref)) / np.linalg.norm(bc)
+    res_got = np.linalg.norm(bc - c.apply(got)) / np.linalg.norm(bc)
+    assert res_ref > 0.1                                    # not an exact solve: the minimiser matters
+    tol = 2e-2 if basis16 == "1" else 2e-3
+    assert rel(got, ref) < tol
+    assert res_got <= res_ref * (1 + tol) + 2e-3
+
+
 def test_cycle_parity(field, fp64_ctx):
     """One multilevel cycle z = M v with the same P (FP64)."""
     torch = torch_cuda()
@@ -312,6 +349,32 @@ def test_fp32_coarse_stencil_batched_parity():
     s.close()
     ref = c.apply(x.astype(np.complex128)).reshape(17, 16, 12)
     assert rel(host(out), ref) < 2e-6
+
+
+@pytest.mark.parametrize("fp16", ["1", "0"])
+def test_coarse_stencil_writes_only_its_rows(fp16, monkeypatch):
+    """The tensor-core stencils run in batches of 16, 12, 8, 4 or 1 right-hand
+    sides; a call with fewer (here 2, 6, 11, 14) must leave the memory after
+    its output untouched (sentinel rows stay NaN) and give the same result as
+    the call with exactly the batch width."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    monkeypatch.setenv("SAPMG_COARSE_FP16", fp16)
+    u = synth.random_gauge_field(DIMS, 0.4, 62)
+    iv = synth.test_vector_draw(DIMS, 8, 63)
+    s = _solver(torch, u, n_levels=2, n_vec=(8,), setup_iters=0, precision="fp32", init_vectors=dev(torch, iv),
+                nrhs_max=16)
+    x = synth.random_spinor((2, 2, 2, 2), 64, nvec=16).reshape(16, 16, 12)
+    x = dev(torch, np.concatenate([x, x[..., :4]], axis=-1), torch.complex64)          # 16 dof per site
+    full = torch.zeros((16, 16, 16), dtype=torch.complex64, device="cuda")
+    G.mg_coarse_apply_batch(s.ctx, 1, x, full, G.MG_FP32, 16)
+    for nr in (2, 6, 11, 14):
+        out = torch.full((nr + 4, 16, 16), float("nan"), dtype=torch.complex64, device="cuda")
+        G.mg_coarse_apply_batch(s.ctx, 1, x[:nr].contiguous(), out, G.MG_FP32, nr)
+        torch.cuda.synchronize()
+        assert torch.isnan(out[nr:]).all(), nr
+        assert torch.equal(out[:nr], full[:nr]), nr
+    s.close()
 
 
 def test_coarse_stencil_fp16_n2_40_parity():
