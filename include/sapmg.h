@@ -86,7 +86,7 @@ typedef struct {
 
 typedef struct {
   int iterations;      /* preconditioned Krylov iterations, summed over right-hand sides */
-  int restarts;        /* outer cycles (restarts or defect corrections), summed */
+  int restarts;        /* plain form: FGMRES restarts; mixed form: FP64 defect corrections (summed) */
   double relres;       /* largest final true relative residual ||b - D z||/||b|| (FP64) */
   double seconds;      /* wall time of the call */
   double precond_seconds;  /* device time in the multilevel preconditioner (profiling on) */

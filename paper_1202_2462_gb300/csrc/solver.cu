@@ -709,6 +709,9 @@ static int host_norms(mg_ctx* c, int type, const void* x, int R, std::vector<dou
 }
 
 // Solve R right-hand sides together: b64 (batched blocked FP64) -> x64.
+// Restart cycles of the mixed form's FP32 flexible GMRES per FP64 correction.
+constexpr int kInnerCycles = 12;
+
 static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relres) {
   const size_t n = c->fine_n();
   std::vector<double> bn, rn, tol(R), ones(R, 1.0), inner(R), est;
@@ -741,17 +744,44 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
     if (c->prec == P64) {
       TRY(fgmres_cycle(c, P64, P64, R, c->r64, act, c->x64, tol, c->p.maxiter - iters, done, est));
     } else {
-      // FP64 defect correction around an FP32 flexible GMRES cycle on the normalised residual
+      // FP64 defect correction: flexible GMRES in FP32 on D e = t, t = the
+      // normalised residual, restarted on its own FP32 residual t - D e until
+      // that is below the inner tolerance (or no longer falls), then x and r
+      // are updated in FP64
       Scal32 a = zero;
       for (int q = 0; q < R; ++q) {
         if (act[q] > 0) a.v[q].x = 1.0 / act[q];
         inner[q] = act[q] > 0 ? std::max(2e-6, 0.5 * tol[q] / act[q]) : 1.0;
       }
-      std::vector<double> unorm(R);
-      for (int q = 0; q < R; ++q) unorm[q] = act[q] > 0 ? 1.0 : 0.0;
+      std::vector<double> rin(R), rin_prev(R, 2.0), aim(R);
+      for (int q = 0; q < R; ++q) rin[q] = act[q] > 0 ? 1.0 : 0.0;
       BLAS(blas_axpby2(P64, a, c->r64, n, P32, zero, c->t64, n, n, R, c->s));
       SAPMG_CUDA_TRY(cudaMemsetAsync(c->e32, 0, (size_t)R * n * 8, c->s));
-      TRY(fgmres_cycle(c, P32, P32, R, c->t64, unorm, c->e32, inner, c->p.maxiter - iters, done, est));
+      const void* rcur = c->t64;
+      int step = 0;
+      for (int cyc = 0; cyc < kInnerCycles; ++cyc) {
+        bool any = false;
+        for (int q = 0; q < R; ++q) {
+          // stop a system at its tolerance or when a cycle gained less than 10%
+          aim[q] = rin[q] > inner[q] && rin[q] < 0.9 * rin_prev[q] ? rin[q] : 0.0;
+          any = any || aim[q] > 0;
+        }
+        if (!any || iters + step >= c->p.maxiter) break;
+        TRY(fgmres_cycle(c, P32, P32, R, rcur, aim, c->e32, inner, c->p.maxiter - iters - step, done, est));
+        int cs = 0;
+        for (int q = 0; q < R; ++q) cs = std::max(cs, done[q]);
+        step += cs;
+        if (cs == 0) break;
+        // w = t - D e in FP32 (the Arnoldi work vector is free between cycles)
+        TRY(fine_dirac(c, P32, c->w, c->e32, R));
+        BLAS(blas_axpby2(P32, one, c->t64, n, P32, minus, c->w, n, n, R, c->s));
+        rin_prev = rin;
+        BLAS(host_norms(c, P32, c->w, R, rin));
+        for (int q = 0; q < R; ++q)
+          if (act[q] == 0) rin[q] = 0;
+        rcur = c->w;
+      }
+      for (int q = 0; q < R; ++q) done[q] = step;
       Scal32 sc = zero;
       for (int q = 0; q < R; ++q) sc.v[q].x = act[q];
       BLAS(blas_axpby2(P32, sc, c->e32, n, P64, one, c->x64, n, n, R, c->s));
