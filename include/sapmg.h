@@ -171,10 +171,11 @@ int mg_prolong(mg_ctx* ctx, int level, const void* in, void* out, int prec);
 int mg_coarse_apply(mg_ctx* ctx, int level, const void* in, void* out, int prec);
 /* Restriction and interpolation of nrhs <= nrhs_max vectors stored back to
  * back (fine side [nrhs][field], coarse side [nrhs][sites][2N]), the batched
- * form the cycle uses.  In the mixed form with nrhs > 1 the level-0
- * restriction runs on the tensor cores: the FP32 fine vectors and the stored
- * P enter as TF32 (10-bit mantissa, rounded to nearest), sums are FP32
- * (environment SAPMG_RESTRICT_TF32=0 selects the FP32 form).  Asynchronous. */
+ * form the cycle uses.  In the mixed form with 1 < nrhs <= 16 the level-0
+ * restriction and interpolation run on the tensor cores: the FP32 vectors and
+ * the stored P enter as TF32 (10-bit mantissa, rounded to nearest), sums are
+ * FP32 (environment SAPMG_RESTRICT_TF32=0 selects the FP32 forms).
+ * Asynchronous. */
 int mg_restrict_batch(mg_ctx* ctx, int level, const void* in, void* out, int prec, int nrhs);
 int mg_prolong_batch(mg_ctx* ctx, int level, const void* in, void* out, int prec, int nrhs);
 /* The same for nrhs coarse vectors stored back to back ([nrhs][sites][2N]);

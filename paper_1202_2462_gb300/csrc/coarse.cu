@@ -347,6 +347,120 @@ __global__ void __launch_bounds__(256) restrict0_mma_kernel(const float2* __rest
   }
 }
 
+// K4'' (tensor cores): interpolation of all right-hand sides (<= 16) for one
+// (aggregate, chirality) per CTA.  With the real embedding A[2K+a][2k+b] of P
+// ((0,0) Re, (0,1) -Im, (1,0) Im, (1,1) Re of P(K, k)) and B[2k][r] = Re e_r(k),
+// B[2k+1][r] = Im e_r(k), Y = A B gives Y[2K][r] = Re out_r(K) and
+// Y[2K+1][r] = Im out_r(K).  mma.sync m16n8k8 TF32 (FP16-stored P converts
+// exactly); P is staged per chunk of kRKC entries by cp.async; B is loaded
+// into registers once.  Neighbouring lanes (real and imaginary rows of one K)
+// swap halves by a shuffle so that each stores whole complex numbers.
+__device__ __forceinline__ float embed_pr(float2 m, int a, int b) { return a == b ? m.x : (a ? m.y : -m.y); }
+
+template <class TV>
+__host__ __device__ constexpr size_t prolong_stage_bytes(int Np) {
+  return (size_t)Np * RPad<TV>::sp * sizeof(TV);
+}
+
+template <int NT, class TV>
+__global__ void __launch_bounds__(256) prolong0_mma_kernel(const float2* __restrict__ in, float2* __restrict__ out,
+                                                           const TV* __restrict__ Pv, int N, int nrhs, int nblocks) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int SP = RPad<TV>::sp;
+  const int Np = (N + 3) & ~3;                                 // k padded to whole k8 steps of the embedding
+  const size_t PB = prolong_stage_bytes<TV>(Np);
+  auto sP = [&](int st) { return reinterpret_cast<TV*>(smem_raw + st * PB); };
+  float* eb = reinterpret_cast<float*>(smem_raw + kRStages * PB);   // [2 Np][16]
+  const int blk = blockIdx.x >> 1, chi = blockIdx.x & 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tig = lane & 3, a = g & 1;
+  const size_t fs = (size_t)nblocks * 12 * 256;
+  const size_t off = ((size_t)blk * 12 + 6 * chi) * 256;
+  const int n2 = 2 * N;
+  for (int e = tid; e < 2 * Np * 16; e += 256) {
+    const int kk = e >> 4, r = e & 15, k = kk >> 1;
+    float v = 0.f;
+    if (k < N && r < nrhs) {
+      const float2 x = in[(size_t)r * nblocks * n2 + (size_t)blk * n2 + chi * N + k];
+      v = (kk & 1) ? x.y : x.x;
+    }
+    eb[e] = v;
+  }
+  for (int st = 0; st < kRStages; ++st) {
+    uint32_t* pz = reinterpret_cast<uint32_t*>(sP(st) + N * SP);
+    for (int e = tid; e < (Np - N) * SP * (int)sizeof(TV) / 4; e += 256) pz[e] = 0u;
+  }
+  constexpr int PP = kRKC * (int)sizeof(TV) / 16;
+  auto load = [&](int st, int kc0) {
+    TV* P = sP(st);
+    for (int e = tid; e < N * PP; e += 256) {
+      const int row = e / PP, pc = e % PP;
+      const TV* src = Pv + ((size_t)(blk * N + row) * 12 + 6 * chi) * 256 + kc0;
+      cp_async16(reinterpret_cast<unsigned char*>(P + row * SP) + pc * 16,
+                 reinterpret_cast<const unsigned char*>(src) + pc * 16);
+    }
+  };
+  constexpr int NC = 1536 / kRKC;
+#pragma unroll
+  for (int st = 0; st < kRStages - 1; ++st) {
+    load(st, st * kRKC);
+    cp_async_commit();
+  }
+  __syncthreads();                                             // eb written
+  const int KS = Np / 4;                                       // k8 steps (<= 8)
+  uint32_t bf[8][NT][2];
+#pragma unroll
+  for (int ks = 0; ks < 8; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      if (ks < KS) {
+        bf[ks][nt][0] = f32_to_tf32(eb[(8 * ks + tig) * 16 + 8 * nt + g]);
+        bf[ks][nt][1] = f32_to_tf32(eb[(8 * ks + tig + 4) * 16 + 8 * nt + g]);
+      } else {
+        bf[ks][nt][0] = bf[ks][nt][1] = 0u;
+      }
+    }
+  for (int c = 0; c < NC; ++c) {
+    cp_async_wait<kRStages - 2>();
+    __syncthreads();
+    if (c + kRStages - 1 < NC) load((c + kRStages - 1) % kRStages, (c + kRStages - 1) * kRKC);
+    cp_async_commit();
+    const TV* P = sP(c % kRStages);
+    for (int mt = warp; mt < kRKC / 8; mt += 8) {              // 16-row tiles of the 2 kRKC real rows
+      const int Kl = 8 * mt + (g >> 1);                        // rows g (K = Kl) and g + 8 (K = Kl + 4)
+      float acc[NT][4];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks) {
+        if (ks < KS) {
+          const int k = 4 * ks + (tig >> 1), b = tig & 1;       // columns tig (k) and tig + 4 (k + 2)
+          const uint32_t a0 = f32_to_tf32(embed_pr(p_ld(P + k * SP + Kl), a, b));
+          const uint32_t a1 = f32_to_tf32(embed_pr(p_ld(P + k * SP + Kl + 4), a, b));
+          const uint32_t a2 = f32_to_tf32(embed_pr(p_ld(P + (k + 2) * SP + Kl), a, b));
+          const uint32_t a3 = f32_to_tf32(embed_pr(p_ld(P + (k + 2) * SP + Kl + 4), a, b));
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) mma_m16n8k8_tf32(acc[nt], a0, a1, a2, a3, bf[ks][nt][0], bf[ks][nt][1]);
+        }
+      }
+      // lane with a = 0 holds Re, its partner (lane ^ 4) Im, of out_r(K) for r = r0, r0 + 1
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const int r0 = 8 * nt + 2 * tig, rw = r0 + a;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {                          // rows K = Kl (h = 0) and Kl + 4
+          const float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+          const float send = a ? v0 : v1;
+          const float recv = __shfl_xor_sync(0xffffffffu, send, 4);
+          const float2 o = a ? make_float2(recv, v1) : make_float2(v0, recv);
+          if (rw < nrhs) out[(size_t)rw * fs + off + c * kRKC + Kl + 4 * h] = o;
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
 template <class TV>
 static int transfer0_mrhs(bool restrict_, const Geom& g, const void* in, void* out, const void* Pv, int N, int nrhs,
                           bool tf32, cudaStream_t s) {
@@ -377,6 +491,24 @@ static int transfer0_mrhs(bool restrict_, const Geom& g, const void* in, void* o
     const unsigned grid = (unsigned)(g.nblocks * 2 * ((nrhs + RG - 1) / RG));
     restrict0_mrhs_kernel<RG, TV><<<grid, 256, smem, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs,
                                                           g.nblocks); count_launches(1);
+  } else if (tf32 && nrhs <= 16 && N <= 32) {
+    const int Np = (N + 3) & ~3;
+    const size_t smem = kRStages * prolong_stage_bytes<TV>(Np) + sizeof(float) * 2 * Np * 16;
+    const unsigned grid = (unsigned)(g.nblocks * 2);
+    static bool pattr = false;
+    if (!pattr) {                                 // enough for N = 32
+      const int mx = (int)(kRStages * prolong_stage_bytes<TV>(32) + sizeof(float) * 2 * 32 * 16);
+      cudaFuncSetAttribute(prolong0_mma_kernel<1, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      cudaFuncSetAttribute(prolong0_mma_kernel<2, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      pattr = true;
+    }
+    if (nrhs <= 8) {
+      prolong0_mma_kernel<1, TV><<<grid, 256, smem, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs,
+                                                          g.nblocks); count_launches(1);
+    } else {
+      prolong0_mma_kernel<2, TV><<<grid, 256, smem, s>>>((const float2*)in, (float2*)out, (const TV*)Pv, N, nrhs,
+                                                          g.nblocks); count_launches(1);
+    }
   } else {
     const size_t smem = sizeof(float2) * nrhs * N;
     dim3 grid(g.nblocks, 12);

@@ -145,7 +145,7 @@ struct mg_ctx {
   int coarse_reorth = 0;  // second Gram-Schmidt pass in the coarse GMRES (SAPMG_COARSE_REORTH=1)
   int generic_coarse = 0; // use the generic coarse stencil kernel (SAPMG_GENERIC_COARSE=1)
   int coarse_tf32 = 1;    // tensor-core (TF32) coarse stencil in the mixed form (SAPMG_COARSE_TF32=0 disables)
-  int restrict_tf32 = 1;  // tensor-core (TF32) multi-RHS restriction in the mixed form (SAPMG_RESTRICT_TF32=0 disables)
+  int restrict_tf32 = 1;  // tensor-core (TF32) multi-RHS level-0 transfers in the mixed form (SAPMG_RESTRICT_TF32=0 disables)
   int coarse_fp16 = 1;    // FP16-stored operator for the tensor-core coarse stencil (SAPMG_COARSE_FP16=0: FP32)
   int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
   double m0 = 0, csw = 0;
