@@ -35,6 +35,9 @@ import synth  # noqa: E402
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (nominal)
+# DRAM bytes per (site, right-hand side) of one BF16 Schwarz colour pass, from an ncu
+# capture of the 16^3x32 lattice with 12 right-hand sides (traffic grows with the units)
+SAP_DRAM_BYTES_PER_UNIT = 310.0e6 / (65536 * 12)
 
 
 def flops_dirac_site():
@@ -340,7 +343,10 @@ def run_ours(a, wl):
         tflops = flops_sap_site(wl["n_mr"]) * units / avg_s / 1e12 if n_prof else None
         alg_bytes = (v // 2) * (nrhs * bytes_sap_spinor(prec) + bytes_sap_fields(prec))
         roof = {"kernel": "sap_colour_kernel", "bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS if tflops else None, "traffic": None,
+                "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS if tflops else None,
+                "traffic": SAP_DRAM_BYTES_PER_UNIT * units if prec == "bf16" else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one colour pass of the "
+                                  "16^3x32 12-RHS case, per site and RHS, scaled to this launch's units",
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "hbm_gbs": alg_bytes / avg_s / 1e9 if n_prof else None,
                 "hbm_frac": alg_bytes / avg_s / 1e9 / hbm if n_prof else None,
