@@ -210,6 +210,35 @@ int mg_coarse_solve_noalloc(mg_ctx* ctx, int level, const void* in, void* out, i
  * MG_FP32 for a mixed one.  Asynchronous. */
 int mg_precondition(mg_ctx* ctx, const void* v, void* z, int prec);
 
+/* ---- Learned set-up (not in the paper): a gauge-covariant convolutional
+ * network that proposes near-kernel test vectors from noise, trained to
+ * imitate the bootstrap set-up (Sec. 3), which stays the fallback.
+ * Layer: out_a(x) = sum_b sum_h W[a][b][h] (T_h in_b)(x), T_0 = identity,
+ * T_{+mu} psi(x) = U_mu(x) psi(x + mu), T_{-mu} psi(x) = U_mu(x - mu)^dagger
+ * psi(x - mu), hop h = 0, 1 + 2 mu (+mu), 2 + 2 mu (-mu), mu = x, y, z, t;
+ * W[a][b][h] a complex 4 x 4 spin matrix.  W: device complex64
+ * [cout][cin][9][4][4] (row s, column t).  Fields: device complex64, blocked
+ * layout (mg_pack_spinor), channel c at c * 12V.  The transports use the
+ * context's FP32 links (mixed-form contexts only; MG_ERR_STATE otherwise),
+ * including an antiperiodic t sign if the context has one.  Gradients follow
+ * G_z = dL/dRe z + i dL/dIm z.  Asynchronous except mg_net_loss. */
+int mg_net_layer_forward(mg_ctx* ctx, int cin, int cout, const void* W, const void* x, void* y);
+/* gx = sum_h T_h^dagger sum_a W[a][b][h]^dagger gy_a (skipped if gx is NULL);
+ * gW[a][b][h] = sum_x gy_a(x) (T_h x_b)(x)^dagger (skipped if gW is NULL;
+ * a fixed-order reduction, deterministic). */
+int mg_net_layer_backward(mg_ctx* ctx, int cin, int cout, const void* W, const void* x, const void* gy, void* gx,
+                          void* gW);
+/* Gate between layers: y = x / sqrt(1 + |x(site)|^2) per channel and site;
+ * backward gx = s gy - (1 + n)^(-3/2) Re<gy, x>_site x. */
+int mg_net_gate_forward(mg_ctx* ctx, int channels, const void* x, void* y);
+int mg_net_gate_backward(mg_ctx* ctx, int channels, const void* x, const void* gy, void* gx);
+/* loss = ||y - t||^2 / ||t||^2 (returned on the host; synchronises) and
+ * gy = 2 (y - t) / ||t||^2 (one channel). */
+int mg_net_loss(mg_ctx* ctx, const void* y, const void* t, void* gy, double* loss);
+/* Adam on n FP32 parameters (first and second moments m, v; step >= 1). */
+int mg_adam_step(mg_ctx* ctx, size_t n, float* p, const float* g, float* m, float* v, double lr, double beta1,
+                 double beta2, double eps, int step);
+
 /* Per-kernel device timing with CUDA events recorded on the context's stream
  * around every launch of the selected kernel families.  mask: 0 = off, 1 = all
  * families, otherwise bit (f + 1) selects family f (0 dirac, 1 Schwarz colour

@@ -95,6 +95,13 @@ _SIGNATURES = {
     "mg_get_profile_bytes": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double)]),
     "mg_reset_profile": (_I, [_VP]),
     "mg_launch_count": (ctypes.c_longlong, []),
+    "mg_net_layer_forward": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
+    "mg_net_layer_backward": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP]),
+    "mg_net_gate_forward": (_I, [_VP, _I, _VP, _VP]),
+    "mg_net_gate_backward": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "mg_net_loss": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double)]),
+    "mg_adam_step": (_I, [_VP, ctypes.c_size_t, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double,
+                          ctypes.c_double, ctypes.c_double, _I]),
 }
 
 _lib = None
@@ -242,6 +249,34 @@ def mg_get_profile_bytes(ctx, family):
     b = ctypes.c_double()
     _check(lib().mg_get_profile_bytes(ctx, family, ctypes.byref(b)), "mg_get_profile_bytes")
     return b.value
+
+
+def mg_net_layer_forward(ctx, cin, cout, w, x, y):
+    return _check(lib().mg_net_layer_forward(ctx, cin, cout, _ptr(w), _ptr(x), _ptr(y)), "mg_net_layer_forward")
+
+
+def mg_net_layer_backward(ctx, cin, cout, w, x, gy, gx, gw):
+    return _check(lib().mg_net_layer_backward(ctx, cin, cout, _ptr(w), _ptr(x), _ptr(gy), _ptr(gx), _ptr(gw)),
+                  "mg_net_layer_backward")
+
+
+def mg_net_gate_forward(ctx, channels, x, y):
+    return _check(lib().mg_net_gate_forward(ctx, channels, _ptr(x), _ptr(y)), "mg_net_gate_forward")
+
+
+def mg_net_gate_backward(ctx, channels, x, gy, gx):
+    return _check(lib().mg_net_gate_backward(ctx, channels, _ptr(x), _ptr(gy), _ptr(gx)), "mg_net_gate_backward")
+
+
+def mg_net_loss(ctx, y, t, gy):
+    out = ctypes.c_double()
+    _check(lib().mg_net_loss(ctx, _ptr(y), _ptr(t), _ptr(gy), ctypes.byref(out)), "mg_net_loss")
+    return out.value
+
+
+def mg_adam_step(ctx, n, p, g, m, v, lr, beta1, beta2, eps, step):
+    return _check(lib().mg_adam_step(ctx, n, _ptr(p), _ptr(g), _ptr(m), _ptr(v), lr, beta1, beta2, eps, step),
+                  "mg_adam_step")
 
 
 def mg_reset_profile(ctx):

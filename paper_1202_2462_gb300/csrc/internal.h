@@ -32,6 +32,15 @@ uint64_t host_splitmix64(uint64_t x);
 int launch_dirac(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
                  cudaStream_t s);
 
+// learned.cu: the set-up network's layers, gate and optimiser
+int launch_gconv_forward(const Geom& g, const void* U, const void* W, const void* x, void* y, int cin, int cout,
+                         cudaStream_t s);
+int launch_gconv_backward(const Geom& g, const void* U, const void* W, const void* x, const void* gy, void* gx,
+                          void* gW, int cin, int cout, cudaStream_t s);
+int launch_gate(const Geom& g, const void* x, const void* gy, void* out, int channels, cudaStream_t s);
+int launch_adam(size_t n, float* p, const float* gr, float* m, float* v, double lr, double b1, double b2,
+                double eps, int step, cudaStream_t s);
+
 // sap.cu
 int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
                       int n_mr, int nrhs, cudaStream_t s);

@@ -1472,6 +1472,64 @@ int mg_precondition(mg_ctx* c, const void* v, void* z, int prec) {
   return MG_OK;
 }
 
+// ------------------------------------------------------------ learned set-up
+static int net_state(mg_ctx* c, int a, int b) {
+  if (!c) return fail(MG_ERR_ARG, "bad argument");
+  if (!c->U32) return fail(MG_ERR_STATE, "the network needs a mixed-form context (FP32 links)");
+  if (a < 1 || b < 1 || a > 64 || b > 64) return fail(MG_ERR_ARG, "channel counts must be in 1..64");
+  return MG_OK;
+}
+
+int mg_net_layer_forward(mg_ctx* c, int cin, int cout, const void* W, const void* x, void* y) {
+  TRY(net_state(c, cin, cout));
+  if (!W || !x || !y) return fail(MG_ERR_ARG, "bad argument");
+  return launch_gconv_forward(c->g, c->U32, W, x, y, cin, cout, c->s);
+}
+
+int mg_net_layer_backward(mg_ctx* c, int cin, int cout, const void* W, const void* x, const void* gy, void* gx,
+                          void* gW) {
+  TRY(net_state(c, cin, cout));
+  if (!W || !x || !gy || (!gx && !gW)) return fail(MG_ERR_ARG, "bad argument");
+  return launch_gconv_backward(c->g, c->U32, W, x, gy, gx, gW, cin, cout, c->s);
+}
+
+int mg_net_gate_forward(mg_ctx* c, int channels, const void* x, void* y) {
+  TRY(net_state(c, channels, 1));
+  if (!x || !y) return fail(MG_ERR_ARG, "bad argument");
+  return launch_gate(c->g, x, nullptr, y, channels, c->s);
+}
+
+int mg_net_gate_backward(mg_ctx* c, int channels, const void* x, const void* gy, void* gx) {
+  TRY(net_state(c, channels, 1));
+  if (!x || !gy || !gx) return fail(MG_ERR_ARG, "bad argument");
+  return launch_gate(c->g, x, gy, gx, channels, c->s);
+}
+
+int mg_net_loss(mg_ctx* c, const void* y, const void* t, void* gy, double* loss) {
+  TRY(net_state(c, 1, 1));
+  if (!y || !t || !gy || !loss) return fail(MG_ERR_ARG, "bad argument");
+  const size_t n = c->fine_n();
+  const BVec bv = bvec(n, 1, n);
+  const Scal32 one = scal_all(1.0, 1), zero = scal_all(0.0, 1), minus = scal_all(-1.0, 1);
+  TRY(blas_axpby2(P32, one, y, n, P32, zero, gy, n, n, 1, c->s));           // gy = y
+  TRY(blas_axpby2(P32, minus, t, n, P32, one, gy, n, n, 1, c->s));          // gy = y - t
+  TRY(dot_to(c, P32, bv, gy, gy, c->hd, 1));
+  TRY(dot_to(c, P32, bv, t, t, c->hd + 1, 1));
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->hh, c->hd, 2 * sizeof(double2), cudaMemcpyDeviceToHost, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  const double dn = c->hh[0].x, tn = c->hh[1].x;
+  if (!(tn > 0)) return fail(MG_ERR_ARG, "target vector is zero");
+  *loss = dn / tn;
+  const Scal32 sc = scal_all(2.0 / tn, 1);
+  return blas_axpby2(P32, sc, gy, n, P32, zero, gy, n, n, 1, c->s);       // G = 2 (y - t) / ||t||^2
+}
+
+int mg_adam_step(mg_ctx* c, size_t n, float* p, const float* g, float* m, float* v, double lr, double beta1,
+                 double beta2, double eps, int step) {
+  if (!c || !p || !g || !m || !v) return fail(MG_ERR_ARG, "bad argument");
+  return launch_adam(n, p, g, m, v, lr, beta1, beta2, eps, step, c->s);
+}
+
 int mg_set_profiling(mg_ctx* c, int mask) {
   if (!c) return fail(MG_ERR_ARG, "bad argument");
   c->prof.on = mask != 0;

@@ -1,0 +1,155 @@
+"""GPU parity of the learned set-up's kernels (transport layer, gate, loss,
+Adam, whole network forward and backward) against the FP64 oracle, and its
+training and use on a small lattice."""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import learned as L
+from tests.gpu_util import torch_cuda, dev, host, rel
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (8, 8, 8, 8)
+M0, CSW = -0.19, 1.0
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u = synth.random_gauge_field(DIMS, 0.3, 101)
+    s = G.Solver(dev(torch, u), CSW, M0, n_levels=1, precision="fp32", fgmres_m=2)
+    yield torch, G, s, u
+    s.close()
+
+
+def _blocked(torch, G, s, x):
+    """canonical (C, ...) numpy -> blocked complex64 device tensor"""
+    from paper_1202_2462_gb300.learned import GaugeNet
+    return torch.cat([GaugeNet.blocked(s, dev(torch, x[c], torch.complex64)) for c in range(x.shape[0])])
+
+
+def _canonical(torch, G, s, y, c):
+    from paper_1202_2462_gb300.learned import GaugeNet
+    fs = y.numel() // c
+    return np.stack([host(GaugeNet.canonical(s, y[k * fs:(k + 1) * fs].contiguous()))[0] for k in range(c)])
+
+
+def _weights(cout, cin, seed):
+    return L.init_weights([(cout, cin)], seed)[0] * 3.0
+
+
+def test_layer_forward_and_backward_parity(ctx):
+    torch, G, s, u = ctx
+    cin, cout = 3, 2
+    w = _weights(cout, cin, 1)
+    x = synth.random_spinor(DIMS, 2, nvec=cin)
+    gy = synth.random_spinor(DIMS, 3, nvec=cout)
+    wd = dev(torch, w, torch.complex64)
+    xd = _blocked(torch, G, s, x)
+    yd = torch.empty(cout * xd.numel() // cin, dtype=torch.complex64, device="cuda")
+    G.mg_net_layer_forward(s.ctx, cin, cout, wd, xd, yd)
+    assert rel(_canonical(torch, G, s, yd, cout), L.layer(u, w, x)) < 2e-6
+    gyd = _blocked(torch, G, s, gy)
+    gxd = torch.empty_like(xd)
+    gwd = torch.empty_like(wd)
+    G.mg_net_layer_backward(s.ctx, cin, cout, wd, xd, gyd, gxd, gwd)
+    gx, gw = L.layer_backward(u, w, x, gy)
+    assert rel(_canonical(torch, G, s, gxd, cin), gx) < 2e-6
+    assert rel(host(gwd), gw) < 2e-6
+
+
+def test_gate_and_loss_parity(ctx):
+    torch, G, s, u = ctx
+    x = synth.random_spinor(DIMS, 4, nvec=2) * 0.7
+    gy = synth.random_spinor(DIMS, 5, nvec=2)
+    xd = _blocked(torch, G, s, x)
+    yd = torch.empty_like(xd)
+    G.mg_net_gate_forward(s.ctx, 2, xd, yd)
+    assert rel(_canonical(torch, G, s, yd, 2), L.gate(x)) < 1e-6
+    gyd = _blocked(torch, G, s, gy)
+    gxd = torch.empty_like(xd)
+    G.mg_net_gate_backward(s.ctx, 2, xd, gyd, gxd)
+    assert rel(_canonical(torch, G, s, gxd, 2), L.gate_backward(x, gy)) < 1e-6
+    out, t = synth.random_spinor(DIMS, 6, nvec=2)
+    od, td = _blocked(torch, G, s, out[None]), _blocked(torch, G, s, t[None])
+    g = torch.empty_like(od)
+    val = G.mg_net_loss(s.ctx, od, td, g)
+    ref, gref = L.loss(out.astype(np.complex64).astype(np.complex128), t.astype(np.complex64).astype(np.complex128))
+    assert abs(val - ref) < 1e-6 * ref
+    assert rel(_canonical(torch, G, s, g, 1)[0], gref) < 1e-6
+
+
+def test_adam_step_matches_its_definition(ctx):
+    torch, G, s, u = ctx
+    rng = np.random.default_rng(7)
+    p0, gr, m0, v0 = (rng.normal(size=1000).astype(np.float32) for _ in range(4))
+    v0 = np.abs(v0)
+    p, m, v = (torch.from_numpy(a.copy()).cuda() for a in (p0, m0, v0))
+    G.mg_adam_step(s.ctx, 1000, p, torch.from_numpy(gr).cuda(), m, v, 0.01, 0.9, 0.999, 1e-8, 3)
+    torch.cuda.synchronize()
+    m1 = 0.9 * m0 + 0.1 * gr
+    v1 = 0.999 * v0 + 0.001 * gr * gr
+    p1 = p0 - 0.01 * (m1 / (1 - 0.9 ** 3)) / (np.sqrt(v1 / (1 - 0.999 ** 3)) + 1e-8)
+    assert np.max(np.abs(host(p) - p1)) < 1e-5 * np.max(np.abs(p1))
+    assert np.max(np.abs(host(m) - m1)) < 1e-6 and np.max(np.abs(host(v) - v1)) < 1e-6
+
+
+def test_network_forward_backward_parity(ctx):
+    """Three layers, 4 channels: loss and every weight gradient against the oracle."""
+    torch, G, s, u = ctx
+    from paper_1202_2462_gb300.learned import GaugeNet
+    net = GaugeNet(channels=4, layers=3, seed=8)
+    ws = [host(w).astype(np.complex128) for w in net.weights]
+    eta = synth.random_spinor(DIMS, 9)
+    t = synth.random_spinor(DIMS, 10)
+    out, cache = net.forward(s, _blocked(torch, G, s, eta[None]))
+    val, grads = net.backward(s, out, cache, _blocked(torch, G, s, t[None]))
+    ref_out, _ = L.forward(u, ws, eta.astype(np.complex64).astype(np.complex128))
+    assert rel(_canonical(torch, G, s, out, 1)[0], ref_out) < 1e-5
+    ref_val, ref_grads = L.backward(u, ws, eta.astype(np.complex64).astype(np.complex128),
+                                    t.astype(np.complex64).astype(np.complex128))
+    assert abs(val - ref_val) < 1e-5 * ref_val
+    for gd, gr in zip(grads, ref_grads):
+        assert rel(host(gd), gr) < 1e-4
+
+
+def test_training_imitates_the_smoother_and_the_hierarchy_converges(ctx):
+    """A short training run on noise -> smoothed noise lowers the loss, and a
+    two-level hierarchy built from the network's proposals (refined by one
+    bootstrap sweep) solves to 1e-10; the iteration counts with and without
+    the network are reported."""
+    torch, G, s, u = ctx
+    from paper_1202_2462_gb300.learned import GaugeNet
+    net = GaugeNet(channels=8, layers=3, seed=11)
+    etas = dev(torch, synth.random_spinor(DIMS, 12, nvec=8), torch.complex64)
+    targets = [net.blocked(s, net.smoothed(s, etas[k], 4)) for k in range(8)]
+    inputs = [net.blocked(s, etas[k]) for k in range(8)]
+    first = last = None
+    for it in range(200):
+        k = it % 8
+        out, cache = net.forward(s, inputs[k])
+        val, grads = net.backward(s, out, cache, targets[k])
+        net.adam(s, grads, lr=1e-2)
+        if it < 8:
+            first = val if first is None else first + val
+        if it >= 192:
+            last = val if last is None else last + val
+    # the three-layer network sees 3 hops; four Schwarz sweeps reach much further,
+    # so it can only partly imitate them: require a clear decrease, not a fit
+    assert last < 0.98 * first, (first / 8, last / 8)
+    # hierarchies from proposals vs from raw noise (same noise, one bootstrap sweep each)
+    noise = dev(torch, synth.test_vector_draw(DIMS, 8, 13), torch.complex64)
+    prop = net.propose(s, noise).to(torch.complex128)
+    b = dev(torch, synth.random_spinor(DIMS, 14))
+    its = {}
+    for name, iv in (("noise", noise.to(torch.complex128)), ("network", prop)):
+        t = G.Solver(dev(torch, u), CSW, M0, n_levels=2, n_vec=(8,), setup_iters=1, precision="fp32",
+                     init_vectors=iv.contiguous())
+        z, info, code = t.solve(b)
+        t.close()
+        assert code == 0
+        its[name] = info.iterations
+    print("learned set-up, outer iterations:", its)
