@@ -11,6 +11,10 @@ sigma_min(D) = 1.0e-2; on the 32^3 x 64 field sigma_min(D) falls from 0.11
 ``m0`` is the bare mass in D = 4 + m0 - (hopping)/2 + clover; it maps to the
 hopping parameter as m0 = 1/(2 kappa) - 4.
 
+The 32^3 x 64 method parameters (one post-smoothing sweep, 16 coarse GMRES
+steps) are the fastest of a scan of nu_post, the coarse steps, n_MR and the
+restart length on this field (time to solution of the 12 point sources).
+
 ``ref_iterations`` scales the reference arm's timed oracle iteration to a whole
 solve: iterations per right-hand side of the method's plain FP64 form on that
 workload (119 at 32^3 x 64, the count the FP64 form reports; 60 where no
@@ -36,7 +40,7 @@ WORKLOADS = {
     "32^3x64": dict(
         dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.8,
         rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
-        n_mr=4, nu_post=2, setup_iters=8, coarse_iters=24, fgmres_m=20, tol=1e-10,
+        n_mr=4, nu_post=1, setup_iters=8, coarse_iters=16, fgmres_m=20, tol=1e-10,
         precision="bf16", metric=METRIC, ref_iterations=119),
     # Mid-size case for Nsight Compute captures: fields larger than L2, a few GB on the device.
     "32^3x32": dict(
