@@ -826,13 +826,13 @@ __global__ void __launch_bounds__(256) dots2h_partial(PtrsV<uint2> v, const floa
 
 // pass 2 with an FP16 basis.  Coefficient q of c1/c2 belongs to [u, w, v_0, ...].
 // first: y1 = c1_u u + c1_w w + sum, y2 likewise; otherwise y1 += sum (y1 kept
-// in u), y2 += sum (in w).  vout != nullptr (last chunk): v_j = y1 is also
-// written to the FP16 basis; partial: ||y1||^2, ||y2||^2.
+// in u), y2 += sum (in w).  vout != nullptr (last chunk): v_j = y1 is
+// written to the FP16 basis and to u only if keep_u; partial: ||y1||^2, ||y2||^2.
 template <int K>
 __global__ void __launch_bounds__(256) axpy2h_kernel(PtrsV<uint2> v, const double2* __restrict__ c1,
                                                      const double2* __restrict__ c2, int ldc, int q0, float4* u,
                                                      float4* w, uint2* __restrict__ vout, size_t nu, size_t stride,
-                                                     int first, double2* __restrict__ partial) {
+                                                     int first, int keep_u, double2* __restrict__ partial) {
   __shared__ float cf[4][18];
   const int r = blockIdx.y;
   if ((int)threadIdx.x < K + 2) {
@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(256) axpy2h_kernel(PtrsV<uint2> v, const doubl
       caxpy(cf[0][2 + q], cf[1][2 + q], av, s1);
       caxpy(cf[2][2 + q], cf[3][2 + q], av, s2);
     }
-    o1[i] = s1;
+    if (!ov || keep_u) o1[i] = s1;
     o2[i] = s2;
     if (ov) ov[i] = f4_to_h4(s1);
     n1 += nrm_of(s1);
@@ -900,8 +900,9 @@ int blas_dcgs2_step_h(const BVec& b, const void* const* vh, int j, void* u, void
             ((reinterpret_cast<uintptr_t>(vout) & 7) == 0);
   for (int q = 0; q < j; ++q) al = al && ((reinterpret_cast<uintptr_t>(vh[q]) & 7) == 0);
   if (!al) return MG_ERR_ARG;
-  // pass 1: j FP16 basis vectors + u, w; pass 2: the same + u, w written + v_j in FP16
-  count_bytes(((double)2 * j * 4 + 6 * 8 + 4) * b.n * b.R);
+  // pass 1: j FP16 basis vectors + u, w; pass 2: the same + w written + v_j in FP16
+  // (u is written back only between chunks, when j > 16)
+  count_bytes(((double)2 * j * 4 + 5 * 8 + 4) * b.n * b.R);
   const size_t nu = b.n / 2, stride = b.vstride / 2;
   const int R = b.R;
   const int ncta1 = std::max(1, std::min(reduce_ctas(nu, R), (int)(kPartialDouble2 / kDots2Slots / (size_t)R)));
@@ -944,7 +945,7 @@ int blas_dcgs2_step_h(const BVec& b, const void* const* vh, int j, void* u, void
 #define SAPMG_A2H(K)                                                                                                \
   case K:                                                                                                           \
     axpy2h_kernel<K><<<g2, 256, 0, s>>>(p, ws.c1, ws.c2, ws.ld, q0, (float4*)u, (float4*)w, vo, nu, stride, first, \
-                                        part);                                                                      \
+                                        0, part);                                                                   \
     count_launches(1);                                                                                              \
     break;
     switch (kk) {

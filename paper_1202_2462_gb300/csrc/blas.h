@@ -53,7 +53,8 @@ int blas_dcgs2_step(int type, const BVec& b, const void* const* v, int j, void* 
                     cudaStream_t s);
 // The same step (FP32 u and w) with the finished basis vectors stored in FP16,
 // scaled by 2^10: vh = v_0 .. v_{j-1}; the new v_j is written to vout in the
-// same format (and stays in u in FP32).
+// same format only (u's contents are undefined afterwards); u need not be
+// normalised.
 int blas_dcgs2_step_h(const BVec& b, const void* const* vh, int j, void* u, void* w, void* vout, const DcgsWork& ws,
                       cudaStream_t s);
 // Kernels on FP16 basis vectors (scaled by 2^10, as blas_dcgs2_step_h stores

@@ -509,12 +509,15 @@ static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r
     if (rnorm[q] > 0 && rnorm[q] > abs_tol[q]) { active[q] = 1; ++n_active; a.v[q].x = 1.0 / rnorm[q]; }
   }
   if (n_active == 0) return MG_OK;
-  // with an FP16 basis the newest (once-orthogonalised) vector lives in V in
-  // FP32 and the finished ones in Vh
+  // With an FP16 basis the finished vectors live in Vh and the newest,
+  // once-orthogonalised one in FP32 in one of two buffers (V, w) that swap
+  // roles every step: step j's new w (not normalised: the second pass
+  // normalises it, and the cycle is homogeneous of degree one) is step j+1's u.
   const bool hb = c->outer_half != 0;
-  auto Uj = [&](int j) { return hb ? c->V : Vj(j); };
+  void* ucur = hb ? c->V : Vj(0);
+  void* wcur = c->w;
   auto Vhj = [&](int j) { return (void*)((char*)c->Vh + (size_t)j * R * n * 4); };
-  BLAS(blas_axpby2(ft, a, r, n, ft, zero, Uj(0), n, n, R, c->s));
+  BLAS(blas_axpby2(ft, a, r, n, ft, zero, ucur, n, n, R, c->s));
   const size_t rl = (size_t)R * ld;
   DcgsWork ws;
   ws.A = c->dcg;
@@ -529,10 +532,11 @@ static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r
   ws.partial = c->partial;
   std::vector<const void*> vl;   // finished basis vectors v_0 .. v_{j-1}
   for (int j = 0; j < m; ++j) {
-    TRY(cycle(c, Uj(j), Zj(j), R));
-    TRY(fine_dirac(c, aprec, c->w, Zj(j), R));
-    if (hb) BLAS(blas_dcgs2_step_h(bv, vl.data(), j, Uj(j), c->w, Vhj(j), ws, c->s));
-    else BLAS(blas_dcgs2_step(ft, bv, vl.data(), j, Vj(j), c->w, ws, c->s));
+    if (!hb) ucur = Vj(j);
+    TRY(cycle(c, ucur, Zj(j), R));
+    TRY(fine_dirac(c, aprec, wcur, Zj(j), R));
+    if (hb) BLAS(blas_dcgs2_step_h(bv, vl.data(), j, ucur, wcur, Vhj(j), ws, c->s));
+    else BLAS(blas_dcgs2_step(ft, bv, vl.data(), j, ucur, wcur, ws, c->s));
     SAPMG_CUDA_TRY(cudaMemcpyAsync(c->dch, ws.hcol, sizeof(double2) * 3 * rl, cudaMemcpyDeviceToHost, c->s));
     SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
     n_active = 0;
@@ -543,7 +547,9 @@ static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r
       const double2* ac = c->dch + rl + (size_t)q * ld;
       const double2* nr = c->dch + 2 * rl + (size_t)q * ld;
       if (j > 0) {
-        const cd hs = Hq(q, j, j - 1);
+        // u was hs * (normalised u) (the normalised form) or the unnormalised
+        // new w itself (FP16 basis), whose coefficients a_i, beta carry the scale
+        const cd hs = hb ? cd(1.0, 0.0) : Hq(q, j, j - 1);
         for (int i = 0; i < j; ++i) Hq(q, i, j - 1) += hs * cd(ac[i].x, ac[i].y);
         Hq(q, j, j - 1) = hs * ac[j].x;
       }
@@ -557,7 +563,11 @@ static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r
       ++n_active;
     }
     if (n_active == 0 || j + 1 == m) break;
-    BLAS(blas_axpby2(ft, a, c->w, n, ft, zero, Uj(j + 1), n, n, R, c->s));
+    if (hb) {
+      std::swap(ucur, wcur);
+    } else {
+      BLAS(blas_axpby2(ft, a, wcur, n, ft, zero, Vj(j + 1), n, n, R, c->s));
+    }
     vl.push_back(hb ? Vhj(j) : Vj(j));
   }
   // least squares per system and x += Z y
