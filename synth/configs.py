@@ -17,7 +17,7 @@ restart length on this field (time to solution of the 12 point sources).
 
 ``ref_iterations`` scales the reference arm's timed oracle iteration to a whole
 solve: iterations per right-hand side of the method's plain FP64 form on that
-workload (119 at 32^3 x 64, the count the FP64 form reports; 60 where no
+workload (167 at 32^3 x 64, the count the FP64 form reports; 60 where no
 full-size FP64 solve was run).
 """
 
@@ -41,7 +41,7 @@ WORKLOADS = {
         dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.8,
         rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=1, setup_iters=8, coarse_iters=16, fgmres_m=20, tol=1e-10,
-        precision="bf16", metric=METRIC, ref_iterations=119),
+        precision="bf16", metric=METRIC, ref_iterations=167),
     # Mid-size case for Nsight Compute captures: fields larger than L2, a few GB on the device.
     "32^3x32": dict(
         dims=(32, 32, 32, 32), eps=0.6, gauge_seed=104, c_sw=1.0, m0=-0.8,
