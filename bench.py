@@ -419,6 +419,65 @@ def fp64_form(a, wl, u_h, rhs_h):
             "relres": info.relres, "status": code, "rhs_measured": 1}
 
 
+def run_cgn(a, wl):
+    """The comparison of Sec. 4 (Tables 1-2) on this workload: the multilevel
+    solve (set-up, one warm-up solve, one timed solve) against CG on the normal
+    equations (CGN) for the same right-hand sides, FP32 iteration with FP64
+    updates in the same context, and, with --cgn-fp64, CGN in FP64 on the
+    first right-hand side (x nrhs for the whole set).  Prints one JSON line
+    per part."""
+    import torch
+    import paper_1202_2462_gb300 as G
+    torch.cuda.set_device(0)
+    dims = tuple(wl["dims"])
+    prec = a.precision or wl["precision"]
+    u_h = synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"])
+    rhs_h = make_rhs(wl, dims)
+    nrhs = rhs_h.shape[0]
+    u = torch.from_numpy(u_h).cuda()
+    b = torch.from_numpy(rhs_h).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = G.Solver(u, wl["c_sw"], wl["m0"], **solver_kwargs(wl, prec, nrhs))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    s.solve(b)
+    (z, info, code), mg_s = timed(lambda: s.solve(b))
+    mg = {"s": mg_s, "setup_s": setup_s, "iterations_per_rhs": info.iterations / nrhs, "relres": info.relres,
+          "status": code}
+    tol, cap = wl["tol"], 20000
+    s.cgn_solve(b, tol=tol, maxiter=1, prec=G.MG_FP32)        # workspace allocation and first launches
+    (z, info, code), cgn_s = timed(lambda: s.cgn_solve(b, tol=tol, maxiter=cap, prec=G.MG_FP32))
+    cgn32 = {"s": cgn_s, "iterations_per_rhs": info.iterations / nrhs, "fp64_updates": info.restarts,
+             "relres": info.relres, "status": code}
+    s.close()
+    out = {"metric": "time to solution, multilevel vs CGN (Sec. 4, Tables 1-2)", "workload": a.workload,
+           "nrhs": nrhs, "tol": tol, "m0": wl["m0"], "mg_mixed": mg, "cgn_fp32_fp64_updates": cgn32,
+           "solve_speedup": cgn_s / mg_s, "speedup_with_setup": cgn_s / (mg_s + setup_s), "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+    if a.cgn_fp64:
+        p = G.Solver(u, wl["c_sw"], wl["m0"], n_levels=1, precision="fp64", nrhs_max=1, fgmres_m=2)
+        b1 = b[:1].contiguous()
+        p.cgn_solve(b1, tol=tol, maxiter=1)
+        (z, info, code), t1 = timed(lambda: p.cgn_solve(b1, tol=tol, maxiter=cap))
+        p.close()
+        print(json.dumps({"cgn_fp64": {"s_per_rhs": t1, "s_all_rhs": t1 * nrhs, "iterations": info.iterations,
+                                       "relres": info.relres, "status": code, "rhs_measured": 1}}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,10 +489,15 @@ def main():
     ap.add_argument("--fp64-form", dest="fp64_form", action="store_true", default=True)
     ap.add_argument("--no-fp64-form", dest="fp64_form", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cgn", action="store_true",
+                    help="instead of the bench line: the multilevel solve against CG on the normal equations")
+    ap.add_argument("--cgn-fp64", action="store_true", help="with --cgn: also CGN in FP64 on one right-hand side")
     a = ap.parse_args()
     wl = synth.workload(a.workload)
     if a.impl == "reference":
         return run_reference(a, wl)
+    if a.cgn:
+        return run_cgn(a, wl)
     return run_ours(a, wl)
 
 

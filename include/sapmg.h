@@ -56,6 +56,9 @@ extern "C" {
 /* OR-ed into a prec argument: spinors are in the library's internal blocked
  * layout (see mg_pack_spinor) instead of the canonical one. */
 #define MG_BLOCKED 0x100
+/* OR-ed into dirac_apply's prec: apply D^dagger = gamma5 D gamma5 instead of D
+ * (MG_FP64 or MG_FP32 only). */
+#define MG_DAGGER 0x200
 
 typedef struct mg_ctx mg_ctx;
 
@@ -110,7 +113,8 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
 
 /* out = D in (Sec. 1, Eq. 1.1) for nrhs fields.  prec: MG_FP64 (complex128
  * fields, FP64 links) or the context's mixed precision / MG_FP32 (complex64
- * fields; links and clover stored in that precision), optionally | MG_BLOCKED.
+ * fields; links and clover stored in that precision), optionally | MG_BLOCKED,
+ * and | MG_DAGGER for D^dagger = gamma5 D gamma5 (MG_FP64 / MG_FP32 only).
  * in and out must not overlap.  Asynchronous. */
 int dirac_apply(mg_ctx* ctx, const void* in, void* out, int prec, int nrhs);
 
@@ -129,6 +133,28 @@ int sap_smooth(mg_ctx* ctx, const void* b, void* z, int n_sweeps, int prec, int 
  * MG_ERR_NONFINITE if the recomputed residual is not finite (NaN or Inf in b,
  * or a breakdown of the reduced-precision iteration). */
 int mg_solve(mg_ctx* ctx, const double* b, double* z, int nrhs, mg_solve_info* info);
+
+/* Solve D z = b by CG on the normal equations D^dagger D z = D^dagger b (CGN,
+ * the method the multilevel solver is compared with in Sec. 4, Tables 1-2),
+ * from z = 0, until ||b - D z|| <= tol ||b|| for every right-hand side, where
+ * the residual is the one the CG recursion updates and is recomputed in FP64
+ * (b - D z) before the call returns.  No preconditioner and no multilevel
+ * set-up are used, so any context serves.  b, z: device, canonical
+ * complex128, nrhs fields, solved nrhs_max at a time.
+ * prec: MG_FP64 (every vector, the links and the clover in FP64) or MG_FP32
+ *   (FP32 iteration with the FP32 links and clover of a mixed-form context;
+ *   the iterate is added to the FP64 solution and the residual recomputed in
+ *   FP64 each time it has fallen by 1e-2, keeping the search direction).
+ * maxiter: cap on CG iterations per right-hand side.
+ * info (may be NULL): iterations summed over right-hand sides, restarts = the
+ * FP64 residual recomputations, relres = the largest final FP64 relative
+ * residual.  Allocates 48 bytes per complex entry per right-hand side on the
+ * first call (kept by the context).  Synchronises.  Returns MG_OK,
+ * MG_NOT_CONVERGED (z holds the last iterate), MG_ERR_ARG (tol <= 0,
+ * maxiter < 1, other prec), MG_ERR_STATE (MG_FP32 in a plain-form context),
+ * MG_ERR_NONFINITE, MG_ERR_OOM or MG_ERR_CUDA. */
+int mg_cgn_solve(mg_ctx* ctx, const double* b, double* z, int nrhs, int prec, double tol, int maxiter,
+                 mg_solve_info* info);
 
 /* Free every device buffer the context owns. */
 void mg_destroy(mg_ctx* ctx);

@@ -161,6 +161,12 @@ class WilsonClover:
     def apply_gamma5(self, psi):
         return np.einsum("st,...tb->...sb", GAMMA5, psi)
 
+    def apply_dagger(self, psi):
+        """D^dagger psi, as gamma5 D gamma5 psi: D is gamma5-Hermitian (the
+        hopping projectors satisfy gamma5 (1 - gamma_mu) gamma5 = 1 + gamma_mu,
+        and the clover term is Hermitian and commutes with gamma5)."""
+        return self.apply_gamma5(self.apply(self.apply_gamma5(psi)))
+
     def chirality_of_dof(self):
         """Chirality index (0: gamma_5 = +1, spins 0,1; 1: spins 2,3) per dof."""
         return np.repeat(np.array([0, 0, 1, 1]), 3).reshape(4, 3)

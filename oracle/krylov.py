@@ -13,6 +13,12 @@
   Reading taken: x0 = 0; the stopping test is ||b - A x|| <= tol ||b|| on the
   true residual, recomputed at every restart and whenever the least-squares
   residual estimate has reached the tolerance.
+* ``cgn``: conjugate gradients on the normal equations A^H A x = A^H b, the
+  method the multilevel solver is compared with in Sec. 4 (Tables 1-2: "CGN").
+  Reading taken: x0 = 0; the residual r = b - A x is carried along by the
+  recursion r -= alpha A p and the iteration stops when ||r|| <= tol ||b||
+  (the same test as the flexible GMRES: the residual of A x = b, not of the
+  normal equations) or at the iteration cap.
 """
 
 import numpy as np
@@ -131,3 +137,37 @@ def fgmres(apply, precond, b, m, tol, maxiter, x0=None):
             v.append(w / h[j + 1, j])
         for i in range(len(y)):
             x = x + y[i] * z[i]
+
+
+def cgn(apply, apply_adj, b, tol, maxiter):
+    """CG on A^H A x = A^H b from x0 = 0 (CGN).
+
+    Hestenes-Stiefel CG for the Hermitian positive definite A^H A with the
+    residual of A x = b kept alongside: r = b, s = A^H r, p = s; each step
+    q = A p, alpha = ||s||^2 / ||q||^2, x += alpha p, r -= alpha q,
+    s = A^H r, beta = ||s_new||^2 / ||s_old||^2, p = s + beta p.
+
+    Returns (x, iterations, true relative residual ||b - A x|| / ||b||,
+    converged flag)."""
+    x = np.zeros_like(b, dtype=np.complex128)
+    bnorm = np.sqrt(_dot(b, b).real)
+    if bnorm == 0.0:
+        return x, 0, 0.0, True
+    r = np.array(b, dtype=np.complex128)
+    s = apply_adj(r)
+    p = s.copy()
+    gam = _dot(s, s).real
+    it = 0
+    while np.sqrt(_dot(r, r).real) > tol * bnorm and it < maxiter:
+        q = apply(p)
+        alpha = gam / _dot(q, q).real
+        x = x + alpha * p
+        r = r - alpha * q
+        s = apply_adj(r)
+        gam_new = _dot(s, s).real
+        p = s + (gam_new / gam) * p
+        gam = gam_new
+        it += 1
+    true = b - apply(x)
+    rel = np.sqrt(_dot(true, true).real) / bnorm
+    return x, it, rel, rel <= tol

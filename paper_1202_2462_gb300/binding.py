@@ -26,6 +26,7 @@ MG_FP32 = 1
 MG_FP16 = 2
 MG_BF16 = 3
 MG_BLOCKED = 0x100
+MG_DAGGER = 0x200
 
 PRECISIONS = {"fp64": MG_FP64, "fp32": MG_FP32, "fp16": MG_FP16, "bf16": MG_BF16}
 
@@ -73,6 +74,7 @@ _SIGNATURES = {
     "dirac_apply": (_I, [_VP, _VP, _VP, _I, _I]),
     "sap_smooth": (_I, [_VP, _VP, _VP, _I, _I, _I]),
     "mg_solve": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(MgSolveInfo)]),
+    "mg_cgn_solve": (_I, [_VP, _VP, _VP, _I, _I, ctypes.c_double, _I, ctypes.POINTER(MgSolveInfo)]),
     "mg_destroy": (None, [_VP]),
     "mg_last_error": (ctypes.c_char_p, []),
     "mg_sizeof_params": (ctypes.c_ulong, []),
@@ -171,6 +173,13 @@ def sap_smooth(ctx, b, z, n_sweeps, prec, nrhs=1):
 def mg_solve(ctx, b, z, nrhs=1):
     info = MgSolveInfo()
     code = _check(lib().mg_solve(ctx, _ptr(b), _ptr(z), nrhs, ctypes.byref(info)), "mg_solve")
+    return code, info
+
+
+def mg_cgn_solve(ctx, b, z, nrhs, prec, tol, maxiter):
+    info = MgSolveInfo()
+    code = _check(lib().mg_cgn_solve(ctx, _ptr(b), _ptr(z), nrhs, prec, float(tol), int(maxiter), ctypes.byref(info)),
+                  "mg_cgn_solve")
     return code, info
 
 

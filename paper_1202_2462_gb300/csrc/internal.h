@@ -31,6 +31,35 @@ uint64_t host_splitmix64(uint64_t x);
 // dirac.cu
 int launch_dirac(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
                  cudaStream_t s);
+// dag: D^dagger = gamma5 D gamma5; part != nullptr: also the per-CTA partial
+// sums of ||out||^2 at part[block * nrhs + r] (FP64 and FP32 fields only).
+int launch_dirac_ex(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
+                    bool dag, double* part, cudaStream_t s);
+
+// cgn.cu: CG on the normal equations, R systems at once; every per-system
+// scalar on the device
+struct CgnState {
+  double thr;    // stop when rr <= thr = tol^2 ||b||^2
+  double rr;     // ||r||^2, r = b - D x (recursively updated)
+  double gam;    // ||D^dagger r||^2
+  double alpha, beta;
+  int act;       // the system iterates in the current iteration
+  int its;       // iterations the system has taken
+};
+constexpr int kCgnMaxG = 304;   // CTAs per system of the vector kernels (2 per SM)
+int cgn_grid(size_t n);
+int launch_cgn_residual(int type, const void* b64, const void* t64, void* r, size_t n, int R, double* part, int G,
+                        cudaStream_t s);
+int launch_cgn_xr(int type, void* x, void* r, const void* p, const void* q, size_t n, int R, const CgnState* st,
+                  double* part, int G, cudaStream_t s);
+int launch_cgn_p(int type, void* p, const void* sv, size_t n, int R, const CgnState* st, bool init, int G,
+                 cudaStream_t s);
+int launch_cgn_accum(void* x64, void* x32, size_t n, int R, int G, cudaStream_t s);
+int launch_cgn_gamma(const double* part_s, int nb, const double* part_r, int G, int R, CgnState* st, double tol2,
+                     bool init, cudaStream_t s);
+int launch_cgn_alpha(const double* part_q, int nb, int R, CgnState* st, int maxiter, cudaStream_t s);
+int launch_cgn_beta(const double* part_s, int nb, const double* part_r, int G, int R, CgnState* st, cudaStream_t s);
+int launch_cgn_rr(const double* part_r, int G, int R, CgnState* st, cudaStream_t s);
 
 // learned.cu: the set-up network's layers, gate and optimiser
 int launch_gconv_forward(const Geom& g, const void* U, const void* W, const void* x, void* y, int cin, int cout,

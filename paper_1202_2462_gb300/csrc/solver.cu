@@ -186,6 +186,11 @@ struct mg_ctx {
   int outer_dcgs2 = 1;                     // outer Arnoldi with the delayed second pass (SAPMG_DCGS2=0: two passes)
   int outer_half = 0;                      // mixed form: finished outer basis vectors in FP16 (SAPMG_OUTER_FP16=0: FP32)
   void* Vh = nullptr;                      // the FP16 basis [m][nrhs_max][fine field] (V then holds only the newest vector)
+  // CG on the normal equations (comparison solver; allocated on first use)
+  void* cg = nullptr;                      // its vectors: 48 bytes per complex per system
+  double* cg_part = nullptr;               // partial sums: 2 x [nblocks][nrhs_max] (Dirac), [nrhs_max][kCgnMaxG]
+  CgnState* cg_st = nullptr;               // per-system scalars (device)
+  CgnState* cg_host = nullptr;             // two pinned copies of them
   Prof prof;
 
   void release(void* ptr) {
@@ -211,6 +216,7 @@ struct mg_ctx {
       if (q) cudaFree(q);
     if (hh) cudaFreeHost(hh);
     if (dch) cudaFreeHost(dch);
+    if (cg_host) cudaFreeHost(cg_host);
   }
   size_t fine_n() const { return (size_t)g.V * 12; }
 };
@@ -806,6 +812,160 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
   }
 }
 
+// ------------------------------------------------------------ CGN
+// CG on the normal equations D^dagger D x = D^dagger b, the method Sec. 4
+// compares the multilevel solver with (Tables 1-2), R systems at once, from
+// x = 0, stopping when ||b - D x|| <= tol ||b||.  The residual r = b - D x is
+// updated by the recursion r -= alpha D p, so the test costs nothing extra.
+// FP64 form: vectors, links and clover in FP64.  FP32 form: the iteration in
+// FP32 with the FP32 links and clover; the FP32 iterate is added to the FP64
+// solution and r replaced by the FP64 residual b - D x whenever a system's
+// residual has fallen by kCgnUpdate since the last such update (reliable
+// updates), keeping the search direction.  Either form ends with the FP64
+// residual; if a system is then above the tolerance, CG restarts from it.
+constexpr double kCgnUpdate = 1e-2;
+constexpr int kCgnMaxRefresh = 20;
+
+static int cgn_alloc(mg_ctx* c) {
+  const size_t n = c->fine_n();
+  const int R = c->p.nrhs_max;
+  if (!c->cg) c->cg = c->alloc((size_t)R * n * 48);
+  if (!c->cg_part) c->cg_part = (double*)c->alloc(sizeof(double) * (2 * (size_t)c->g.nblocks * R + (size_t)R * kCgnMaxG));
+  if (!c->cg_st) c->cg_st = (CgnState*)c->alloc(sizeof(CgnState) * R);
+  if (!c->cg || !c->cg_part || !c->cg_st) return fail(MG_ERR_OOM, "CGN workspace");
+  if (!c->cg_host && cudaMallocHost((void**)&c->cg_host, sizeof(CgnState) * 2 * R) != cudaSuccess) {
+    c->cg_host = nullptr;
+    return fail(MG_ERR_OOM, "CGN host buffer");
+  }
+  return MG_OK;
+}
+
+static int cgn_dirac(mg_ctx* c, int type, void* out, const void* in, int R, bool dag, double* part) {
+  ProfScope ps(c->prof, FAM_DIRAC, c->s);
+  count_bytes((double)c->g.V * (R * 2 * 12 * vec_bytes(type) + fields_bytes(type)));
+  return launch_dirac_ex(type, c->g, out, in, type == P64 ? c->U64 : c->U32, type == P64 ? c->A64 : c->A32, R, dag,
+                         part, c->s);
+}
+
+// RAII pair of events for the pipelined convergence check.
+struct EventPair {
+  cudaEvent_t e[2] = {nullptr, nullptr};
+  ~EventPair() {
+    for (auto& q : e)
+      if (q) cudaEventDestroy(q);
+  }
+};
+
+static int cgn_batch(mg_ctx* c, int type, int R, double tol, int maxiter, int& iters, int& updates, double& relres) {
+  const size_t n = c->fine_n();
+  const int nb = c->g.nblocks;
+  const int G = cgn_grid(type == P64 ? n : n / 2);
+  cudaStream_t s = c->s;
+  char* w = (char*)c->cg;
+  const size_t vb = (size_t)R * n * (type == P64 ? 16 : 8);
+  void* x = type == P64 ? c->x64 : (void*)w;
+  void* r = type == P64 ? c->r64 : (void*)(w + vb);
+  void* p = w + (type == P64 ? 0 : 2) * vb;
+  void* q = w + (type == P64 ? 1 : 3) * vb;
+  void* sv = w + (type == P64 ? 2 : 4) * vb;
+  double* part_q = c->cg_part;
+  double* part_s = part_q + (size_t)nb * R;
+  double* part_r = part_s + (size_t)nb * R;
+  CgnState* st = c->cg_st;
+  CgnState* hs = c->cg_host;
+  EventPair ev;
+  for (auto& e : ev.e) SAPMG_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+
+  // x = 0, r = b, s = D^dagger r, p = s
+  SAPMG_CUDA_TRY(cudaMemsetAsync(c->x64, 0, (size_t)R * n * 16, s));
+  if (type == P32) SAPMG_CUDA_TRY(cudaMemsetAsync(x, 0, vb, s));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(c->t64, 0, (size_t)R * n * 16, s));
+  BLAS(launch_cgn_residual(type, c->b64, c->t64, r, n, R, part_r, G, s));
+  TRY(cgn_dirac(c, type, sv, r, R, true, part_s));
+  BLAS(launch_cgn_gamma(part_s, nb, part_r, G, R, st, tol * tol, true, s));
+  BLAS(launch_cgn_p(type, p, sv, n, R, st, true, G, s));
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof(CgnState) * R, cudaMemcpyDeviceToHost, s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<double> bb(R), ref(R);
+  for (int k = 0; k < R; ++k) {
+    bb[k] = hs[k].rr;
+    ref[k] = hs[k].rr;
+    if (!std::isfinite(bb[k])) return fail(MG_ERR_NONFINITE, "non-finite right-hand side");
+  }
+  // x64 += x32 (FP32 form), r = b - D x64 in FP64, rr of every system
+  auto refresh = [&]() -> int {
+    if (type == P32) BLAS(launch_cgn_accum(c->x64, x, n, R, G, s));
+    TRY(cgn_dirac(c, P64, c->t64, c->x64, R, false, nullptr));
+    BLAS(launch_cgn_residual(type, c->b64, c->t64, r, n, R, part_r, G, s));
+    BLAS(launch_cgn_rr(part_r, G, R, st, s));
+    return MG_OK;
+  };
+  updates = 0;
+  int refreshes = 0, it = 0;
+  bool update_now = false;
+  for (;;) {
+    // iterate until no system is active; the host reads the scalars of the
+    // previous iteration while the device runs the current one
+    for (int k = 0;; ++k, ++it) {
+      TRY(cgn_dirac(c, type, q, p, R, false, part_q));
+      BLAS(launch_cgn_alpha(part_q, nb, R, st, maxiter, s));
+      SAPMG_CUDA_TRY(cudaMemcpyAsync(hs + (it & 1) * R, st, sizeof(CgnState) * R, cudaMemcpyDeviceToHost, s));
+      SAPMG_CUDA_TRY(cudaEventRecord(ev.e[it & 1], s));
+      BLAS(launch_cgn_xr(type, x, r, p, q, n, R, st, part_r, G, s));
+      if (update_now) {
+        TRY(refresh());
+        ++updates;
+        update_now = false;
+      }
+      TRY(cgn_dirac(c, type, sv, r, R, true, part_s));
+      BLAS(launch_cgn_beta(part_s, nb, part_r, G, R, st, s));
+      BLAS(launch_cgn_p(type, p, sv, n, R, st, false, G, s));
+      if (k == 0) continue;
+      SAPMG_CUDA_TRY(cudaEventSynchronize(ev.e[(it - 1) & 1]));
+      const CgnState* h = hs + ((it - 1) & 1) * R;
+      bool any = false;
+      for (int j = 0; j < R; ++j) {
+        if (!h[j].act) continue;
+        any = true;
+        if (type == P32 && h[j].rr < kCgnUpdate * kCgnUpdate * ref[j]) update_now = true;
+      }
+      if (!any) break;
+      if (update_now)
+        for (int j = 0; j < R; ++j) ref[j] = h[j].rr;
+    }
+    TRY(refresh());
+    ++refreshes;
+    ++updates;
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof(CgnState) * R, cudaMemcpyDeviceToHost, s));
+    SAPMG_CUDA_TRY(cudaStreamSynchronize(s));
+    bool conv = true, left = false;
+    relres = 0;
+    iters = 0;
+    for (int j = 0; j < R; ++j) {
+      const double rr = hs[j].rr;
+      if (!std::isfinite(rr)) {
+        relres = rr;
+        return fail(MG_ERR_NONFINITE, "the residual became non-finite");
+      }
+      relres = std::max(relres, bb[j] > 0 ? std::sqrt(rr / bb[j]) : 0.0);
+      iters += hs[j].its;
+      if (rr > hs[j].thr) {
+        conv = false;
+        if (hs[j].its < maxiter) left = true;
+      }
+      ref[j] = rr;
+    }
+    if (c->p.verbose)
+      std::fprintf(stderr, "[sapmg] CGN %d iterations (summed), %d updates, max relres %.3e\n", iters, updates, relres);
+    if (conv) return MG_OK;
+    if (!left || refreshes >= kCgnMaxRefresh) return MG_NOT_CONVERGED;
+    // CG again from the FP64 residual: s = D^dagger r, p = s
+    TRY(cgn_dirac(c, type, sv, r, R, true, part_s));
+    BLAS(launch_cgn_gamma(part_s, nb, part_r, G, R, st, 0.0, false, s));
+    BLAS(launch_cgn_p(type, p, sv, n, R, st, true, G, s));
+  }
+}
+
 // ------------------------------------------------------------ set-up
 __global__ void nonfinite_kernel(const double* __restrict__ x, size_t n, int* flag) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -1233,14 +1393,20 @@ void mg_destroy(mg_ctx* c) {
 int dirac_apply(mg_ctx* c, const void* in, void* out, int prec, int nrhs) {
   if (!c || !in || !out || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
   const bool blocked = (prec & MG_BLOCKED) != 0;
+  const bool dag = (prec & MG_DAGGER) != 0;
   prec &= 0xff;
   if (prec < MG_FP64 || prec > MG_BF16) return fail(MG_ERR_ARG, "unknown precision");
+  if (dag && prec != MG_FP64 && prec != MG_FP32) return fail(MG_ERR_ARG, "D^dagger is applied in MG_FP64 or MG_FP32");
+  if (dag && prec == MG_FP32 && !c->U32) return fail(MG_ERR_STATE, "requested precision not set up in this context");
   if (!blocked && nrhs > c->p.nrhs_max) return fail(MG_ERR_ARG, "nrhs exceeds nrhs_max for canonical layout");
   const int t = prec == P64 ? P64 : P32;
   const void* src;
   TRY(stage_in(c, in, prec, blocked, nrhs, &src));
   void* dst = blocked ? out : c->io_b;
-  TRY(fine_dirac(c, prec, dst, src, nrhs));
+  if (dag)
+    TRY(cgn_dirac(c, prec, dst, src, nrhs, true, nullptr));
+  else
+    TRY(fine_dirac(c, prec, dst, src, nrhs));
   if (!blocked) TRY(launch_unpack_spinor(t, dst, t, out, c->g, nrhs, c->s));
   return MG_OK;
 }
@@ -1282,6 +1448,41 @@ int mg_solve(mg_ctx* c, const double* b, double* z, int nrhs, mg_solve_info* inf
   if (info) {
     info->iterations = it_sum;
     info->restarts = rs_sum;
+    info->relres = worst;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->precond_seconds = 0;
+  }
+  return status;
+}
+
+int mg_cgn_solve(mg_ctx* c, const double* b, double* z, int nrhs, int prec, double tol, int maxiter,
+                 mg_solve_info* info) {
+  if (!c || !b || !z || nrhs < 1 || !(tol > 0) || maxiter < 1) return fail(MG_ERR_ARG, "bad argument");
+  const int type = prec == MG_FP64 ? P64 : (prec == MG_FP32 ? P32 : -1);
+  if (type < 0) return fail(MG_ERR_ARG, "CGN runs in MG_FP64 or MG_FP32");
+  if (type == P32 && (!c->U32 || !c->A32)) return fail(MG_ERR_STATE, "the FP32 form needs a mixed-precision context");
+  TRY(cgn_alloc(c));
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t n = c->fine_n();
+  int status = MG_OK, it_sum = 0, up_sum = 0;
+  double worst = 0;
+  for (int r0 = 0; r0 < nrhs; r0 += c->p.nrhs_max) {
+    const int R = std::min(c->p.nrhs_max, nrhs - r0);
+    TRY(launch_pack_spinor(P64, b + (size_t)r0 * n * 2, P64, c->b64, c->g, R, c->s));
+    int it = 0, up = 0;
+    double rel = 0;
+    const int rc = cgn_batch(c, type, R, tol, maxiter, it, up, rel);
+    if (rc < 0) return rc;
+    if (rc == MG_NOT_CONVERGED) status = MG_NOT_CONVERGED;
+    TRY(launch_unpack_spinor(P64, c->x64, P64, z + (size_t)r0 * n * 2, c->g, R, c->s));
+    it_sum += it;
+    up_sum += up;
+    worst = std::max(worst, rel);
+  }
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  if (info) {
+    info->iterations = it_sum;
+    info->restarts = up_sum;
     info->relres = worst;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     info->precond_seconds = 0;

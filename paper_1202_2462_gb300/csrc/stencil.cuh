@@ -167,27 +167,32 @@ __device__ __forceinline__ void hop_bwd(const TG* __restrict__ U, int nblk, int 
 }
 
 // Sum of all eight hops at (blk, loc) with neighbours read from global field f.
-template <int MU, class R, class TS, class TG>
+// DAG: the hops of D^dagger = gamma5 D gamma5, whose projectors are
+// gamma5 (1 -+ gamma_mu) gamma5 = (1 +- gamma_mu) (gamma5 anticommutes with
+// gamma_mu; the clover term commutes with gamma5 and is Hermitian, so it is
+// the same in D and D^dagger).
+template <int MU, class R, class TS, class TG, bool DAG = false>
 __device__ __forceinline__ void hops_global_dir(const Geom& g, const TS* __restrict__ f, const TG* __restrict__ U,
                                                 int blk, int loc, Cplx<R> (&acc)[12]) {
+  constexpr int SF = DAG ? 1 : -1;   // projector sign of the forward hop
   int nb, nl;
   Cplx<R> h[6], gg[6], u[9];
   neighbour(g, blk, loc, MU, 1, nb, nl);
   {
     const TS* q = f + (size_t)nb * 12 * 256 + nl;
-    spin_project_ld<MU, -1, R>([&](int c) { return Io<R, TS>::ldc(q + c * 256); }, h);
+    spin_project_ld<MU, SF, R>([&](int c) { return Io<R, TS>::ldc(q + c * 256); }, h);
   }
   load_link<R>(U, blk, MU, loc, u);
   su3_mul(u, h, gg);
-  spin_reconstruct_add<MU, -1>(gg, acc);
+  spin_reconstruct_add<MU, SF>(gg, acc);
   neighbour(g, blk, loc, MU, -1, nb, nl);
   {
     const TS* q = f + (size_t)nb * 12 * 256 + nl;
-    spin_project_ld<MU, 1, R>([&](int c) { return Io<R, TS>::ldc(q + c * 256); }, h);
+    spin_project_ld<MU, -SF, R>([&](int c) { return Io<R, TS>::ldc(q + c * 256); }, h);
   }
   load_link<R>(U, nb, MU, nl, u);
   su3_dag_mul(u, h, gg);
-  spin_reconstruct_add<MU, 1>(gg, acc);
+  spin_reconstruct_add<MU, -SF>(gg, acc);
 }
 
 template <class R, class TS, class TG>

@@ -74,6 +74,13 @@ class Solver:
         code, info = B.mg_solve(self.ctx, b, z, nrhs)
         return z, info, code
 
+    def cgn_solve(self, b, tol=1e-10, maxiter=100000, prec=B.MG_FP64):
+        """CG on the normal equations (the comparison method): (z, info, code)."""
+        nrhs = 1 if b.dim() == 6 else b.shape[0]
+        z = torch.empty_like(b)
+        code, info = B.mg_cgn_solve(self.ctx, b, z, nrhs, prec, tol, maxiter)
+        return z, info, code
+
     def close(self):
         if self.ctx is not None:
             B.mg_destroy(self.ctx)
