@@ -429,6 +429,8 @@ def run_cgn(a, wl):
     import torch
     import paper_1202_2462_gb300 as G
     torch.cuda.set_device(0)
+    if a.m0 is not None:
+        wl["m0"] = a.m0
     dims = tuple(wl["dims"])
     prec = a.precision or wl["precision"]
     u_h = synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"])
@@ -462,8 +464,13 @@ def run_cgn(a, wl):
     (z, info, code), cgn_s = timed(lambda: s.cgn_solve(b, tol=tol, maxiter=cap, prec=G.MG_FP32))
     cgn32 = {"s": cgn_s, "iterations_per_rhs": info.iterations / nrhs, "fp64_updates": info.restarts,
              "relres": info.relres, "status": code}
+    sigma = None
+    if a.sigma:
+        from paper_1202_2462_gb300.tune import sigma_min
+        sigma = sigma_min(s, s.lat + (4, 3), iters=8)[-1]
     s.close()
     out = {"metric": "time to solution, multilevel vs CGN (Sec. 4, Tables 1-2)", "workload": a.workload,
+           "sigma_min": sigma,
            "nrhs": nrhs, "tol": tol, "m0": wl["m0"], "mg_mixed": mg, "cgn_fp32_fp64_updates": cgn32,
            "solve_speedup": cgn_s / mg_s, "speedup_with_setup": cgn_s / (mg_s + setup_s), "data": "synthetic"}
     print(json.dumps(out), flush=True)
@@ -492,6 +499,9 @@ def main():
     ap.add_argument("--cgn", action="store_true",
                     help="instead of the bench line: the multilevel solve against CG on the normal equations")
     ap.add_argument("--cgn-fp64", action="store_true", help="with --cgn: also CGN in FP64 on one right-hand side")
+    ap.add_argument("--m0", type=float, default=None, help="with --cgn: bare mass instead of the workload's")
+    ap.add_argument("--sigma", action="store_true",
+                    help="with --cgn: also sigma_min(D) by inverse iteration (16 solves of one right-hand side)")
     a = ap.parse_args()
     wl = synth.workload(a.workload)
     if a.impl == "reference":

@@ -4,20 +4,28 @@ seeded fields stand in for them at c_sw = 1.0 (the value of Table 2), with the
 bare mass m0 chosen near the point where the smallest singular value of D
 reaches the stated target (measured by inverse iteration with this library,
 ``python -m paper_1202_2462_gb300.tune``): 8^4 at m0 = -0.19 has
-sigma_min(D) = 1.0e-2; on the 32^3 x 64 field sigma_min(D) falls from 0.11
-(m0 = -0.6) to 0.064 (m0 = -0.8) and rises again beyond (0.16 at -0.9), so
--0.8 is the closest to critical the scan reached.
+sigma_min(D) = 1.0e-2.  On these fields sigma_min(D) is close to
+0.9 |m0 - m_c| on both sides of a critical mass m_c where the lowest real
+eigenvalue of D crosses zero; beyond it (m0 < m_c) D has eigenvalues with
+negative real part, the Schwarz smoother no longer damps them and the
+multilevel iteration count grows quickly, so "near-critical" is taken on the
+physical side m0 > m_c.  32^3 x 64 (eps 0.6): sigma_min = 0.11 at m0 = -0.6,
+0.064 at -0.8, 0.081 / 0.098 / 0.115 / 0.133 at -0.82 / -0.84 / -0.86 / -0.88,
+hence m_c = -0.723; the workload uses m0 = -0.715 with sigma_min = 7.4e-3.
+16^3 x 32 (eps 0.5): sigma_min = 0.096 / 0.0026 / 0.042 / 0.088 / 0.133 / 0.178
+at m0 = -0.40 / -0.50 / -0.55 / -0.60 / -0.65 / -0.70.
 
 ``m0`` is the bare mass in D = 4 + m0 - (hopping)/2 + clover; it maps to the
 hopping parameter as m0 = 1/(2 kappa) - 4.
 
 The 32^3 x 64 method parameters (one post-smoothing sweep, 16 coarse GMRES
 steps) are the fastest of a scan of nu_post, the coarse steps, n_MR and the
-restart length on this field (time to solution of the 12 point sources).
+restart length on this field at m0 = -0.8 (time to solution of the 12 point
+sources); they were kept for m0 = -0.715.
 
 ``ref_iterations`` scales the reference arm's timed oracle iteration to a whole
 solve: iterations per right-hand side of the method's plain FP64 form on that
-workload (167 at 32^3 x 64, the count the FP64 form reports; 60 where no
+workload (93 at 32^3 x 64, the count the FP64 form reports; 60 where no
 full-size FP64 solve was run).
 """
 
@@ -30,23 +38,31 @@ WORKLOADS = {
         rhs="gaussian", rhs_seed=201, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(8,),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
         precision="fp64", metric=METRIC, ref_iterations=60),
-    # Plain vs mixed precision, three levels.
+    # Plain vs mixed precision, three levels (m0 = -0.50: sigma_min = 2.6e-3,
+    # measured with two levels; the three-level form has not been run at it).
     "16^3x32": dict(
-        dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.55,
+        dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.50,
         rhs="z2", rhs_seed=202, n_levels=3, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
         precision="fp16", metric=METRIC, ref_iterations=60),
     # Multi-RHS: 12 spin-colour point sources.
     "32^3x64": dict(
-        dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.8,
+        dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.715,
         rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=1, setup_iters=8, coarse_iters=16, fgmres_m=20, tol=1e-10,
-        precision="bf16", metric=METRIC, ref_iterations=167),
+        precision="bf16", metric=METRIC, ref_iterations=93),
     # Mid-size case for Nsight Compute captures: fields larger than L2, a few GB on the device.
     "32^3x32": dict(
         dims=(32, 32, 32, 32), eps=0.6, gauge_seed=104, c_sw=1.0, m0=-0.8,
         rhs="gaussian", rhs_seed=204, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(12,),
         n_mr=4, nu_post=2, setup_iters=2, coarse_iters=12, fgmres_m=10, tol=1e-10, maxiter=30,
+        precision="bf16", metric=METRIC, ref_iterations=60),
+    # 12 point sources on the 16^3 x 32 field with the 32^3 x 64 method parameters:
+    # the multilevel-vs-CGN comparison across bare masses (bench.py --cgn --m0 ...).
+    "16^3x32-12rhs-solve": dict(
+        dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.55,
+        rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
+        n_mr=4, nu_post=1, setup_iters=8, coarse_iters=16, fgmres_m=20, tol=1e-10, maxiter=2000,
         precision="bf16", metric=METRIC, ref_iterations=60),
     # 12 point sources on a small lattice: Nsight Compute captures of the multi-RHS kernels.
     "16^3x32-12rhs": dict(
