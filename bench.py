@@ -141,6 +141,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks: the job's step time is its slowest rank's
+    (replicas: each rank solves its own right-hand sides, no data exchange)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def make_rhs(wl, dims):
     if wl["rhs"] == "point12":
         return synth.point_sources(dims)
@@ -300,10 +312,7 @@ def run_ours(a, wl):
     n_prof, ms_prof = G.mg_get_profile(s.ctx, G.PROFILE_FAMILIES[dominant])
     bytes_prof = G.mg_get_profile_bytes(s.ctx, G.PROFILE_FAMILIES[dominant])
     G.mg_set_profiling(s.ctx, 0)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ms, world, "cuda")
 
     # end to end through the public API with host buffers
     e2e_steps = max(1, min(a.steps, 2))
