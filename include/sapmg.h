@@ -156,6 +156,23 @@ int mg_solve(mg_ctx* ctx, const double* b, double* z, int nrhs, mg_solve_info* i
 int mg_cgn_solve(mg_ctx* ctx, const double* b, double* z, int nrhs, int prec, double tol, int maxiter,
                  mg_solve_info* info);
 
+/* Harmonic Ritz pairs (Sec. 3, set-up part 2) of an Arnoldi relation
+ * A V_m = V_{m+1} Hbar, on the host: the pairs (theta, y) with
+ * Hbar^H Hbar y = theta H_m^H y (H_m the top m x m part), i.e. A V_m y - theta
+ * V_m y orthogonal to A V_m.  hbar: (m+1) x m complex, column-major, re/im
+ * interleaved (host).  theta: m complex, sorted by |theta|; y: m x m complex,
+ * column k the unit-norm coefficient vector of theta_k (host, caller-owned).
+ * Returns MG_OK, MG_ERR_ARG, or MG_ERR_NONFINITE (H_m singular or the QR
+ * iteration did not converge).  Used by the set-up; exported for checking. */
+int mg_harmonic_ritz(int m, const double* hbar, double* theta, double* y);
+
+/* Eigen-decomposition of a Hermitian n x n complex matrix on the host (the
+ * (DV)^dagger DV reduction of set-up part 2): a column-major, re/im
+ * interleaved; w: n ascending eigenvalues; v: n x n orthonormal eigenvectors
+ * (column k for w[k]).  Returns MG_OK or MG_ERR_ARG.  Used by the set-up;
+ * exported for checking. */
+int mg_eigh(int n, const double* a, double* w, double* v);
+
 /* Free every device buffer the context owns. */
 void mg_destroy(mg_ctx* ctx);
 

@@ -75,6 +75,8 @@ _SIGNATURES = {
     "sap_smooth": (_I, [_VP, _VP, _VP, _I, _I, _I]),
     "mg_solve": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(MgSolveInfo)]),
     "mg_cgn_solve": (_I, [_VP, _VP, _VP, _I, _I, ctypes.c_double, _I, ctypes.POINTER(MgSolveInfo)]),
+    "mg_harmonic_ritz": (_I, [_I, _VP, _VP, _VP]),
+    "mg_eigh": (_I, [_I, _VP, _VP, _VP]),
     "mg_destroy": (None, [_VP]),
     "mg_last_error": (ctypes.c_char_p, []),
     "mg_sizeof_params": (ctypes.c_ulong, []),
@@ -181,6 +183,28 @@ def mg_cgn_solve(ctx, b, z, nrhs, prec, tol, maxiter):
     code = _check(lib().mg_cgn_solve(ctx, _ptr(b), _ptr(z), nrhs, prec, float(tol), int(maxiter), ctypes.byref(info)),
                   "mg_cgn_solve")
     return code, info
+
+
+def mg_harmonic_ritz(hbar):
+    """(m+1) x m complex numpy Hessenberg matrix -> (theta (m,), y (m, m)), host only."""
+    import numpy as np
+    m = hbar.shape[1]
+    h = np.asfortranarray(hbar, dtype=np.complex128)
+    theta = np.zeros(m, dtype=np.complex128)
+    y = np.zeros((m, m), dtype=np.complex128, order="F")
+    _check(lib().mg_harmonic_ritz(m, h.ctypes.data, theta.ctypes.data, y.ctypes.data), "mg_harmonic_ritz")
+    return theta, y
+
+
+def mg_eigh(a):
+    """Hermitian complex numpy matrix -> (ascending eigenvalues, eigenvectors as columns), host only."""
+    import numpy as np
+    n = a.shape[0]
+    am = np.asfortranarray(a, dtype=np.complex128)
+    w = np.zeros(n, dtype=np.float64)
+    v = np.zeros((n, n), dtype=np.complex128, order="F")
+    _check(lib().mg_eigh(n, am.ctypes.data, w.ctypes.data, v.ctypes.data), "mg_eigh")
+    return w, v
 
 
 def mg_destroy(ctx):

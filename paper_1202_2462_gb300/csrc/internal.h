@@ -36,6 +36,11 @@ int launch_dirac(int prec, const Geom& g, void* out, const void* in, const void*
 int launch_dirac_ex(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
                     bool dag, double* part, cudaStream_t s);
 
+// dense_eig.cu: host eigen-solvers of the set-up's second part (column-major
+// complex, re/im interleaved)
+int harmonic_ritz_host(int m, const double* hbar, double* theta, double* y);
+int eigh_host(int n, const double* a, double* w, double* v);
+
 // cgn.cu: CG on the normal equations, R systems at once; every per-system
 // scalar on the device
 struct CgnState {

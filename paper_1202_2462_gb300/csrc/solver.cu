@@ -1490,6 +1490,19 @@ int mg_cgn_solve(mg_ctx* c, const double* b, double* z, int nrhs, int prec, doub
   return status;
 }
 
+int mg_harmonic_ritz(int m, const double* hbar, double* theta, double* y) {
+  const int rc = harmonic_ritz_host(m, hbar, theta, y);
+  if (rc == MG_ERR_ARG) return fail(rc, "bad argument");
+  if (rc == MG_ERR_NONFINITE) return fail(rc, "the harmonic Ritz problem did not converge or is singular");
+  return rc;
+}
+
+int mg_eigh(int n, const double* a, double* w, double* v) {
+  const int rc = eigh_host(n, a, w, v);
+  if (rc == MG_ERR_ARG) return fail(rc, "bad argument");
+  return rc;
+}
+
 int mg_pack_spinor(mg_ctx* c, const void* canonical, void* blocked, int prec, int nrhs) {
   if (!c || !canonical || !blocked || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
   const int t = (prec & 0xff) == P64 ? P64 : P32;
