@@ -85,6 +85,13 @@ typedef struct {
                                  complex128 fine fields used instead of the
                                  random initial test vectors */
   int verbose;
+  int setup2_iters;         /* set-up part 2 (Sec. 3; two levels only): Schwarz
+                               sweeps iota of S(lambda) per harmonic Ritz vector;
+                               0 = part 1 only */
+  const double* setup2_start; /* optional device pointer: start vector of the
+                                 part-2 Arnoldi process on D_c, complex128
+                                 [coarse site][2N] (coarse sites in block order);
+                                 NULL = drawn from seed */
 } mg_params;
 
 typedef struct {

@@ -53,6 +53,8 @@ class MgParams(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("init_vectors", ctypes.c_void_p),
         ("verbose", ctypes.c_int),
+        ("setup2_iters", ctypes.c_int),
+        ("setup2_start", ctypes.c_void_p),
     ]
 
 

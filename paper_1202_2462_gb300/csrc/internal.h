@@ -36,6 +36,10 @@ int launch_dirac(int prec, const Geom& g, void* out, const void* in, const void*
 int launch_dirac_ex(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
                     bool dag, double* part, cudaStream_t s);
 
+// setup2.cu: out = P phi with the FP64 vector-major test vectors v64 (N fine
+// fields, blocked layout) and an FP64 coarse vector phi [nblocks][2N]
+int launch_prolong_v64(const Geom& g, const void* v64, int N, const void* phi, void* out, cudaStream_t s);
+
 // dense_eig.cu: host eigen-solvers of the set-up's second part (column-major
 // complex, re/im interleaved)
 int harmonic_ritz_host(int m, const double* hbar, double* theta, double* y);
@@ -78,5 +82,9 @@ int launch_adam(size_t n, float* p, const float* gr, float* m, float* v, double 
 // sap.cu
 int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
                       int n_mr, int nrhs, cudaStream_t s);
+// sap_shift.cu: the same pass for D - shift[r] (per right-hand side r; device
+// array of nrhs values), the set-up's S(lambda)
+int launch_sap_colour_shifted(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A,
+                              int colour, int n_mr, int nrhs, const double2* shift, cudaStream_t s);
 
 }  // namespace sapmg

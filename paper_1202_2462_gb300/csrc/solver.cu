@@ -1001,6 +1001,207 @@ static int orthonormalise(mg_ctx* c, void* V, int N, size_t n) {
   return MG_OK;
 }
 
+// P (in the cycle's storage) and D_c = P^dagger D P from the global test
+// vectors in V64, which are locally orthonormalised in place (buffers
+// allocated on the first call, refilled on later ones).
+static int build_level0_operators(mg_ctx* c) {
+  const size_t n = c->fine_n();
+  const int N = c->N0;
+  TRY(launch_block_gs0(c->g, c->V64, N, c->s));
+  if (!c->Pv) c->Pv = c->alloc((size_t)N * n * complex_bytes(c->pv_prec));
+  if (!c->Pv) return fail(MG_ERR_OOM, "interpolation");
+  TRY(launch_store_p0(c->pv_prec, c->g, c->V64, c->Pv, N, c->s));
+  // Galerkin coarse operator
+  CoarseLevel& L = c->c1;
+  for (int mu = 0; mu < 4; ++mu) L.cg.L[mu] = c->g.nb[mu];
+  L.cg.nsites = c->g.nblocks;
+  L.cg.n2 = 2 * N;
+  const size_t msz = (size_t)L.cg.nsites * 9 * L.cg.n2 * L.cg.n2;
+  if (!L.M64) L.M64 = c->alloc(msz * 16);
+  if (!L.M64) return fail(MG_ERR_OOM, "coarse operator");
+  TRY(launch_assemble0(c->g, c->V64, c->U64, c->A64, L.M64, N, c->s));
+  L.store = c->dc_prec;
+  if (c->dc_prec == P64) {
+    L.M = L.M64;
+  } else {
+    if (!L.M) L.M = c->alloc(msz * complex_bytes(c->dc_prec));
+    if (!L.M) return fail(MG_ERR_OOM, "coarse operator");
+    TRY(launch_convert(P64, L.M64, c->dc_prec, L.M, msz, c->s));
+    if (c->dc_prec == P32 && c->coarse_fp16 && L.cg.n2 % 8 == 0 && L.cg.n2 <= 64) {
+      if (!L.Mh) L.Mh = c->alloc(msz * complex_bytes(P16));
+      if (!L.Mh) return fail(MG_ERR_OOM, "coarse operator");
+      TRY(launch_convert(P64, L.M64, P16, L.Mh, msz, c->s));
+    }
+  }
+  return MG_OK;
+}
+
+// Bootstrap set-up part 2 (Sec. 3), run once on a two-level hierarchy:
+//  1. N harmonic Ritz pairs (theta_i, phi_i) of D_c from the Arnoldi space of
+//     dimension 2N of a start vector (FP64, two Gram-Schmidt passes; a
+//     subdiagonal entry below 1e-12 of the largest ends the space, which is
+//     then invariant); the small eigenproblem on the host;
+//  2. x_i = S(theta_i)^iota P phi_i: P phi_i with the FP64 local vectors, then
+//     iota sweeps of the shifted Schwarz pass on (D - theta_i) x = 0;
+//  3. V = {x_i} followed by the part-1 vectors (the second half of V2),
+//     orthonormalised (two classical Gram-Schmidt passes, FP64);
+//  4. the N eigenvectors y_k of (DV)^dagger DV (= V^dagger D^dagger D V) with
+//     the smallest eigenvalues give the new test vectors V y_k;
+//  5. P and D_c rebuilt from them.
+static int setup_part2(mg_ctx* c, void* V2) {
+  const mg_params& p = c->p;
+  const size_t n = c->fine_n();
+  const int N = c->N0;
+  CoarseLevel& L = c->c1;
+  const size_t nc = L.n();
+  const int m = (int)std::min<size_t>((size_t)2 * N, nc);
+  const BVec bc = bvec(nc, 1, nc), bf = bvec(n, 1, n);
+  cudaStream_t s = c->s;
+  void* Q = c->alloc((size_t)(m + 2) * nc * 16);            // basis q_0..q_m and phi
+  double2* d = (double2*)c->alloc(sizeof(double2) * 320);   // device scalars
+  if (!Q || !d) return fail(MG_ERR_OOM, "set-up part 2 workspace");
+  double2 *h1 = d, *h2 = d + 72, *coef = d + 144, *nrm = d + 216, *shift = d + 224;
+  auto Qj = [&](int j) { return (void*)((char*)Q + (size_t)j * nc * 16); };
+  auto Vk = [&](int k) { return (void*)((char*)V2 + (size_t)k * n * 16); };
+  void* phi = Qj(m + 1);
+  auto to_dev = [&](double2* dst, const std::vector<double2>& src) -> int {
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(dst, src.data(), sizeof(double2) * src.size(), cudaMemcpyHostToDevice, s));
+    SAPMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return MG_OK;
+  };
+  auto to_host = [&](std::vector<double2>& dst, const double2* src, size_t cnt) -> int {
+    dst.resize(cnt);
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(dst.data(), src, sizeof(double2) * cnt, cudaMemcpyDeviceToHost, s));
+    SAPMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return MG_OK;
+  };
+
+  // 1. Arnoldi on D_c from the start vector
+  if (p.setup2_start) {
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(Qj(0), p.setup2_start, nc * 16, cudaMemcpyDeviceToDevice, s));
+  } else {
+    // uniform in [-1, 1) per real component from SplitMix64 counters (stream 6)
+    std::vector<double2> h0(nc);
+    const uint64_t key = host_splitmix64(host_splitmix64(p.seed) + 6ull);
+    for (size_t i = 0; i < nc; ++i) {
+      const double re = (double)(host_splitmix64(key + 2 * i) >> 11) * 0x1.0p-52 - 1.0;
+      const double im = (double)(host_splitmix64(key + 2 * i + 1) >> 11) * 0x1.0p-52 - 1.0;
+      h0[i] = make_double2(re, im);
+    }
+    TRY(to_dev((double2*)Qj(0), h0));
+  }
+  TRY(dot_to(c, P64, bc, Qj(0), Qj(0), nrm, 1));
+  TRY(blas_normalize(P64, bc, Qj(0), Qj(0), nrm, 1, nullptr, 0, s));
+  std::vector<double2> H((size_t)(m + 1) * m, make_double2(0, 0)), t1, t2, tn;
+  std::vector<const void*> vl;
+  int steps = m;
+  double hmax = 0;
+  for (int j = 0; j < m; ++j) {
+    vl.push_back(Qj(j));
+    void* w = Qj(j + 1);
+    TRY(launch_coarse_apply(P64, L.cg, L.M64, Qj(j), w, 1, s));
+    TRY(blas_multidot(P64, bc, vl.data(), j + 1, w, h1, 1, 0, nullptr, c->partial, s));
+    TRY(blas_multiaxpy(P64, bc, w, vl.data(), j + 1, h1, 1, -1.0, s));
+    TRY(blas_multidot(P64, bc, vl.data(), j + 1, w, h2, 1, 0, nullptr, c->partial, s));
+    TRY(blas_multiaxpy(P64, bc, w, vl.data(), j + 1, h2, 1, -1.0, s));
+    TRY(dot_to(c, P64, bc, w, w, nrm, 1));
+    TRY(to_host(t1, h1, j + 1));
+    TRY(to_host(t2, h2, j + 1));
+    TRY(to_host(tn, nrm, 1));
+    for (int i = 0; i <= j; ++i) {
+      H[(size_t)j * (m + 1) + i] = make_double2(t1[i].x + t2[i].x, t1[i].y + t2[i].y);
+      hmax = std::max(hmax, std::hypot(t1[i].x + t2[i].x, t1[i].y + t2[i].y));
+    }
+    const double beta = std::sqrt(std::max(tn[0].x, 0.0));
+    if (!std::isfinite(beta)) return fail(MG_ERR_NONFINITE, "set-up part 2: non-finite Arnoldi vector");
+    hmax = std::max(hmax, beta);
+    if (beta <= 1e-12 * hmax) {            // invariant space: stop here
+      steps = j + 1;
+      break;
+    }
+    H[(size_t)j * (m + 1) + j + 1] = make_double2(beta, 0);
+    TRY(blas_normalize(P64, bc, w, w, nrm, 1, nullptr, 0, s));
+  }
+  std::vector<double> hb((size_t)2 * (steps + 1) * steps, 0.0), th(2 * (size_t)steps), Y((size_t)2 * steps * steps);
+  for (int j = 0; j < steps; ++j)
+    for (int i = 0; i <= steps; ++i) {
+      const double2 v = H[(size_t)j * (m + 1) + i];
+      hb[2 * ((size_t)j * (steps + 1) + i)] = v.x;
+      hb[2 * ((size_t)j * (steps + 1) + i) + 1] = v.y;
+    }
+  if (harmonic_ritz_host(steps, hb.data(), th.data(), Y.data()) != MG_OK)
+    return fail(MG_ERR_NONFINITE, "set-up part 2: the harmonic Ritz problem failed");
+  const int nr = std::min(N, steps);
+
+  // 2. x_i = S(theta_i)^iota P phi_i into the first nr slots of V2
+  for (int i = 0; i < nr; ++i) {
+    std::vector<double2> y(steps);
+    for (int k = 0; k < steps; ++k) y[k] = make_double2(Y[2 * ((size_t)i * steps + k)], Y[2 * ((size_t)i * steps + k) + 1]);
+    TRY(to_dev(coef, y));
+    SAPMG_CUDA_TRY(cudaMemsetAsync(phi, 0, nc * 16, s));
+    TRY(blas_multiaxpy(P64, bc, phi, vl.data(), steps, coef, 1, 1.0, s));
+    void* xi = Vk(i);
+    TRY(launch_prolong_v64(c->g, c->V64, N, phi, xi, s));
+    TRY(to_dev(shift, std::vector<double2>{make_double2(th[2 * i], th[2 * i + 1])}));
+    if (c->vt == P64) {
+      for (int it = 0; it < p.setup2_iters; ++it)
+        for (int col = 0; col < 2; ++col)
+          TRY(launch_sap_colour_shifted(P64, c->g, xi, c->zero_f, c->U64, c->A64, col, p.n_mr, 1, shift, s));
+    } else {
+      const Scal32 one = scal_all(1.0, 1), zero = scal_all(0.0, 1);
+      TRY(blas_axpby2(P64, one, xi, n, P32, zero, c->io_b, n, n, 1, s));
+      for (int it = 0; it < p.setup2_iters; ++it)
+        for (int col = 0; col < 2; ++col)
+          TRY(launch_sap_colour_shifted(c->prec, c->g, c->io_b, c->zero_f, c->Us, c->As, col, p.n_mr, 1, shift, s));
+      TRY(blas_axpby2(P32, one, c->io_b, n, P64, zero, xi, n, n, 1, s));
+    }
+  }
+  // the part-1 vectors follow the nr new ones (one vector at a time, upwards: no overlap)
+  if (nr < N)
+    for (int k = 0; k < N; ++k)
+      SAPMG_CUDA_TRY(cudaMemcpyAsync(Vk(nr + k), Vk(N + k), n * 16, cudaMemcpyDeviceToDevice, s));
+  const int nv = nr + N;
+
+  // 3. orthonormalise V (classical Gram-Schmidt, two passes)
+  std::vector<const void*> vall;
+  for (int k = 0; k < nv; ++k) {
+    for (int pass = 0; pass < 2 && k > 0; ++pass) {
+      TRY(blas_multidot(P64, bf, vall.data(), k, Vk(k), h1, 1, 0, nullptr, c->partial, s));
+      TRY(blas_multiaxpy(P64, bf, Vk(k), vall.data(), k, h1, 1, -1.0, s));
+    }
+    TRY(dot_to(c, P64, bf, Vk(k), Vk(k), nrm, 1));
+    TRY(blas_normalize(P64, bf, Vk(k), Vk(k), nrm, 1, nullptr, 0, s));
+    vall.push_back(Vk(k));
+  }
+  // 4. G = V^dagger D^dagger D V, its N lowest eigenvectors
+  std::vector<double> G((size_t)2 * nv * nv), ev(nv), EV((size_t)2 * nv * nv);
+  for (int k = 0; k < nv; ++k) {
+    TRY(fine_dirac(c, P64, c->t64, Vk(k), 1));
+    TRY(cgn_dirac(c, P64, c->r64, c->t64, 1, true, nullptr));
+    TRY(blas_multidot(P64, bf, vall.data(), nv, c->r64, h1, 1, 0, nullptr, c->partial, s));
+    TRY(to_host(t1, h1, nv));
+    for (int j = 0; j < nv; ++j) {
+      G[2 * ((size_t)k * nv + j)] = t1[j].x;
+      G[2 * ((size_t)k * nv + j) + 1] = t1[j].y;
+    }
+  }
+  TRY(eigh_host(nv, G.data(), ev.data(), EV.data()));
+  // 5. new test vectors and the rebuilt hierarchy
+  for (int k = 0; k < N; ++k) {
+    std::vector<double2> y(nv);
+    for (int j = 0; j < nv; ++j) y[j] = make_double2(EV[2 * ((size_t)k * nv + j)], EV[2 * ((size_t)k * nv + j) + 1]);
+    TRY(to_dev(coef, y));
+    void* vk = (char*)c->V64 + (size_t)k * n * 16;
+    SAPMG_CUDA_TRY(cudaMemsetAsync(vk, 0, n * 16, s));
+    TRY(blas_multiaxpy(P64, bf, vk, vall.data(), nv, coef, 1, 1.0, s));
+  }
+  TRY(build_level0_operators(c));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(s));
+  c->release(Q);
+  c->release(d);
+  return MG_OK;
+}
+
 static int setup_level0(mg_ctx* c) {
   const size_t n = c->fine_n();
   const int N = c->N0;
@@ -1032,31 +1233,18 @@ static int setup_level0(mg_ctx* c) {
     if (!c->Vs64) return fail(MG_ERR_OOM, "set-up vectors");
     SAPMG_CUDA_TRY(cudaMemcpyAsync(c->Vs64, c->V64, (size_t)N * n * 16, cudaMemcpyDeviceToDevice, c->s));
   }
-  TRY(launch_block_gs0(c->g, c->V64, N, c->s));
-  c->Pv = c->alloc((size_t)N * n * complex_bytes(c->pv_prec));
-  if (!c->Pv) return fail(MG_ERR_OOM, "interpolation");
-  TRY(launch_store_p0(c->pv_prec, c->g, c->V64, c->Pv, N, c->s));
-  // Galerkin coarse operator
-  CoarseLevel& L = c->c1;
-  for (int mu = 0; mu < 4; ++mu) L.cg.L[mu] = c->g.nb[mu];
-  L.cg.nsites = c->g.nblocks;
-  L.cg.n2 = 2 * N;
-  const size_t msz = (size_t)L.cg.nsites * 9 * L.cg.n2 * L.cg.n2;
-  L.M64 = c->alloc(msz * 16);
-  if (!L.M64) return fail(MG_ERR_OOM, "coarse operator");
-  TRY(launch_assemble0(c->g, c->V64, c->U64, c->A64, L.M64, N, c->s));
-  L.store = c->dc_prec;
-  if (c->dc_prec == P64) {
-    L.M = L.M64;
-  } else {
-    L.M = c->alloc(msz * complex_bytes(c->dc_prec));
-    if (!L.M) return fail(MG_ERR_OOM, "coarse operator");
-    TRY(launch_convert(P64, L.M64, c->dc_prec, L.M, msz, c->s));
-    if (c->dc_prec == P32 && c->coarse_fp16 && L.cg.n2 % 8 == 0 && L.cg.n2 <= 64) {
-      L.Mh = c->alloc(msz * complex_bytes(P16));
-      if (!L.Mh) return fail(MG_ERR_OOM, "coarse operator");
-      TRY(launch_convert(P64, L.M64, P16, L.Mh, msz, c->s));
-    }
+  void* V2 = nullptr;
+  if (p.setup2_iters > 0) {                // part 2 keeps the part-1 vectors as the second half of its set
+    V2 = c->alloc((size_t)2 * N * n * 16);
+    if (!V2) return fail(MG_ERR_OOM, "set-up part 2 vectors");
+    SAPMG_CUDA_TRY(cudaMemcpyAsync((char*)V2 + (size_t)N * n * 16, c->V64, (size_t)N * n * 16,
+                                   cudaMemcpyDeviceToDevice, c->s));
+  }
+  TRY(build_level0_operators(c));
+  if (p.setup2_iters > 0) {
+    TRY(setup_part2(c, V2));
+    SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+    c->release(V2);
   }
   return MG_OK;
 }
@@ -1206,6 +1394,8 @@ static int validate(const mg_params* p) {
   if (p->maxiter < 1) return fail(MG_ERR_ARG, "maxiter must be positive");
   if (p->precision < MG_FP64 || p->precision > MG_BF16) return fail(MG_ERR_ARG, "unknown precision");
   if (p->nrhs_max < 1 || p->nrhs_max > 32) return fail(MG_ERR_ARG, "nrhs_max must be in 1..32");
+  if (p->setup2_iters < 0) return fail(MG_ERR_ARG, "negative iteration count");
+  if (p->setup2_iters > 0 && p->n_levels != 2) return fail(MG_ERR_ARG, "set-up part 2 is built for two levels");
   return MG_OK;
 }
 

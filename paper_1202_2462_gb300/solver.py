@@ -31,10 +31,12 @@ class Solver:
     U: complex128 CUDA tensor (Lt, Lz, Ly, Lx, 4, 3, 3) of forward links.
     Keyword arguments are mg_params fields (precision may be 'fp64', 'fp32',
     'fp16', 'bf16'); ``init_vectors`` is an optional complex128 CUDA tensor of
-    initial test vectors (N, Lt, Lz, Ly, Lx, 4, 3).
+    initial test vectors (N, Lt, Lz, Ly, Lx, 4, 3); ``setup2_start`` an optional
+    complex128 CUDA tensor (coarse sites, 2N), the start vector of set-up part 2
+    (used with ``setup2_iters`` > 0).
     """
 
-    def __init__(self, U, c_sw, m0, init_vectors=None, stream=None, **params):
+    def __init__(self, U, c_sw, m0, init_vectors=None, setup2_start=None, stream=None, **params):
         if not (U.is_cuda and U.dtype == torch.complex128 and U.is_contiguous()):
             raise ValueError("U must be a contiguous complex128 CUDA tensor")
         lt, lz, ly, lx = U.shape[:4]
@@ -49,9 +51,14 @@ class Solver:
         if init_vectors is not None:
             self._init = init_vectors.contiguous()
             self.params.init_vectors = self._init.data_ptr()
+        self._start = None
+        if setup2_start is not None:
+            self._start = setup2_start.contiguous()
+            self.params.setup2_start = self._start.data_ptr()
         self.prec = self.params.precision
         self.ctx = B.mg_setup(U, c_sw, m0, self.params)
         self._init = None
+        self._start = None
 
     def spinor(self, nrhs=None, dtype=torch.complex128):
         shape = self.lat + (4, 3) if nrhs is None else (nrhs,) + self.lat + (4, 3)
