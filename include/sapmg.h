@@ -113,8 +113,11 @@ int mg_default_params(mg_params* p);
  *    D = 4 + m0 - hopping/2 + clover (kappa = 1/(2 m0 + 8)).
  * Builds the clover term, packs U in every precision the context needs, runs
  * the bootstrap set-up (Schwarz sweeps on random or given test vectors, kept
- * orthonormal; local orthonormalisation; D_c = P^dagger D P, recursively) and
- * allocates all solve workspace.  Synchronises.  *out receives the context.
+ * orthonormal; local orthonormalisation; D_c = P^dagger D P, recursively),
+ * with setup2_iters > 0 also its second part (harmonic Ritz vectors of D_c
+ * interpolated, smoothed by S(lambda), merged with the part-1 vectors by the
+ * (DV)^dagger DV reduction; P and D_c rebuilt), and allocates all solve
+ * workspace.  Synchronises.  *out receives the context.
  * Errors: MG_ERR_ARG (dims, params), MG_ERR_NONFINITE (U), MG_ERR_OOM, MG_ERR_CUDA. */
 int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx** out);
 
