@@ -81,3 +81,14 @@ def test_null_arguments_rejected():
     assert lib.sap_smooth(None, None, None, 1, 0, 1) == b.MG_ERR_ARG
     assert lib.mg_solve(None, None, None, 1, None) == b.MG_ERR_ARG
     lib.mg_destroy(None)
+
+
+def test_new_entry_points_reject_bad_arguments_on_host():
+    """CGN, the set-up's host eigen-solvers: argument checks before any device work."""
+    b = _lib()
+    lib = b.lib()
+    info = b.MgSolveInfo()
+    assert lib.mg_cgn_solve(None, None, None, 1, b.MG_FP64, 1e-10, 10, ctypes.byref(info)) == b.MG_ERR_ARG
+    assert lib.mg_harmonic_ritz(0, None, None, None) == b.MG_ERR_ARG
+    assert lib.mg_eigh(0, None, None, None) == b.MG_ERR_ARG
+    assert len(lib.mg_last_error()) > 0
