@@ -33,6 +33,8 @@
 #ifndef SAPMG_H
 #define SAPMG_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
