@@ -70,10 +70,10 @@ def bytes_dirac_site(prec):
 
 # the kernels behind each timed family (a family call may issue several launches)
 FAMILY_KERNELS = {
-    "dirac": "dirac_kernel", "sap": "sap_colour_kernel", "coarse": "coarse_apply_mma_kernel",
-    "restrict": "restrict0_mma_kernel", "prolong": "prolong0_mrhs_kernel",
-    "blas": "multidot_partial_f4 + multiaxpy_kernel (outer flexible GMRES, fine vectors)",
-    "coarse_blas": "multidot/multiaxpy/normalize on coarse vectors",
+    "dirac": "dirac_kernel", "sap": "sap_colour_kernel", "coarse": "coarse_apply_mma16_kernel",
+    "restrict": "restrict0_mma_kernel", "prolong": "prolong0_mma_kernel",
+    "blas": "dots2h_partial + dcgs2_coeff_kernel + axpy2h_kernel (outer Arnoldi, FP16 basis)",
+    "coarse_blas": "multidot_h_partial + multiaxpy_h_kernel + normalize_h_kernel + hessenberg_solve_kernel",
 }
 
 
