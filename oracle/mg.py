@@ -13,6 +13,11 @@ the coarsest operator is solved directly, Sec. 3):
   3. z = P e_c  (the subspace correction of Eq. 3.2 from z = 0);
   4. nu_post Schwarz sweeps (Algorithm 1) on A_l z = v starting from z.
   With one level the cycle is nu_post Schwarz sweeps from zero.
+  The block systems of the sweeps are solved by n_MR minimal-residual steps
+  (``block_solver="mr"``, the method's reading) or exactly by dense LU
+  (``block_solver="exact"``: B_i = I D_i^{-1} I^T of Sec. 2), which makes the
+  cycle a linear map whose error propagator the tests compare with the dense
+  product of the Schwarz and coarse-correction propagators.
 * Bootstrap set-up, part 1 (Sec. 3): N test vectors (random, drawn by the
   caller) -> per round: one Schwarz sweep of the smoother's iteration matrix
   on every vector (a sweep on A x = 0 started at x = v), then global modified
@@ -25,7 +30,7 @@ the coarsest operator is solved directly, Sec. 3):
 
 import numpy as np
 
-from .sap import BlockDecomposition, sap, sap_sweep
+from .sap import BlockDecomposition, block_dense_matrices, sap, sap_sweep
 from .aggregation import Aggregation, orthonormalise
 from .coarse import CoarseOperator
 from .krylov import gmres_fixed, fgmres_fixed, fgmres
@@ -44,6 +49,7 @@ DEFAULTS = dict(
     fgmres_m=20,
     tol=1e-10,
     maxiter=500,
+    block_solver="mr",
 )
 
 
@@ -53,6 +59,7 @@ class Level:
         self.blocks = BlockDecomposition(op.dims, sap_block)
         self.agg = None
         self.vectors = None
+        self.exact = None
 
 
 class Multigrid:
@@ -68,6 +75,8 @@ class Multigrid:
         p = dict(DEFAULTS)
         p.update(params)
         self.p = p
+        if p["block_solver"] not in ("mr", "exact"):
+            raise ValueError(f"unknown block solver {p['block_solver']!r}")
         self.levels = [Level(op, p["sap_block"][0])]
         nl = p["n_levels"]
         init = init_vectors
@@ -76,7 +85,8 @@ class Multigrid:
             nvec = p["n_vec"][l]
             v = [np.array(x) for x in init[:nvec]]
             for _ in range(p["setup_iters"]):
-                v = [sap_sweep(lev.op, lev.blocks, np.zeros_like(x), x, p["n_mr"]) for x in v]
+                v = [sap_sweep(lev.op, lev.blocks, np.zeros_like(x), x, p["n_mr"], self.exact_blocks(l))
+                     for x in v]
                 v = orthonormalise(v)
             lev.vectors = v
             lev.agg = Aggregation(lev.op.dims, p["agg"][l], lev.op.dof_shape).build(np.stack(v))
@@ -89,6 +99,16 @@ class Multigrid:
                 nxt = Level.__new__(Level)
                 nxt.op, nxt.blocks, nxt.agg, nxt.vectors = cop, None, None, None
                 self.levels.append(nxt)
+
+    def exact_blocks(self, l):
+        """Dense block matrices of both colours on level l when the block
+        solver is exact (built once), else None (MR block solves)."""
+        if self.p["block_solver"] != "exact":
+            return None
+        lev = self.levels[l]
+        if getattr(lev, "exact", None) is None:
+            lev.exact = tuple(block_dense_matrices(lev.op, lev.blocks, c) for c in (0, 1))
+        return lev.exact
 
     def coarse_solve(self, l, vc):
         """Approximate solve on level l (l >= 1)."""
@@ -103,11 +123,11 @@ class Multigrid:
         p = self.p
         lev = self.levels[l]
         if len(self.levels) == 1:
-            return sap(lev.op, lev.blocks, v, np.zeros_like(v), p["nu_post"], p["n_mr"])
+            return sap(lev.op, lev.blocks, v, np.zeros_like(v), p["nu_post"], p["n_mr"], self.exact_blocks(l))
         vc = lev.agg.restrict(v)
         ec = self.coarse_solve(l + 1, vc)
         z = lev.agg.prolong(ec)
-        return sap(lev.op, lev.blocks, v, z, p["nu_post"], p["n_mr"])
+        return sap(lev.op, lev.blocks, v, z, p["nu_post"], p["n_mr"], self.exact_blocks(l))
 
     def solve(self, b):
         """Outer FGMRES(m) with the cycle as preconditioner."""

@@ -148,11 +148,11 @@ def sap_sweep(op, blocks, b, z, n_mr, exact=None):
     return z
 
 
-def sap(op, blocks, b, z0, n_sweeps, n_mr):
-    """n_sweeps red-black Schwarz iterations from z0."""
+def sap(op, blocks, b, z0, n_sweeps, n_mr, exact=None):
+    """n_sweeps red-black Schwarz iterations from z0 (``exact``: as in sap_sweep)."""
     z = z0
     for _ in range(n_sweeps):
-        z = sap_sweep(op, blocks, b, z, n_mr)
+        z = sap_sweep(op, blocks, b, z, n_mr, exact)
     return z
 
 
