@@ -244,18 +244,24 @@ int mg_coarse_solve(mg_ctx* ctx, int level, const void* in, void* out, int prec)
 
 /* The coarse solve of mg_coarse_solve without any device allocation.
  * The paper has no counterpart: this entry point is for callers that cannot
- * call cudaMalloc at the time they solve -- code running while a CUDA graph is
- * being captured, under an allocator that forbids new device memory, or on a
- * real-time path where an allocation's synchronisation or failure is not
- * acceptable.  Its Krylov basis, Hessenberg matrix and reduction partials live
- * in a fixed 8 MiB array inside the library's own device memory (every device
- * that loads the library holds it until the process exits); the result is
- * written straight to `out`, which starts from zero.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  Every
- * call shares the one array, which keeps the previous call's contents, so
- * calls that overlap on the GPU (other streams, other contexts on the same
- * device) race: serialise them.  A coarse system whose basis does not fit
+ * call cudaMalloc at the time they solve -- code running under an allocator
+ * that forbids new device memory (a memory pool sized up front, or a budget
+ * that another framework owns), or on a real-time path where an allocation's
+ * implicit synchronisation or its failure is not acceptable.  Its Krylov
+ * basis, Hessenberg matrix and reduction partials live in a fixed 8 MiB array
+ * inside the library's own device memory (every device that loads the library
+ * holds it until the process exits); the result is written straight to `out`,
+ * which starts from zero.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  Every call shares the one array,
+ * which keeps the previous call's contents, so calls that overlap on the GPU
+ * (other streams, other contexts on the same device) race: serialise them.
+ * Two-level contexts only (level 1 is then the coarsest level, solved by
+ * fixed-step GMRES); a three-level context gets MG_ERR_STATE.  The Krylov
+ * basis is kept in the context's vector precision (FP64, or FP32 in the mixed
+ * form): where mg_coarse_solve keeps the mixed form's basis in FP16 (the FP16
+ * operator copy exists, 2N a multiple of 8), the two results differ by the
+ * FP16 rounding of that basis.  A coarse system whose basis does not fit
  * (about (coarse_iters + 2) vectors of the level's size) is rejected with
  * MG_ERR_ARG and a message naming the sizes.  Synchronises. */
 int mg_coarse_solve_noalloc(mg_ctx* ctx, int level, const void* in, void* out, int prec);
@@ -314,6 +320,16 @@ int mg_reset_profile(mg_ctx* ctx);
 
 /* Number of kernel launches the library has issued in this process. */
 long long mg_launch_count(void);
+
+/* Measured peaks of the current device, the denominators of the roofline of
+ * the CUDA-core kernels (no paper counterpart; measurement only): FP32 FMA
+ * throughput with scalar FMAs and with the packed two-wide FMA (TFLOP/s,
+ * 2 flop per FMA), and shared-memory load bandwidth (GB/s), each the best of
+ * ten timed launches of a probe kernel that fills every SM, after three
+ * warm-up launches.  stream: a cudaStream_t (NULL: the legacy default
+ * stream).  Allocates a few KB with cudaMallocAsync; synchronises; takes
+ * about a tenth of a second. */
+int mg_probe_peaks(void* stream, double* fp32_tflops, double* fp32x2_tflops, double* smem_gbs);
 
 #ifdef __cplusplus
 }

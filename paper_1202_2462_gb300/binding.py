@@ -101,6 +101,8 @@ _SIGNATURES = {
     "mg_get_profile_bytes": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double)]),
     "mg_reset_profile": (_I, [_VP]),
     "mg_launch_count": (ctypes.c_longlong, []),
+    "mg_probe_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double)]),
     "mg_net_layer_forward": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "mg_net_layer_backward": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP]),
     "mg_net_gate_forward": (_I, [_VP, _I, _VP, _VP]),
@@ -320,6 +322,14 @@ def mg_reset_profile(ctx):
 
 def mg_launch_count():
     return lib().mg_launch_count()
+
+
+def mg_probe_peaks(stream=None):
+    """(FP32 TFLOP/s scalar FMA, FP32 TFLOP/s packed FMA, shared-memory GB/s) of the current device."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    s = ctypes.c_void_p(stream.cuda_stream if stream is not None else None)
+    _check(lib().mg_probe_peaks(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "mg_probe_peaks")
+    return a.value, b.value, c.value
 
 
 def profile_mask(*families):

@@ -80,11 +80,21 @@ int launch_adam(size_t n, float* p, const float* gr, float* m, float* v, double 
                 double eps, int step, cudaStream_t s);
 
 // sap.cu
+// pair_shape >= 0: an even number of right-hand sides in FP32 arithmetic
+// goes to the paired kernel with that launch shape; < 0: the one-RHS-per-CTA kernel.
 int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
-                      int n_mr, int nrhs, cudaStream_t s);
+                      int n_mr, int nrhs, cudaStream_t s, int pair_shape = 0);
+// The paired kernel: two right-hand sides per thread (sap2.cu).  shape 0: two
+// CTAs per SM, rho re-read from shared memory for the update; 1: two CTAs per
+// SM, rho kept in registers; 2: one CTA per SM, rho kept in registers.
+int launch_sap_colour_pair(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
+                           int n_mr, int nrhs, cudaStream_t s, int shape);
 // sap_shift.cu: the same pass for D - shift[r] (per right-hand side r; device
 // array of nrhs values), the set-up's S(lambda)
 int launch_sap_colour_shifted(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A,
                               int colour, int n_mr, int nrhs, const double2* shift, cudaStream_t s);
+
+// Measured FP32 FMA (scalar and packed two-wide) and shared-memory peaks (probe.cu).
+int probe_peaks(cudaStream_t s, double* fp32_tflops, double* fp32x2_tflops, double* smem_gbs);
 
 }  // namespace sapmg

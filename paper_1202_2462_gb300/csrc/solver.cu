@@ -145,6 +145,7 @@ struct mg_ctx {
   int coarse_reorth = 0;  // second Gram-Schmidt pass in the coarse GMRES (SAPMG_COARSE_REORTH=1)
   int generic_coarse = 0; // use the generic coarse stencil kernel (SAPMG_GENERIC_COARSE=1)
   int coarse_tf32 = 1;    // tensor-core (TF32) coarse stencil in the mixed form (SAPMG_COARSE_TF32=0 disables)
+  int sap_shape = 0;      // Schwarz launch shape for an even number of RHS (SAPMG_SAP_SHAPE; -1: one RHS per CTA)
   int restrict_tf32 = 1;  // tensor-core (TF32) multi-RHS level-0 transfers in the mixed form (SAPMG_RESTRICT_TF32=0 disables)
   int coarse_fp16 = 1;    // FP16-stored operator for the tensor-core coarse stencil (SAPMG_COARSE_FP16=0: FP32)
   int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
@@ -236,7 +237,7 @@ static int smoother_sweeps(mg_ctx* c, const void* b, void* z, int n_sweeps, int 
       ProfScope ps(c->prof, FAM_SAP, c->s);
       // one colour: half the sites; b and z read, z written, z read across the block faces
       count_bytes(0.5 * c->g.V * (nrhs * 4 * 12 * vec_bytes(c->prec) + fields_bytes(c->prec)));
-      TRY(launch_sap_colour(c->prec, c->g, z, b, c->Us, c->As, col, c->p.n_mr, nrhs, c->s));
+      TRY(launch_sap_colour(c->prec, c->g, z, b, c->Us, c->As, col, c->p.n_mr, nrhs, c->s, c->sap_shape));
     }
   return MG_OK;
 }
@@ -1559,6 +1560,7 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   c->coarse_reorth = std::getenv("SAPMG_COARSE_REORTH") ? std::atoi(std::getenv("SAPMG_COARSE_REORTH")) : 0;
   c->generic_coarse = std::getenv("SAPMG_GENERIC_COARSE") ? std::atoi(std::getenv("SAPMG_GENERIC_COARSE")) : 0;
   c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
+  c->sap_shape = std::getenv("SAPMG_SAP_SHAPE") ? std::atoi(std::getenv("SAPMG_SAP_SHAPE")) : 0;
   c->restrict_tf32 = std::getenv("SAPMG_RESTRICT_TF32") ? std::atoi(std::getenv("SAPMG_RESTRICT_TF32")) : 1;
   c->outer_dcgs2 = std::getenv("SAPMG_DCGS2") ? std::atoi(std::getenv("SAPMG_DCGS2")) : 1;
   c->coarse_fp16 = std::getenv("SAPMG_COARSE_FP16") ? std::atoi(std::getenv("SAPMG_COARSE_FP16")) : 1;
@@ -1812,6 +1814,9 @@ int mg_coarse_solve_noalloc(mg_ctx* c, int level, const void* in, void* out, int
   if (!c || !in || !out) return fail(MG_ERR_ARG, "bad argument");
   prec &= 0xff;
   if (level != 1 || !c->c1.M) return fail(MG_ERR_STATE, "no coarse operator on that level");
+  if (c->p.n_levels != 2)
+    return fail(MG_ERR_STATE, "the no-alloc coarse solve serves two-level contexts only (on a three-level "
+                              "context level 1 is solved by flexible GMRES with the level-1 cycle)");
   if ((prec == P64) != (c->prec == P64)) return fail(MG_ERR_STATE, "precision does not match the context");
   CoarseLevel& L = c->c1;
   const size_t n = L.n();
@@ -1952,6 +1957,11 @@ int mg_set_profiling(mg_ctx* c, int mask) {
 }
 
 long long mg_launch_count(void) { return g_launches.load(); }
+
+int mg_probe_peaks(void* stream, double* fp32_tflops, double* fp32x2_tflops, double* smem_gbs) {
+  if (!fp32_tflops || !fp32x2_tflops || !smem_gbs) return fail(MG_ERR_ARG, "bad argument");
+  return probe_peaks((cudaStream_t)stream, fp32_tflops, fp32x2_tflops, smem_gbs);
+}
 
 int mg_get_profile(mg_ctx* c, int family, long long* launches, double* ms) {
   if (!c || family < 0 || family >= FAM_N) return fail(MG_ERR_ARG, "bad argument");
