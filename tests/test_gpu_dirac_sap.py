@@ -168,3 +168,52 @@ def test_sap_multi_rhs_matches_single(prec):
         s.smooth(b[k:k + 1].contiguous(), zk, 2)
         assert torch.equal(zk[0], z[k])
     s.close()
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("prec,n_mr", [("fp32", 4), ("fp16", 1), ("bf16", 4), ("bf16", 2)])
+def test_sap_pair_kernel_parity(prec, n_mr, shape, monkeypatch):
+    """The paired Schwarz kernel (two right-hand sides per thread, packed
+    two-wide FP32 arithmetic; every launch shape): two sweeps on four
+    right-hand sides from a nonzero start, with FP32/FP16/BF16 fields, against
+    the oracle's sweeps with the identically rounded fields.  n_MR = 1 takes
+    the kernel's first-and-last MR step path, n_MR = 2 its first and last
+    without a middle step."""
+    monkeypatch.setenv("SAPMG_SAP_SHAPE", str(shape))
+    torch = torch_cuda()
+    dims = (8, 8, 16, 8)
+    u = synth.random_gauge_field(dims, 0.5, 32)
+    m0 = 0.05
+    op = WilsonClover(round_storage(u, prec), m0, 1.0)
+    op.a = round_storage(WilsonClover(u, m0, 1.0).a, prec)
+    bl = BlockDecomposition(dims, (4, 4, 4, 4))
+    b = synth.random_spinor(dims, 33, nvec=4).astype(np.complex64).astype(np.complex128)
+    z0 = (0.1 * synth.random_spinor(dims, 34, nvec=4)).astype(np.complex64).astype(np.complex128)
+    s = _solver(torch, u, 1.0, m0, False, n_mr=n_mr, precision=prec, nrhs_max=4)
+    z = dev(torch, z0, torch.complex64)
+    s.smooth(dev(torch, b, torch.complex64), z, 2)
+    out = host(z).astype(np.complex128)
+    s.close()
+    for k in range(4):
+        ref = sap_sweep(op, bl, b[k], sap_sweep(op, bl, b[k], z0[k], n_mr), n_mr)
+        err = np.max(np.abs(out[k] - ref)) / np.max(np.abs(ref))
+        assert err < 5e-6, (k, err)
+
+
+def test_sap_pair_kernel_matches_single_kernel(monkeypatch):
+    """Two right-hand sides through the paired kernel and through the
+    one-RHS-per-CTA kernel (SAPMG_SAP_SHAPE=-1): the same sweep up to FP32
+    rounding (the two order their sums differently)."""
+    torch = torch_cuda()
+    dims = (8, 8, 8, 16)
+    u = synth.random_gauge_field(dims, 0.5, 35)
+    b = dev(torch, synth.random_spinor(dims, 36, nvec=2), torch.complex64)
+    outs = []
+    for shape in ("0", "-1"):
+        monkeypatch.setenv("SAPMG_SAP_SHAPE", shape)
+        s = _solver(torch, u, 1.0, 0.0, False, precision="bf16", nrhs_max=2)
+        z = torch.zeros_like(b)
+        s.smooth(b, z, 2)
+        outs.append(host(z))
+        s.close()
+    assert np.max(np.abs(outs[0] - outs[1])) / np.max(np.abs(outs[1])) < 2e-6
