@@ -20,6 +20,7 @@ for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
 
 import argparse
 import json
+import platform
 import statistics
 import subprocess
 import sys
@@ -169,59 +170,222 @@ def solver_kwargs(wl, precision, nrhs):
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
-def oracle_sample(wl, steps=1):
-    """Time one multilevel-preconditioned FGMRES iteration of the oracle on a
-    sub-lattice of 1/128 of the workload's volume (same method parameters, a
-    hierarchy from the initial random vectors); returns seconds per iteration
-    at the sub-volume and the sub-lattice dims."""
+# The oracle (plain numpy FP64) cannot solve the full workload in minutes (one
+# Schwarz sweep of 32^3 x 64 alone takes about 100 s on one core), so both CPU
+# legs time a bounded sample and scale it: one outer flexible-GMRES iteration
+# (the two-level cycle with the workload's parameters, one application of D
+# and one Gram-Schmidt step) on a sub-lattice of 1/32 of the volume, run for
+# independent right-hand sides in concurrent processes, one per core used.
+SAMPLE_DIV = (2, 2, 2, 4)
+
+
+def cpu_info():
+    """Host CPU model and core counts (recorded beside every CPU figure)."""
+    info = {"nproc": os.cpu_count(), "machine": platform.machine(), "model": None}
+    try:
+        info["usable_cores"] = len(os.sched_getaffinity(0))
+    except AttributeError:
+        info["usable_cores"] = os.cpu_count()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                info["model"] = ln.split(":", 1)[1].strip()
+                if not info["model"].isdigit():
+                    break
+    except Exception:
+        pass
+    return info
+
+
+def sample_dims(wl):
+    return tuple(d // k for d, k in zip(wl["dims"], SAMPLE_DIV))
+
+
+def _oracle_worker(wl, sub, n_iter, seed, barrier, q):
+    """One process of the sample: build a two-level oracle hierarchy on the
+    sub-lattice (initial random test vectors; the cost of a cycle does not
+    depend on them), wait for the other processes, then time n_iter outer
+    iterations on its own right-hand side."""
+    sys.path.insert(0, ROOT)
     from oracle.dirac import WilsonClover
     from oracle.mg import Multigrid
-    dims = tuple(wl["dims"])
-    sub = (dims[0] // 2, dims[1] // 2, dims[2] // 4, dims[3] // 8)
     u = synth.random_gauge_field(sub, wl["eps"], wl["gauge_seed"])
     op = WilsonClover(u, wl["m0"], wl["c_sw"])
     n = wl["n_vec"][0]
     mg = Multigrid(op, dict(n_levels=2, n_vec=(n,), setup_iters=0, n_mr=wl["n_mr"], nu_post=wl["nu_post"],
                             coarse_iters=wl["coarse_iters"], sap_block=((4, 4, 4, 4),), agg=((4, 4, 4, 4),)),
                    synth.test_vector_draw(sub, n, 1))
-    v = synth.random_spinor(sub, 7)
+    v = synth.random_spinor(sub, 7 + seed)
     v = v / np.linalg.norm(v)
+    barrier.wait()
     times = []
-    for _ in range(steps):
+    for _ in range(n_iter):
         t0 = time.perf_counter()
         z = mg.cycle(0, v)
         w = op.apply(z)
         h = np.vdot(v, w)                 # one orthogonalisation step of the Arnoldi process
         w = w - h * v
         times.append(time.perf_counter() - t0)
-    return times, sub
+    q.put((seed, times))
+
+
+def oracle_sample(wl, n_iter, procs):
+    """Per-iteration wall times of the sample with `procs` concurrent processes
+    (spawned: no CUDA state is inherited): iteration k's wall time is the
+    slowest process's k-th iteration."""
+    import multiprocessing as mp
+    sub = sample_dims(wl)
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(wl, sub, n_iter, k, barrier, q)) for k in range(procs)]
+    for p in ps:
+        p.start()
+    res = [q.get() for _ in ps]
+    for p in ps:
+        p.join()
+    per = [max(t[i] for _, t in res) for i in range(n_iter)]
+    return {"sub": sub, "procs": procs, "wall_per_iter": per}
+
+
+def mem_available():
+    """Host memory available to new processes (bytes), from /proc/meminfo."""
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except Exception:
+        pass
+    return None
+
+
+def oracle_bytes(dims, n_vec=0):
+    """Rough host memory of one oracle process on `dims`: FP64 links (576 B
+    per site), the 12 x 12 clover (2304 B), about ten spinors (192 B each) and
+    n_vec test vectors with their aggregated copies."""
+    return int(np.prod(dims)) * (576 + 2304 + 10 * 192 + 2 * n_vec * 192)
+
+
+def cpu_procs(nrhs, per_proc_bytes=0):
+    """Concurrent oracle processes: one per right-hand side, at most one per
+    usable core, and no more than half the available host memory holds."""
+    n = max(1, min(nrhs, cpu_info()["usable_cores"] or 1))
+    avail = mem_available()
+    if avail and per_proc_bytes:
+        n = max(1, min(n, int(0.5 * avail // per_proc_bytes)))
+    return n
+
+
+def oracle_estimate(wl, smp, timed, iters_per_rhs, nrhs, iters_source):
+    """Scale the sample to the workload: seconds for all right-hand sides =
+    median wall time of a concurrent iteration x volume ratio x outer
+    iterations per right-hand side x rounds of `procs` right-hand sides."""
+    sub = smp["sub"]
+    scale = int(np.prod(wl["dims"])) // int(np.prod(sub))
+    t = statistics.median(timed)
+    rounds = -(-nrhs // smp["procs"])
+    value = t * scale * iters_per_rhs * rounds
+    info = cpu_info()
+    return value, {
+        "value": value, "unit": "s", "cores": smp["procs"], "kind": "oracle", "estimate": True,
+        "cpu": info,
+        "sample": f"{len(timed)} timed outer FGMRES iterations of the oracle (two-level cycle with the workload's "
+                  f"parameters + one D + one Gram-Schmidt step) on {sub[0]}x{sub[1]}x{sub[2]}x{sub[3]} "
+                  f"(1/{scale} of the volume), {smp['procs']} right-hand sides at once in concurrent processes "
+                  f"(one per core); median {t:.2f} s per iteration, scaled by the volume (x{scale}), by "
+                  f"{iters_per_rhs:.1f} outer iterations per right-hand side ({iters_source}) and by "
+                  f"{rounds} round(s) of {smp['procs']} of the {nrhs} right-hand sides: an estimate"}
 
 
 def run_reference(a, wl):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    dims = tuple(wl["dims"])
-    scale = int(np.prod(dims))
-    t_all, sub = oracle_sample(wl, a.warmup + a.steps)
-    t = t_all[a.warmup:]
-    per_iter = statistics.mean(t) * (scale / int(np.prod(sub)))
-    iters = wl["ref_iterations"]
     nrhs = 12 if wl["rhs"] == "point12" else 1
-    value = per_iter * iters * nrhs
+    if wl.get("fp64_iterations_per_rhs") is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no measured FP64 iteration count stored for "
+                                                              f"workload {a.workload}"}), flush=True)
+        return 0
+    procs = cpu_procs(nrhs, oracle_bytes(sample_dims(wl), wl["n_vec"][0]))
+    smp = oracle_sample(wl, a.warmup + a.steps, procs)
+    timed = smp["wall_per_iter"][a.warmup:]
+    value, cpu = oracle_estimate(wl, smp, timed, wl["fp64_iterations_per_rhs"], nrhs,
+                                 "the FP64 method's count on this workload, stored with the workload")
     line = {
         "impl": "reference", "metric": wl["metric"], "value": value, "unit": "s", "n_gpus": 0,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(t) * 1e3,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(timed) * 1e3,
+        "step": "one concurrent sample iteration (see cpu_baseline.sample); value is the scaled estimate",
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": wl_config(wl, a.workload, "fp64"),
-        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": f"one oracle FGMRES iteration (two-level cycle + D + one Gram-Schmidt step) "
-                                   f"on {sub[0]}x{sub[1]}x{sub[2]}x{sub[3]} = 1/{scale // int(np.prod(sub))} "
-                                   f"of the volume, scaled by volume, x{iters} iterations per RHS "
-                                   f"(documented estimate) x{nrhs} RHS"},
+        "data": "synthetic", "config": wl_config(wl, a.workload, "fp64"), "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def _oracle_kernel_worker(dims, eps, seed, barrier, q):
+    """One process of the per-kernel study: one oracle D application and one
+    Schwarz sweep (n_MR = 4) of one right-hand side on `dims`."""
+    sys.path.insert(0, ROOT)
+    from oracle.dirac import WilsonClover
+    from oracle.sap import BlockDecomposition, sap_sweep
+    op = WilsonClover(synth.random_gauge_field(dims, eps, 1), -0.5, 1.0)
+    x = synth.random_spinor(dims, 2 + seed)
+    bl = BlockDecomposition(dims, (4, 4, 4, 4))
+    barrier.wait()
+    t0 = time.perf_counter()
+    op.apply(x)
+    t1 = time.perf_counter()
+    sap_sweep(op, bl, x, np.zeros_like(x), 4)
+    t2 = time.perf_counter()
+    q.put((seed, t1 - t0, t2 - t1))
+
+
+def oracle_study(a):
+    """The CPU oracle on the host cores (one JSON line per measurement): one D
+    application and one Schwarz sweep at every lattice size, on one core and
+    with one right-hand side per core in concurrent processes; then the whole
+    two-level FP64 solve of the 8^4 workload on one core."""
+    import multiprocessing as mp
+    info = cpu_info()
+    print(json.dumps({"oracle_study": "cpu", "mem_available": mem_available(), **info}), flush=True)
+    ctx = mp.get_context("spawn")
+    sizes = [(8, 8, 8, 8), (16, 16, 16, 16), (16, 16, 16, 32), (32, 32, 32, 64)]
+    for dims in sizes:
+        for procs in sorted({1, cpu_procs(12, oracle_bytes(dims))}):
+            barrier = ctx.Barrier(procs)
+            q = ctx.Queue()
+            ps = [ctx.Process(target=_oracle_kernel_worker, args=(dims, 0.5, k, barrier, q)) for k in range(procs)]
+            for p in ps:
+                p.start()
+            res = [q.get() for _ in ps]
+            for p in ps:
+                p.join()
+            d = max(r[1] for r in res)
+            sw = max(r[2] for r in res)
+            v = int(np.prod(dims))
+            print(json.dumps({"oracle_study": "kernels", "dims": list(dims), "processes": procs,
+                              "dirac_s": d, "sweep_s": sw, "dirac_sites_per_s": procs * v / d,
+                              "sweep_sites_per_s": procs * v / sw}), flush=True)
+    from oracle.dirac import WilsonClover
+    from oracle.mg import Multigrid
+    wl = synth.workload("8^4")
+    dims = tuple(wl["dims"])
+    op = WilsonClover(synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"]), wl["m0"], wl["c_sw"])
+    b = synth.random_spinor(dims, wl["rhs_seed"])
+    t0 = time.perf_counter()
+    mg = Multigrid(op, dict(n_levels=2, n_vec=tuple(wl["n_vec"]), setup_iters=wl["setup_iters"], n_mr=wl["n_mr"],
+                            nu_post=wl["nu_post"], coarse_iters=wl["coarse_iters"], fgmres_m=wl["fgmres_m"],
+                            tol=wl["tol"], sap_block=((4, 4, 4, 4),), agg=((4, 4, 4, 4),)),
+                   synth.test_vector_draw(dims, wl["n_vec"][0], 1))
+    t1 = time.perf_counter()
+    z, it, hist, ok = mg.solve(b)
+    t2 = time.perf_counter()
+    rel = float(np.linalg.norm(b - op.apply(z)) / np.linalg.norm(b))
+    print(json.dumps({"oracle_study": "solve", "workload": "8^4", "cores": 1, "setup_s": t1 - t0,
+                      "solve_s": t2 - t1, "iterations": it, "relres": rel, "converged": bool(ok)}), flush=True)
     return 0
 
 
@@ -386,14 +550,13 @@ def run_ours(a, wl):
     if a.fp64_form and rank == 0:
         line["fp64_form"] = fp64_form(a, wl, u_h, rhs_h)
     if rank == 0 and world == 1 and not a.no_cpu:
-        t, sub = oracle_sample(wl, 2)
-        per_iter = t[-1] * (v / int(np.prod(sub)))
-        it_rhs = statistics.mean(iters) / nrhs
-        line["cpu_baseline"] = {
-            "value": per_iter * it_rhs * nrhs, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"one oracle FGMRES iteration (two-level cycle + D + one Gram-Schmidt step) on "
-                      f"{sub[0]}x{sub[1]}x{sub[2]}x{sub[3]} ({t[-1]:.2f} s), scaled by volume x{v // int(np.prod(sub))}"
-                      f" and by this run's {it_rhs:.1f} iterations per RHS x{nrhs} RHS"}
+        f64 = line.get("fp64_form")
+        if f64:
+            it_rhs, src = f64["iterations_per_rhs"], "this run's FP64 form"
+        else:
+            it_rhs, src = statistics.mean(iters) / nrhs, "this run's mixed form (the FP64 form was not run)"
+        smp = oracle_sample(wl, 3, cpu_procs(nrhs, oracle_bytes(sample_dims(wl), wl["n_vec"][0])))
+        line["cpu_baseline"] = oracle_estimate(wl, smp, smp["wall_per_iter"][1:], it_rhs, nrhs, src)[1]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -401,13 +564,11 @@ def run_ours(a, wl):
     return 0
 
 
-def nrhs_per_launch(nrhs):
-    return 1
-
-
 def fp64_form(a, wl, u_h, rhs_h):
-    """Time-to-solution of the plain FP64 form (same method, FP64 everywhere) on
-    the first right-hand side; the 12-RHS figure is that time x nrhs."""
+    """Time-to-solution of the plain FP64 form (same method, FP64 everywhere,
+    one right-hand side at a time): the first `--fp64-rhs` right-hand sides
+    (default all) solved and timed one after the other; s_all_rhs is their sum
+    scaled to all right-hand sides when fewer were measured."""
     import torch
     import paper_1202_2462_gb300 as G
     u = torch.from_numpy(u_h).cuda()
@@ -418,14 +579,22 @@ def fp64_form(a, wl, u_h, rhs_h):
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
     del u
-    b = torch.from_numpy(rhs_h[:1]).cuda()
-    t0 = time.perf_counter()
-    z, info, code = s.solve(b)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter() - t0
+    n_all = rhs_h.shape[0]
+    n = n_all if a.fp64_rhs is None else max(1, min(a.fp64_rhs, n_all))
+    total, its, rel, codes = 0.0, [], 0.0, []
+    for r in range(n):
+        b = torch.from_numpy(rhs_h[r:r + 1]).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        z, info, code = s.solve(b)
+        torch.cuda.synchronize()
+        total += time.perf_counter() - t0
+        its.append(info.iterations)
+        rel = max(rel, info.relres)
+        codes.append(code)
     s.close()
-    return {"setup_s": setup, "s_per_rhs": t1, "s_all_rhs": t1 * rhs_h.shape[0], "iterations": info.iterations,
-            "relres": info.relres, "status": code, "rhs_measured": 1}
+    return {"setup_s": setup, "s_measured": total, "s_all_rhs": total * n_all / n, "rhs_measured": n,
+            "iterations": its, "iterations_per_rhs": statistics.mean(its), "relres": rel, "status": codes}
 
 
 def run_cgn(a, wl):
@@ -494,6 +663,64 @@ def run_cgn(a, wl):
     return 0
 
 
+def run_kernel(a, wl):
+    """One kernel family of the path alone at the workload's lattice size
+    (inputs resident on the device, blocked layout, 3 warm-up and --steps
+    timed launches, CUDA events on the library's stream): 'dirac' applies D
+    (storage precision of the workload) to --nrhs right-hand sides, 'sap' runs
+    one Schwarz sweep (two colour passes) on them.  Prints one JSON line with
+    the time per launch and the algorithmic bytes and flops behind it; the
+    process launches nothing else in between, so it is the target of the
+    profiles of these kernels."""
+    import torch
+    import paper_1202_2462_gb300 as G
+    torch.cuda.set_device(0)
+    dims = tuple(wl["dims"])
+    prec = a.precision or wl["precision"]
+    nrhs = a.nrhs
+    u = torch.from_numpy(synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"])).cuda()
+    s = G.Solver(u, wl["c_sw"], wl["m0"], n_levels=1, precision=prec, nrhs_max=nrhs, n_mr=wl["n_mr"], fgmres_m=1)
+    del u
+    v = int(np.prod(dims))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    x = torch.randn((nrhs * v * 12, 2), device="cuda", generator=g).view(torch.complex64).reshape(-1)
+    y = torch.zeros_like(x)
+    pd = G.PRECISIONS[prec] | G.MG_BLOCKED
+    stream = torch.cuda.current_stream()
+    if a.kernel == "dirac":
+        launch = lambda: G.dirac_apply(s.ctx, x, y, pd, nrhs)
+        per_launch = 1
+        alg = v * (nrhs * 2 * 12 * 8 + bytes_sap_fields(prec))
+        flop = v * nrhs * flops_dirac_site()
+    else:
+        launch = lambda: G.sap_smooth(s.ctx, x, y, 1, pd, nrhs)
+        per_launch = 2                                   # two colour passes per sweep
+        alg = (v // 2) * (nrhs * bytes_sap_spinor(prec) + bytes_sap_fields(prec))
+        flop = (v // 2) * nrhs * flops_sap_site(wl["n_mr"])
+    for _ in range(3):
+        launch()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    G.mg_sync(s.ctx)
+    t = e0.elapsed_time(e1) / 1e3 / (a.steps * per_launch)
+    hbm, kind = load_peaks()
+    out = {"kernel": a.kernel, "workload": a.workload, "lattice": list(dims), "storage": prec, "nrhs": nrhs,
+           "launches_timed": a.steps * per_launch, "ms_per_launch": t * 1e3,
+           "alg_bytes_per_launch": alg, "alg_gbs": alg / t / 1e9, "hbm_frac": alg / t / 1e9 / hbm,
+           "flop_per_launch": flop, "tflops": flop / t / 1e12, "peak_hbm_gbs": hbm, "peak_kind": kind,
+           "sap_shape": os.environ.get("SAPMG_SAP_SHAPE", "default")}
+    s.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -505,6 +732,13 @@ def main():
     ap.add_argument("--fp64-form", dest="fp64_form", action="store_true", default=True)
     ap.add_argument("--no-fp64-form", dest="fp64_form", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kernel", choices=["dirac", "sap"], default=None,
+                    help="instead of the bench line: time one kernel family alone (see run_kernel)")
+    ap.add_argument("--nrhs", type=int, default=1, help="with --kernel: right-hand sides per launch")
+    ap.add_argument("--oracle-study", action="store_true",
+                    help="instead of the bench line: oracle kernel timings at every size and the 8^4 oracle solve")
+    ap.add_argument("--fp64-rhs", type=int, default=None,
+                    help="right-hand sides the FP64 form solves and times (default: all)")
     ap.add_argument("--cgn", action="store_true",
                     help="instead of the bench line: the multilevel solve against CG on the normal equations")
     ap.add_argument("--cgn-fp64", action="store_true", help="with --cgn: also CGN in FP64 on one right-hand side")
@@ -513,6 +747,10 @@ def main():
                     help="with --cgn: also sigma_min(D) by inverse iteration (16 solves of one right-hand side)")
     a = ap.parse_args()
     wl = synth.workload(a.workload)
+    if a.oracle_study:
+        return oracle_study(a)
+    if a.kernel:
+        return run_kernel(a, wl)
     if a.impl == "reference":
         return run_reference(a, wl)
     if a.cgn:

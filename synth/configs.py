@@ -23,10 +23,12 @@ steps) are the fastest of a scan of nu_post, the coarse steps, n_MR and the
 restart length on this field at m0 = -0.8 (time to solution of the 12 point
 sources); they were kept for m0 = -0.715.
 
-``ref_iterations`` scales the reference arm's timed oracle iteration to a whole
-solve: iterations per right-hand side of the method's plain FP64 form on that
-workload (93 at 32^3 x 64, the count the FP64 form reports; 60 where no
-full-size FP64 solve was run).
+``fp64_iterations_per_rhs`` scales the reference arm's timed oracle iteration
+to a whole solve: the outer iterations per right-hand side of the method's
+plain FP64 form on that workload, as the library's FP64 form reports them
+(the FP64 form computes the oracle's iteration: its cycle matches the
+oracle's to 1e-11); None where no full-size FP64 solve was run (the reference
+arm then reports itself unavailable for that workload).
 """
 
 METRIC = "time-to-solution to 1e-10 at 32^3x64 (mixed vs FP64); Dirac-apply HBM GB/s"
@@ -37,39 +39,39 @@ WORKLOADS = {
         dims=(8, 8, 8, 8), eps=0.3, gauge_seed=101, c_sw=1.0, m0=-0.19,
         rhs="gaussian", rhs_seed=201, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(8,),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
-        precision="fp64", metric=METRIC, ref_iterations=60),
+        precision="fp64", metric=METRIC, fp64_iterations_per_rhs=None),
     # Plain vs mixed precision, three levels (m0 = -0.50: sigma_min = 2.6e-3,
     # measured with two levels; the three-level form has not been run at it).
     "16^3x32": dict(
         dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.50,
         rhs="z2", rhs_seed=202, n_levels=3, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=2, setup_iters=3, coarse_iters=12, fgmres_m=20, tol=1e-10,
-        precision="fp16", metric=METRIC, ref_iterations=60),
+        precision="fp16", metric=METRIC, fp64_iterations_per_rhs=None),
     # Multi-RHS: 12 spin-colour point sources.
     "32^3x64": dict(
         dims=(32, 32, 32, 64), eps=0.6, gauge_seed=103, c_sw=1.0, m0=-0.715,
         rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=1, setup_iters=8, coarse_iters=16, fgmres_m=20, tol=1e-10,
-        precision="bf16", metric=METRIC, ref_iterations=93),
+        precision="bf16", metric=METRIC, fp64_iterations_per_rhs=93),
     # Mid-size case for Nsight Compute captures: fields larger than L2, a few GB on the device.
     "32^3x32": dict(
         dims=(32, 32, 32, 32), eps=0.6, gauge_seed=104, c_sw=1.0, m0=-0.8,
         rhs="gaussian", rhs_seed=204, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(12,),
         n_mr=4, nu_post=2, setup_iters=2, coarse_iters=12, fgmres_m=10, tol=1e-10, maxiter=30,
-        precision="bf16", metric=METRIC, ref_iterations=60),
+        precision="bf16", metric=METRIC, fp64_iterations_per_rhs=None),
     # 12 point sources on the 16^3 x 32 field with the 32^3 x 64 method parameters:
     # the multilevel-vs-CGN comparison across bare masses (bench.py --cgn --m0 ...).
     "16^3x32-12rhs-solve": dict(
         dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.55,
         rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(20, 20),
         n_mr=4, nu_post=1, setup_iters=8, coarse_iters=16, fgmres_m=20, tol=1e-10, maxiter=2000,
-        precision="bf16", metric=METRIC, ref_iterations=60),
+        precision="bf16", metric=METRIC, fp64_iterations_per_rhs=None),
     # 12 point sources on a small lattice: Nsight Compute captures of the multi-RHS kernels.
     "16^3x32-12rhs": dict(
         dims=(16, 16, 16, 32), eps=0.5, gauge_seed=102, c_sw=1.0, m0=-0.55,
         rhs="point12", rhs_seed=0, n_levels=2, agg=((4, 4, 4, 4),), n_vec=(20,),
         n_mr=4, nu_post=2, setup_iters=2, coarse_iters=12, fgmres_m=6, tol=1e-10, maxiter=12,
-        precision="bf16", metric=METRIC, ref_iterations=60),
+        precision="bf16", metric=METRIC, fp64_iterations_per_rhs=None),
 }
 
 
