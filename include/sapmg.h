@@ -133,7 +133,9 @@ int dirac_apply(mg_ctx* ctx, const void* in, void* out, int prec, int nrhs);
 /* n_sweeps red-black Schwarz sweeps (Sec. 2, Algorithm 1) on D z = b, updating z
  * in place (z is the starting guess).  Each sweep: for colour 0 then 1,
  * r = b - D z and z += (n_MR MR steps of the block system) on every block of
- * that colour.  prec and layout as for dirac_apply.  Asynchronous. */
+ * that colour.  prec and layout as for dirac_apply.  Asynchronous (a bounded
+ * device wait that gives up is reported by the next synchronising call, e.g.
+ * mg_sync). */
 int sap_smooth(mg_ctx* ctx, const void* b, void* z, int n_sweeps, int prec, int nrhs);
 
 /* Solve D z = b for nrhs right-hand sides to ||b - D z|| <= tol ||b|| (Sec. 4).
@@ -320,6 +322,21 @@ int mg_reset_profile(mg_ctx* ctx);
 
 /* Number of kernel launches the library has issued in this process. */
 long long mg_launch_count(void);
+
+/* Wait for the context's stream and report a device-side wait that gave up
+ * since the last check (MG_ERR_TIMEOUT; the flag is then cleared).  The
+ * asynchronous entry points (sap_smooth, dirac_apply, the transfers) leave
+ * such a flag for the next synchronising call; this one only checks it. */
+int mg_sync(mg_ctx* ctx);
+
+/* Bound on the main-loop waits of the kernels that stage data with bulk
+ * copies (the coarse stencils, the block-resident Schwarz pass): a wait that
+ * has not completed after `spins` tries gives up, the kernel drains its copies
+ * in flight (those waits keep the default bound) and raises the flag that the
+ * synchronising calls report as MG_ERR_TIMEOUT.  spins < 0 restores the
+ * default (2^22 tries); 0 makes every such wait give up at once, which tests
+ * of the timeout path use.  Diagnostics only.  Synchronises. */
+int mg_set_wait_limit(mg_ctx* ctx, int spins);
 
 /* Measured peaks of the current device, the denominators of the roofline of
  * the CUDA-core kernels (no paper counterpart; measurement only): FP32 FMA

@@ -101,6 +101,8 @@ _SIGNATURES = {
     "mg_get_profile_bytes": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double)]),
     "mg_reset_profile": (_I, [_VP]),
     "mg_launch_count": (ctypes.c_longlong, []),
+    "mg_sync": (_I, [_VP]),
+    "mg_set_wait_limit": (_I, [_VP, _I]),
     "mg_probe_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)]),
     "mg_net_layer_forward": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
@@ -322,6 +324,14 @@ def mg_reset_profile(ctx):
 
 def mg_launch_count():
     return lib().mg_launch_count()
+
+
+def mg_sync(ctx):
+    return _check(lib().mg_sync(ctx), "mg_sync")
+
+
+def mg_set_wait_limit(ctx, spins):
+    return _check(lib().mg_set_wait_limit(ctx, spins), "mg_set_wait_limit")
 
 
 def mg_probe_peaks(stream=None):

@@ -38,13 +38,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: true when the phase completed, false after kMaxSpins tries.
+// Bounded wait: true when the phase completed, false after `spins` tries
+// (kMaxSpins by default).
 constexpr int kMaxSpins = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kMaxSpins; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int spins = kMaxSpins) {
+  for (int i = 0; i < spins; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+
+// The device error word of a context: err[0] is the flag a wait that gave up
+// raises, err[1] the bound on the main-loop waits of the bulk-copy kernels
+// (kMaxSpins unless a test lowers it to drive the timeout path; the drain
+// waits after a failure always use kMaxSpins).
+__device__ __forceinline__ int wait_spins(const int* err) { return err[1]; }
 
 
 }  // namespace sapmg

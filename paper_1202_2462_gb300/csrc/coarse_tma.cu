@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(256) coarse_apply_tma_kernel(const float2* __r
                                                                float2* __restrict__ out, CGeom c, int r0,
                                                                int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
+  const int spins = wait_spins(err);
   __shared__ __align__(8) uint64_t bar[2];
   const int n2 = c.n2;
   const int tile = n2 * n2;                                   // complex entries per block
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(256) coarse_apply_tma_kernel(const float2* __r
       }
       for (int e = tid; e < RB * n2; e += blockDim.x) xs[e] = xr[(size_t)(e / n2) * fs + (size_t)nb * n2 + e % n2];
     }
-    const bool waited = mbar_wait(&bar[t & 1], (uint32_t)((t >> 1) & 1));
+    const bool waited = mbar_wait(&bar[t & 1], (uint32_t)((t >> 1) & 1), spins);
     if (__syncthreads_or(!waited)) {          // uniform decision: every thread leaves together
       tfail = t;
       break;
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restr
                                                                float2* __restrict__ out, CGeom c, int r0, int nr,
                                                                int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
+  const int spins = wait_spins(err);
   __shared__ __align__(8) uint64_t bar[kStages];
   const int n2 = c.n2;
   const int xst = n2 + 2;                                     // padded row stride of the staged vectors
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restr
       issue(t + kStages - 1);
     }
     const int st = t % kStages;
-    const bool waited = mbar_wait(&bar[st], (uint32_t)((t / kStages) & 1));
+    const bool waited = mbar_wait(&bar[st], (uint32_t)((t / kStages) & 1), spins);
     if (__syncthreads_or(!waited)) {
       tfail = t;
       break;
@@ -297,7 +299,9 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restr
     // wait (bounded) for this CTA's copies still in flight before leaving
     if (tid == 0) {
       atomicExch(err, 1);
-      for (int u = tfail; u < T && u < tfail + kStages - 1; ++u) mbar_wait(&bar[u % kStages], (uint32_t)((u / kStages) & 1));
+      // stages tfail .. tfail + kStages - 1 were issued (the copy of t + kStages - 1
+      // goes out before the wait of t): let every one of them land
+      for (int u = tfail; u < T && u < tfail + kStages; ++u) mbar_wait(&bar[u % kStages], (uint32_t)((u / kStages) & 1));
     }
     __syncthreads();
   }
@@ -332,6 +336,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
                                                                  float2* __restrict__ out, CGeom c, int r0, int nr,
                                                                  int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
+  const int spins = wait_spins(err);
   __shared__ __align__(8) uint64_t bar[ST];
   const int n2 = N2 > 0 ? N2 : c.n2;                         // N2 > 0: block size fixed at compile time
   const int xst = n2 + 4;                                     // padded row stride (conflict-free fragment loads)
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
       issue(t + ST - 1);
     }
     const int st = t % ST;
-    const bool waited = mbar_wait(&bar[st], (uint32_t)((t / ST) & 1));
+    const bool waited = mbar_wait(&bar[st], (uint32_t)((t / ST) & 1), spins);
     if (__syncthreads_or(!waited)) {
       tfail = t;
       break;
@@ -445,7 +450,9 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
   if (tfail >= 0) {
     if (tid == 0) {
       atomicExch(err, 1);
-      for (int u = tfail; u < T && u < tfail + ST - 1; ++u) mbar_wait(&bar[u % ST], (uint32_t)((u / ST) & 1));
+      // stages tfail .. tfail + ST - 1 were issued (the copy of t + ST - 1 goes out
+      // before the wait of t): let every one of them land
+      for (int u = tfail; u < T && u < tfail + ST; ++u) mbar_wait(&bar[u % ST], (uint32_t)((u / ST) & 1));
     }
     __syncthreads();
   }

@@ -12,6 +12,7 @@
 #include <atomic>
 #include <mutex>
 
+#include "async.cuh"
 #include "internal.h"
 #include "blas.h"
 #include "coarse.h"
@@ -146,6 +147,7 @@ struct mg_ctx {
   int generic_coarse = 0; // use the generic coarse stencil kernel (SAPMG_GENERIC_COARSE=1)
   int coarse_tf32 = 1;    // tensor-core (TF32) coarse stencil in the mixed form (SAPMG_COARSE_TF32=0 disables)
   int sap_shape = 0;      // Schwarz launch shape for an even number of RHS (SAPMG_SAP_SHAPE; -1: one RHS per CTA)
+  int dirac_pair = 1;     // paired Dirac kernel for an even number of FP32-arithmetic RHS (SAPMG_DIRAC_PAIR=0: off)
   int restrict_tf32 = 1;  // tensor-core (TF32) multi-RHS level-0 transfers in the mixed form (SAPMG_RESTRICT_TF32=0 disables)
   int coarse_fp16 = 1;    // FP16-stored operator for the tensor-core coarse stencil (SAPMG_COARSE_FP16=0: FP32)
   int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
@@ -173,7 +175,7 @@ struct mg_ctx {
   void* io_a = nullptr;                    // canonical <-> blocked staging (FP64, nrhs_max fields)
   void* io_b = nullptr;
   double2* partial = nullptr;
-  int* dev_err = nullptr;                  // raised by kernels whose bounded waits gave up
+  int* dev_err = nullptr;                  // [0] raised by kernels whose bounded waits gave up, [1] their bound
   // Krylov workspace
   int m = 0;
   void *V = nullptr, *Z = nullptr, *w = nullptr;       // outer (plain: FP64; mixed: FP32 inner)
@@ -237,7 +239,7 @@ static int smoother_sweeps(mg_ctx* c, const void* b, void* z, int n_sweeps, int 
       ProfScope ps(c->prof, FAM_SAP, c->s);
       // one colour: half the sites; b and z read, z written, z read across the block faces
       count_bytes(0.5 * c->g.V * (nrhs * 4 * 12 * vec_bytes(c->prec) + fields_bytes(c->prec)));
-      TRY(launch_sap_colour(c->prec, c->g, z, b, c->Us, c->As, col, c->p.n_mr, nrhs, c->s, c->sap_shape));
+      TRY(launch_sap_colour(c->prec, c->g, z, b, c->Us, c->As, col, c->p.n_mr, nrhs, c->s, c->sap_shape, c->dev_err));
     }
   return MG_OK;
 }
@@ -248,6 +250,8 @@ static int fine_dirac(mg_ctx* c, int prec, void* out, const void* in, int nrhs) 
   if (!U || !A) return fail(MG_ERR_STATE, "requested precision not set up in this context");
   ProfScope ps(c->prof, FAM_DIRAC, c->s);
   count_bytes((double)c->g.V * (nrhs * 2 * 12 * vec_bytes(prec) + fields_bytes(prec)));
+  if (c->dirac_pair && prec != P64 && nrhs >= 2 && nrhs % 2 == 0)
+    return launch_dirac_pair(prec, c->g, out, in, U, A, nrhs, c->s);
   return launch_dirac(prec, c->g, out, in, U, A, nrhs, c->s);
 }
 
@@ -1434,9 +1438,13 @@ static int do_setup(mg_ctx* c, const double* U) {
   const size_t eb = complex_bytes(c->vt);
   const int R = p.nrhs_max;
   c->partial = (double2*)c->alloc(sizeof(double2) * kPartialDouble2);
-  c->dev_err = (int*)c->alloc(sizeof(int));
+  c->dev_err = (int*)c->alloc(2 * sizeof(int));
   if (!c->dev_err) return fail(MG_ERR_OOM, "workspace");
-  SAPMG_CUDA_TRY(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->s));
+  {
+    const int init[2] = {0, kMaxSpins};
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->dev_err, init, sizeof(init), cudaMemcpyHostToDevice, c->s));
+    SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  }
   c->zero_f = c->alloc(n * eb);
   c->io_a = c->alloc((size_t)R * n * 16);
   c->io_b = c->alloc((size_t)R * n * 16);
@@ -1561,6 +1569,7 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   c->generic_coarse = std::getenv("SAPMG_GENERIC_COARSE") ? std::atoi(std::getenv("SAPMG_GENERIC_COARSE")) : 0;
   c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
   c->sap_shape = std::getenv("SAPMG_SAP_SHAPE") ? std::atoi(std::getenv("SAPMG_SAP_SHAPE")) : 0;
+  c->dirac_pair = std::getenv("SAPMG_DIRAC_PAIR") ? std::atoi(std::getenv("SAPMG_DIRAC_PAIR")) : 1;
   c->restrict_tf32 = std::getenv("SAPMG_RESTRICT_TF32") ? std::atoi(std::getenv("SAPMG_RESTRICT_TF32")) : 1;
   c->outer_dcgs2 = std::getenv("SAPMG_DCGS2") ? std::atoi(std::getenv("SAPMG_DCGS2")) : 1;
   c->coarse_fp16 = std::getenv("SAPMG_COARSE_FP16") ? std::atoi(std::getenv("SAPMG_COARSE_FP16")) : 1;
@@ -1957,6 +1966,19 @@ int mg_set_profiling(mg_ctx* c, int mask) {
 }
 
 long long mg_launch_count(void) { return g_launches.load(); }
+
+int mg_set_wait_limit(mg_ctx* c, int spins) {
+  if (!c) return fail(MG_ERR_ARG, "bad argument");
+  const int v = spins < 0 ? kMaxSpins : spins;
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(c->dev_err + 1, &v, sizeof(int), cudaMemcpyHostToDevice, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  return MG_OK;
+}
+
+int mg_sync(mg_ctx* c) {
+  if (!c) return fail(MG_ERR_ARG, "bad argument");
+  return check_device_error(c);
+}
 
 int mg_probe_peaks(void* stream, double* fp32_tflops, double* fp32x2_tflops, double* smem_gbs) {
   if (!fp32_tflops || !fp32x2_tflops || !smem_gbs) return fail(MG_ERR_ARG, "bad argument");
