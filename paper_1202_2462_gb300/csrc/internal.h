@@ -31,6 +31,9 @@ uint64_t host_splitmix64(uint64_t x);
 // dirac.cu
 int launch_dirac(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
                  cudaStream_t s);
+// The same for an even number of right-hand sides in FP32 arithmetic, two per thread (dirac2.cu).
+int launch_dirac_pair(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
+                      cudaStream_t s);
 // dag: D^dagger = gamma5 D gamma5; part != nullptr: also the per-CTA partial
 // sums of ||out||^2 at part[block * nrhs + r] (FP64 and FP32 fields only).
 int launch_dirac_ex(int prec, const Geom& g, void* out, const void* in, const void* U, const void* A, int nrhs,
@@ -83,12 +86,14 @@ int launch_adam(size_t n, float* p, const float* gr, float* m, float* v, double 
 // pair_shape >= 0: an even number of right-hand sides in FP32 arithmetic
 // goes to the paired kernel with that launch shape; < 0: the one-RHS-per-CTA kernel.
 int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
-                      int n_mr, int nrhs, cudaStream_t s, int pair_shape = 0);
-// The paired kernel: two right-hand sides per thread (sap2.cu).  shape 0: two
+                      int n_mr, int nrhs, cudaStream_t s, int pair_shape = 0, int* err = nullptr);
+// The paired kernels: two right-hand sides per thread (sap2.cu).  shape 0: two
 // CTAs per SM, rho re-read from shared memory for the update; 1: two CTAs per
-// SM, rho kept in registers; 2: one CTA per SM, rho kept in registers.
+// SM, rho kept in registers; 2: one CTA per SM, rho kept in registers; 3: one
+// CTA per block holding the block's fields in shared memory for every pair
+// (err: the device flag a bounded wait that gives up raises; needed by shape 3).
 int launch_sap_colour_pair(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
-                           int n_mr, int nrhs, cudaStream_t s, int shape);
+                           int n_mr, int nrhs, cudaStream_t s, int shape, int* err);
 // sap_shift.cu: the same pass for D - shift[r] (per right-hand side r; device
 // array of nrhs values), the set-up's S(lambda)
 int launch_sap_colour_shifted(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A,

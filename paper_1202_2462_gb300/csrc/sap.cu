@@ -165,11 +165,11 @@ static int run(const Geom& g, void* z, const void* b, const void* U, const void*
 }
 
 int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
-                      int n_mr, int nrhs, cudaStream_t s, int pair_shape) {
+                      int n_mr, int nrhs, cudaStream_t s, int pair_shape, int* err) {
   // an even number of FP32-arithmetic right-hand sides goes to the paired
   // kernel (sap2.cu) unless pair_shape < 0
   if (pair_shape >= 0 && prec != P64 && nrhs >= 2 && nrhs % 2 == 0 && n_mr >= 1)
-    return launch_sap_colour_pair(prec, g, z, b, U, A, colour, n_mr, nrhs, s, pair_shape);
+    return launch_sap_colour_pair(prec, g, z, b, U, A, colour, n_mr, nrhs, s, pair_shape, err);
   switch (prec) {
     case P64: return run<double, double2, double2>(g, z, b, U, A, colour, n_mr, nrhs, s);
     case P32: return run<float, float2, float2>(g, z, b, U, A, colour, n_mr, nrhs, s);

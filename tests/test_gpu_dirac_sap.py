@@ -170,7 +170,7 @@ def test_sap_multi_rhs_matches_single(prec):
     s.close()
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec,n_mr", [("fp32", 4), ("fp16", 1), ("bf16", 4), ("bf16", 2)])
 def test_sap_pair_kernel_parity(prec, n_mr, shape, monkeypatch):
     """The paired Schwarz kernel (two right-hand sides per thread, packed
@@ -215,5 +215,44 @@ def test_sap_pair_kernel_matches_single_kernel(monkeypatch):
         z = torch.zeros_like(b)
         s.smooth(b, z, 2)
         outs.append(host(z))
+        s.close()
+    assert np.max(np.abs(outs[0] - outs[1])) / np.max(np.abs(outs[1])) < 2e-6
+
+
+@pytest.mark.parametrize("prec,ap", [("fp32", False), ("fp16", False), ("bf16", True)])
+def test_dirac_pair_kernel_parity(prec, ap):
+    """Four right-hand sides (the paired Dirac kernel: two per thread, packed
+    two-wide FP32 arithmetic) against the oracle with the identically rounded
+    fields, element by element; with an antiperiodic time boundary too."""
+    torch = torch_cuda()
+    from paper_1202_2462_gb300 import PRECISIONS
+    dims = (8, 8, 16, 8)
+    m0 = 0.05
+    u = synth.random_gauge_field(dims, 0.5, 37)
+    op = WilsonClover(u, m0, 1.0, antiperiodic_t=ap)
+    opr = WilsonClover(round_storage(u, prec), m0, 1.0, antiperiodic_t=ap)
+    opr.a = round_storage(op.a, prec)
+    psi = synth.random_spinor(dims, 38, nvec=4).astype(np.complex64).astype(np.complex128)
+    s = _solver(torch, u, 1.0, m0, ap, precision=prec, nrhs_max=4)
+    out = host(s.dirac(dev(torch, psi, torch.complex64), PRECISIONS[prec])).astype(np.complex128)
+    s.close()
+    for k in range(4):
+        ref = opr.apply(psi[k])
+        assert np.max(np.abs(out[k] - ref)) / np.max(np.abs(ref)) < 2e-6, k
+
+
+def test_dirac_pair_kernel_matches_single_kernel(monkeypatch):
+    """Two right-hand sides through the paired and the one-RHS-per-CTA Dirac
+    kernels (SAPMG_DIRAC_PAIR=0): equal up to FP32 rounding."""
+    torch = torch_cuda()
+    from paper_1202_2462_gb300 import MG_FP32
+    dims = (8, 8, 8, 16)
+    u = synth.random_gauge_field(dims, 0.5, 39)
+    psi = dev(torch, synth.random_spinor(dims, 40, nvec=2), torch.complex64)
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SAPMG_DIRAC_PAIR", flag)
+        s = _solver(torch, u, 1.0, 0.0, False, precision="fp32", nrhs_max=2)
+        outs.append(host(s.dirac(psi, MG_FP32)))
         s.close()
     assert np.max(np.abs(outs[0] - outs[1])) / np.max(np.abs(outs[1])) < 2e-6
