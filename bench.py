@@ -36,9 +36,14 @@ import synth  # noqa: E402
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (nominal)
-# DRAM bytes per (site, right-hand side) of one BF16 Schwarz colour pass, from an ncu
-# capture of the 16^3x32 lattice with 12 right-hand sides (traffic grows with the units)
-SAP_DRAM_BYTES_PER_UNIT = 310.0e6 / (65536 * 12)
+# DRAM bytes per (site of the colour, right-hand side) of one BF16 Schwarz colour pass,
+# from ncu captures of the 16^3x32 lattice with 12 right-hand sides (traffic grows with
+# the units), per launch shape of the paired kernels: shape 0 (sap_colour_pair_kernel)
+# and shape 3 (sap_block_kernel); none for the other shapes
+SAP_DRAM_BYTES_PER_UNIT = {0: (266.179328e6 + 66.372352e6) / (65536 * 12),
+                           3: (263.003904e6 + 52.152320e6) / (65536 * 12)}
+SAP_KERNEL = {-1: "sap_colour_kernel", 0: "sap_colour_pair_kernel", 1: "sap_colour_pair_kernel",
+              2: "sap_colour_pair_kernel", 3: "sap_block_kernel"}
 
 
 def flops_dirac_site():
@@ -71,7 +76,8 @@ def bytes_dirac_site(prec):
 
 # the kernels behind each timed family (a family call may issue several launches)
 FAMILY_KERNELS = {
-    "dirac": "dirac_kernel", "sap": "sap_colour_kernel", "coarse": "coarse_apply_mma16_kernel",
+    "dirac": "dirac_pair_kernel + dirac_kernel", "sap": "sap_colour_pair_kernel + sap_block_kernel",
+    "coarse": "coarse_apply_mma16_kernel",
     "restrict": "restrict0_mma_kernel", "prolong": "prolong0_mma_kernel",
     "blas": "dots2h_partial + dcgs2_coeff_kernel + axpy2h_kernel (outer Arnoldi, FP16 basis)",
     "coarse_blas": "multidot_h_partial + multiaxpy_h_kernel + normalize_h_kernel + hessenberg_solve_kernel",
@@ -163,10 +169,12 @@ def make_rhs(wl, dims):
 
 
 def solver_kwargs(wl, precision, nrhs):
+    """Solver parameters of the workload; the mixed form tunes its launch shapes at set-up."""
     return dict(n_levels=wl["n_levels"], n_vec=tuple(wl["n_vec"]), setup_iters=wl["setup_iters"],
                 n_mr=wl["n_mr"], nu_post=wl["nu_post"], coarse_iters=wl["coarse_iters"],
                 fgmres_m=wl["fgmres_m"], tol=wl["tol"], maxiter=wl.get("maxiter", 500),
-                precision=precision, nrhs_max=nrhs, seed=wl.get("vec_seed", 1))
+                precision=precision, nrhs_max=nrhs, seed=wl.get("vec_seed", 1),
+                autotune=int(precision != "fp64"))
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
@@ -426,6 +434,7 @@ def run_ours(a, wl):
     s = G.Solver(u, wl["c_sw"], wl["m0"], **solver_kwargs(wl, prec, nrhs))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    tuning = G.mg_get_tuning(s.ctx)
     del u
 
     # warm-up steps, profiled per kernel family to find the dominant one
@@ -509,18 +518,25 @@ def run_ours(a, wl):
     s.close()
 
     hbm, peak_kind = load_peaks()
+    f32, f32x2, smem = G.mg_probe_peaks(stream)
+    probe = {"fp32_tflops_scalar_fma": f32, "fp32_tflops_packed_fma": f32x2, "smem_gbs": smem,
+             "how": "mg_probe_peaks: independent FMA chains and conflict-free 16-byte shared loads on every SM"}
     if dominant == "sap":
         # one launch = one colour pass over V/2 sites for every right-hand side
         units = (v // 2) * nrhs
         avg_s = ms_prof / max(n_prof, 1) / 1e3
         tflops = flops_sap_site(wl["n_mr"]) * units / avg_s / 1e12 if n_prof else None
         alg_bytes = (v // 2) * (nrhs * bytes_sap_spinor(prec) + bytes_sap_fields(prec))
-        roof = {"kernel": "sap_colour_kernel", "bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
+        shape = tuning["sap_shape"] if nrhs % 2 == 0 else -1
+        per_unit = SAP_DRAM_BYTES_PER_UNIT.get(shape) if prec == "bf16" else None
+        roof = {"kernel": SAP_KERNEL[shape], "bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS if tflops else None,
-                "traffic": SAP_DRAM_BYTES_PER_UNIT * units if prec == "bf16" else None,
+                "traffic": per_unit * units if per_unit else None,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one colour pass of the "
-                                  "16^3x32 12-RHS case, per site and RHS, scaled to this launch's units",
+                                  "16^3x32 12-RHS case with this launch shape, per site and RHS, scaled to this "
+                                  "launch's units",
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_probe": probe,
                 "hbm_gbs": alg_bytes / avg_s / 1e9 if n_prof else None,
                 "hbm_frac": alg_bytes / avg_s / 1e9 / hbm if n_prof else None,
                 "launches": n_prof, "avg_launch_ms": avg_s * 1e3, "sites_x_rhs_per_launch": units,
@@ -539,7 +555,7 @@ def run_ours(a, wl):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": wl_config(wl, a.workload, prec),
         "iterations_per_step": iters, "restarts_per_step": [c[3] for c in codes],
         "relres": max(c[1] for c in codes), "status": [c[2] for c in codes], "rhs_per_step": nrhs * world,
-        "setup_s": setup_s, "input_generation_s": gen_s,
+        "setup_s": setup_s, "input_generation_s": gen_s, "tuning": tuning,
         "dirac_apply": {"storage": prec, "gbs": dirac_gbs, "frac_of_measured_hbm": dirac_gbs / hbm,
                         "frac_of_8tbs": dirac_gbs / 8000.0, "us": dirac_s * 1e6},
         "families_warmup": fam, "roofline": roof, "peak_hbm_gbs": hbm, "peak_kind": peak_kind,

@@ -78,27 +78,36 @@ class Multigrid:
         if p["block_solver"] not in ("mr", "exact"):
             raise ValueError(f"unknown block solver {p['block_solver']!r}")
         self.levels = [Level(op, p["sap_block"][0])]
-        nl = p["n_levels"]
         init = init_vectors
-        for l in range(nl - 1):
-            lev = self.levels[l]
-            nvec = p["n_vec"][l]
-            v = [np.array(x) for x in init[:nvec]]
-            for _ in range(p["setup_iters"]):
-                v = [sap_sweep(lev.op, lev.blocks, np.zeros_like(x), x, p["n_mr"], self.exact_blocks(l))
-                     for x in v]
-                v = orthonormalise(v)
-            lev.vectors = v
-            lev.agg = Aggregation(lev.op.dims, p["agg"][l], lev.op.dof_shape).build(np.stack(v))
-            cop = CoarseOperator(lev.op, lev.agg)
+        for l in range(p["n_levels"] - 1):
+            init = self.bootstrap_level(l, init)
+
+    def bootstrap_level(self, l, init, sweeps=None):
+        """Bootstrap part 1 on level l from the initial vectors ``init``:
+        ``sweeps`` (default setup_iters) rounds of one smoother sweep on
+        A_l x = 0 per vector, each round followed by global modified
+        Gram-Schmidt; then P_l from the locally orthonormalised vectors and
+        A_{l+1} = P_l^dagger A_l P_l, which replaces level l+1 (and drops the
+        levels below it).  Returns the next level's initial vectors, the
+        smoothed vectors restricted with P_l^dagger (None on the last pair)."""
+        p = self.p
+        lev = self.levels[l]
+        v = [np.array(x) for x in init[:p["n_vec"][l]]]
+        for _ in range(p["setup_iters"] if sweeps is None else sweeps):
+            v = [sap_sweep(lev.op, lev.blocks, np.zeros_like(x), x, p["n_mr"], self.exact_blocks(l)) for x in v]
+            v = orthonormalise(v)
+        lev.vectors = v
+        lev.agg = Aggregation(lev.op.dims, p["agg"][l], lev.op.dof_shape).build(np.stack(v))
+        cop = CoarseOperator(lev.op, lev.agg)
+        del self.levels[l + 1:]
+        if l + 1 < p["n_levels"] - 1:
             blk = p["sap_block"][l + 1] if l + 1 < len(p["sap_block"]) else p["sap_block"][-1]
-            if l + 1 < nl - 1:
-                self.levels.append(Level(cop, blk))
-                init = [lev.agg.restrict(x) for x in v]
-            else:
-                nxt = Level.__new__(Level)
-                nxt.op, nxt.blocks, nxt.agg, nxt.vectors = cop, None, None, None
-                self.levels.append(nxt)
+            self.levels.append(Level(cop, blk))
+            return [lev.agg.restrict(x) for x in v]
+        nxt = Level.__new__(Level)
+        nxt.op, nxt.blocks, nxt.agg, nxt.vectors, nxt.exact = cop, None, None, None, None
+        self.levels.append(nxt)
+        return None
 
     def exact_blocks(self, l):
         """Dense block matrices of both colours on level l when the block

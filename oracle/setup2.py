@@ -32,6 +32,7 @@ the procedure once, starting on the coarsest grid):
    matrix (DV)^dagger DV for its N smallest eigenvalues (the squared N
    smallest singular values of DV) give the new vectors V y_k.
 5. P and D_c are rebuilt from the N new vectors.
+(The three-level reading is stated with ``part2``.)
 """
 
 import numpy as np
@@ -132,19 +133,35 @@ def reduce_vectors(apply, vectors, n):
 
 
 def part2(mg, iota, start, n_mr=None, exact=False):
-    """Run the second set-up part once on the two-level oracle hierarchy ``mg``
-    (oracle.mg.Multigrid with n_levels = 2, built by part 1) and rebuild its
-    P and D_c in place.  ``start``: the coarse start vector of the Arnoldi
-    process (shape of a coarse field).  Returns the harmonic Ritz values used."""
-    lev, coarse = mg.levels[0], mg.levels[1]
+    """Run the second set-up part once on the oracle hierarchy ``mg``
+    (oracle.mg.Multigrid with two or three levels, built by part 1) and
+    rebuild it in place.  ``start``: the start vector of the Arnoldi process
+    on the coarsest operator (shape of a coarsest-level field).  Returns the
+    harmonic Ritz values used.
+
+    Reading for three levels (the paper ran two): the procedure starts on the
+    coarsest grid, as the paper says -- the harmonic Ritz vectors of the
+    coarsest operator are interpolated through every level to the finest,
+    smoothed and reduced there with the finest level's part-1 vectors; the
+    finest P and the level-1 operator are rebuilt from the result, and the
+    coarser level is then rebuilt as part 1 builds it (the new fine vectors
+    restricted, its own smoother sweeps, P_1 and the coarsest operator)."""
+    levels = mg.levels
+    lev, coarsest = levels[0], levels[-1]
     n = len(lev.vectors)
     n_mr = mg.p["n_mr"] if n_mr is None else n_mr
-    nc = int(np.prod(coarse.op.lat)) * coarse.op.dof_shape[0]
-    theta, phis = harmonic_ritz(coarse.op.apply, start, min(2 * n, nc))
-    new = [shifted_smoothing(lev.op, lev.blocks, lev.agg.prolong(phis[i]), theta[i], iota, n_mr, exact)
+    nc = int(np.prod(coarsest.op.lat)) * coarsest.op.dof_shape[0]
+    theta, phis = harmonic_ritz(coarsest.op.apply, start, min(2 * n, nc))
+
+    def to_fine(x):
+        for l in range(len(levels) - 2, -1, -1):
+            x = levels[l].agg.prolong(x)
+        return x
+
+    new = [shifted_smoothing(lev.op, lev.blocks, to_fine(phis[i]), theta[i], iota, n_mr, exact)
            for i in range(min(n, len(phis)))]
     vhat, _ = reduce_vectors(lev.op.apply, new + list(lev.vectors), n)
-    lev.vectors = vhat
-    lev.agg = Aggregation(lev.op.dims, mg.p["agg"][0], lev.op.dof_shape).build(np.stack(vhat))
-    coarse.op = CoarseOperator(lev.op, lev.agg)
+    nxt = mg.bootstrap_level(0, vhat, sweeps=0)          # P and the level-1 operator from the new vectors
+    if nxt is not None:
+        mg.bootstrap_level(1, nxt)                        # the coarser level rebuilt as part 1 builds it
     return theta[:n]

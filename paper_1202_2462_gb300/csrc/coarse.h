@@ -47,11 +47,20 @@ int launch_coarse_export(int prec, const CGeom& c, const void* M, double* out, c
 // err: device flag raised when a bounded wait gives up.
 int launch_coarse_apply_tma(const CGeom& c, const void* M, const void* x, void* out, int nrhs, int* err,
                             cudaStream_t s);
+// Launch shape of the FP16 tensor-core stencil (chosen by the autotuner; every
+// choice computes each output with the same operations): right-hand sides per
+// launch (1..16), depth of the bulk-copy ring (2 or 3; 3 only for 2N = 40)
+// and a cap on the CTAs per SM (0: as many as shared memory allows).
+struct CoarseTune {
+  int batch = 16;
+  int stages = 2;
+  int ctas = 0;
+};
 // The same stencil with the block products on tensor cores (TF32 inputs, FP32
 // accumulation; n2 % 8 == 0, n2 <= 64); operator stored in FP32 (P32) or FP16 (P16).
 // x_half (FP16 operator only): x holds FP16 basis vectors scaled by kBasisScale.
 int launch_coarse_apply_mma(const CGeom& c, int store, const void* M, const void* x, void* out, int nrhs, int* err,
-                            bool x_half, cudaStream_t s);
+                            bool x_half, cudaStream_t s, const CoarseTune& t = CoarseTune());
 
 // Intermediate level of a three-level hierarchy (coarse1.cu).
 int launch_coarse_sap(int prec, const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,

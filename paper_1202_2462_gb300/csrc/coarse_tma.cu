@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
 
 template <int RB, int N2, int ST, bool XH>
 static void launch_mma16_t(const CGeom& c, const __half2* M, const void* x, float2* out, int r0, int nr, int* err,
-                           cudaStream_t s) {
+                           int ctas, cudaStream_t s) {
   const size_t stage = (size_t)c.n2 * c.n2 * sizeof(__half2) + (size_t)16 * (c.n2 + 4) * (XH ? 4 : 8);
   const size_t smem = ST * stage;
   static bool attr = false;
@@ -470,7 +470,8 @@ static void launch_mma16_t(const CGeom& c, const __half2* M, const void* x, floa
     attr = true;
   }
   const int threads = 32 * (c.n2 / 8);
-  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / (smem + 1024)));
+  int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, (220 * 1024) / (smem + 1024)));
+  if (ctas > 0) per_sm = std::min(per_sm, ctas);
   const int grid = std::min(c.nsites, 152 * per_sm);
   coarse_apply_mma16_kernel<RB, N2, ST, XH><<<grid, threads, smem, s>>>(M, x, out, c, r0, nr, err); count_launches(1);
 }
@@ -481,9 +482,10 @@ static void launch_mma16_t(const CGeom& c, const __half2* M, const void* x, floa
 // instance with the k loop unrolled.
 template <int RB, bool XH>
 static void launch_mma16(const CGeom& c, const __half2* M, const void* x, float2* out, int r0, int nr, int* err,
-                         cudaStream_t s) {
-  if (c.n2 == 40) launch_mma16_t<RB, 40, 2, XH>(c, M, x, out, r0, nr, err, s);
-  else launch_mma16_t<RB, 0, 2, XH>(c, M, x, out, r0, nr, err, s);
+                         const CoarseTune& t, cudaStream_t s) {
+  if (c.n2 == 40 && t.stages == 3) launch_mma16_t<RB, 40, 3, XH>(c, M, x, out, r0, nr, err, t.ctas, s);
+  else if (c.n2 == 40) launch_mma16_t<RB, 40, 2, XH>(c, M, x, out, r0, nr, err, t.ctas, s);
+  else launch_mma16_t<RB, 0, 2, XH>(c, M, x, out, r0, nr, err, t.ctas, s);
 }
 
 template <int RB, class TM>
@@ -519,7 +521,7 @@ static void launch_mma_all(const CGeom& c, const TM* M, const float2* x, float2*
 // launch (nr of them, the template width RB >= nr fixes the fragment count);
 // the operator in FP32 (store P32) or FP16 (store P16).
 int launch_coarse_apply_mma(const CGeom& c, int store, const void* M, const void* x, void* out, int nrhs, int* err,
-                            bool x_half, cudaStream_t s) {
+                            bool x_half, cudaStream_t s, const CoarseTune& t) {
   if (x_half && store != P16) return MG_ERR_ARG;
   if (c.n2 % 8 != 0 || c.n2 > 64) return MG_ERR_ARG;
   if (store == P32) {
@@ -527,14 +529,15 @@ int launch_coarse_apply_mma(const CGeom& c, int store, const void* M, const void
   } else if (store == P16) {
     const __half2* m = (const __half2*)M;
     const size_t xe = x_half ? 4 : 8;                         // bytes per complex vector entry
-    for (int r0 = 0; r0 < nrhs; r0 += 16) {
-      const int rb = std::min(16, nrhs - r0);
+    const int batch = std::max(1, std::min(16, t.batch));
+    for (int r0 = 0; r0 < nrhs; r0 += batch) {
+      const int rb = std::min(batch, nrhs - r0);
       const void* xs = x;
       float2* o = (float2*)out;
       (void)xe;
 #define SAPMG_M16(RB_)                                                                       \
-  if (x_half) launch_mma16<RB_, true>(c, m, xs, o, r0, rb, err, s);                          \
-  else launch_mma16<RB_, false>(c, m, xs, o, r0, rb, err, s);
+  if (x_half) launch_mma16<RB_, true>(c, m, xs, o, r0, rb, err, t, s);                       \
+  else launch_mma16<RB_, false>(c, m, xs, o, r0, rb, err, t, s);
       if (rb > 12) { SAPMG_M16(16) }
       else if (rb > 8) { SAPMG_M16(12) }
       else if (rb > 4) { SAPMG_M16(8) }

@@ -24,7 +24,7 @@ def test_per_site_figures():
     # flops: residual + n_MR block MR steps
     assert bench.flops_sap_site(4) == 9312.0
     assert abs(bench.FP32_PEAK_TFLOPS - 80.54784) < 1e-9
-    assert abs(bench.SAP_DRAM_BYTES_PER_UNIT - 394.2) < 0.1
+    assert abs(bench.SAP_DRAM_BYTES_PER_UNIT[0] - 422.9) < 0.1 and abs(bench.SAP_DRAM_BYTES_PER_UNIT[3] - 400.7) < 0.1
 
 
 def test_reported_kernel_names_exist():

@@ -1,0 +1,63 @@
+"""The autotuner of the mixed form's launch shapes (the Schwarz pass's launch
+shape, right-hand sides per transfer launch, the coarse stencil's ring depth,
+CTAs per SM and right-hand sides per launch).  Every candidate computes each
+output with the same operations in the same order, so a solve is bit for bit
+the same whatever the shapes; the tuner only changes the time.  Checked here
+for the tuner's own choice, for a choice taken from its cache, and for every
+candidate value of each knob forced through the environment."""
+
+import pytest
+
+import synth
+from tests.gpu_util import torch_cuda, dev
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (8, 8, 8, 16)                   # 32 coarse sites, 2N = 40 (the benchmark's coarse block size)
+KW = dict(n_levels=2, n_vec=(20,), setup_iters=2, precision="bf16", nrhs_max=12, seed=4, coarse_iters=16,
+          nu_post=1, fgmres_m=12)
+
+
+def _solve(torch, G, u, b, **kw):
+    s = G.Solver(dev(torch, u), 1.0, -0.1, **dict(KW, **kw))
+    z, info, code = s.solve(b)
+    tune = G.mg_get_tuning(s.ctx)
+    s.close()
+    assert code == 0
+    return z, info.iterations, tune
+
+
+@pytest.fixture(scope="module")
+def base():
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u = synth.random_gauge_field(DIMS, 0.4, 131)
+    b = dev(torch, synth.random_spinor(DIMS, 132, nvec=12))
+    z, its, tune = _solve(torch, G, u, b)
+    assert tune["source"] == "default"
+    return torch, G, u, b, z, its
+
+
+def test_tuned_and_cached_contexts_match_the_default_bit_for_bit(base):
+    torch, G, u, b, z0, its0 = base
+    z1, its1, t1 = _solve(torch, G, u, b, autotune=1)
+    assert t1["source"] in ("tuned", "cached")
+    assert 0 <= t1["sap_shape"] <= 3 and t1["coarse_stages"] in (2, 3) and 1 <= t1["coarse_batch"] <= 16
+    assert torch.equal(z1, z0) and its1 == its0
+    z2, its2, t2 = _solve(torch, G, u, b, autotune=1)      # same key: the cached choice
+    assert t2["source"] == "cached" and {k: v for k, v in t2.items() if k != "source"} == \
+        {k: v for k, v in t1.items() if k != "source"}
+    assert torch.equal(z2, z0)
+
+
+@pytest.mark.parametrize("env", [
+    {"SAPMG_SAP_SHAPE": "1"}, {"SAPMG_SAP_SHAPE": "2"}, {"SAPMG_SAP_SHAPE": "3"},
+    {"SAPMG_XFER_BATCH": "4"}, {"SAPMG_XFER_BATCH": "8"}, {"SAPMG_XFER_BATCH": "6"},
+    {"SAPMG_COARSE_TUNE": "4,3,8"}, {"SAPMG_COARSE_TUNE": "8,2,4"}, {"SAPMG_COARSE_TUNE": "16,3,0"},
+])
+def test_every_candidate_matches_the_default_bit_for_bit(base, env, monkeypatch):
+    torch, G, u, b, z0, its0 = base
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    z, its, tune = _solve(torch, G, u, b)
+    assert torch.equal(z, z0) and its == its0
