@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (nominal)
 SAP_DRAM_BYTES_PER_UNIT = {0: (266.179328e6 + 66.372352e6) / (65536 * 12),
                            3: (263.003904e6 + 52.152320e6) / (65536 * 12)}
 SAP_KERNEL = {-1: "sap_colour_kernel", 0: "sap_colour_pair_kernel", 1: "sap_colour_pair_kernel",
-              2: "sap_colour_pair_kernel", 3: "sap_block_kernel"}
+              2: "sap_colour_pair_kernel", 3: "sap_block_kernel", 4: "sap_block_kernel"}
 
 
 def flops_dirac_site():

@@ -87,13 +87,18 @@ typedef struct {
                                  complex128 fine fields used instead of the
                                  random initial test vectors */
   int verbose;
-  int setup2_iters;         /* set-up part 2 (Sec. 3; two levels only): Schwarz
-                               sweeps iota of S(lambda) per harmonic Ritz vector;
-                               0 = part 1 only */
+  int setup2_iters;         /* set-up part 2 (Sec. 3; two or three levels):
+                               Schwarz sweeps iota of S(lambda) per harmonic
+                               Ritz vector; 0 = part 1 only */
   const double* setup2_start; /* optional device pointer: start vector of the
-                                 part-2 Arnoldi process on D_c, complex128
-                                 [coarse site][2N] (coarse sites in block order);
+                                 part-2 Arnoldi process on the coarsest
+                                 operator, complex128 [coarse site][2N] of the
+                                 coarsest level (sites in block order);
                                  NULL = drawn from seed */
+  int autotune;             /* 1: at the end of mg_setup, time the candidate
+                               launch shapes of the mixed form's multi-RHS
+                               kernels for nrhs_max right-hand sides and keep
+                               the fastest (see mg_get_tuning); 0 = defaults */
 } mg_params;
 
 typedef struct {
@@ -116,10 +121,12 @@ int mg_default_params(mg_params* p);
  * Builds the clover term, packs U in every precision the context needs, runs
  * the bootstrap set-up (Schwarz sweeps on random or given test vectors, kept
  * orthonormal; local orthonormalisation; D_c = P^dagger D P, recursively),
- * with setup2_iters > 0 also its second part (harmonic Ritz vectors of D_c
- * interpolated, smoothed by S(lambda), merged with the part-1 vectors by the
- * (DV)^dagger DV reduction; P and D_c rebuilt), and allocates all solve
- * workspace.  Synchronises.  *out receives the context.
+ * with setup2_iters > 0 also its second part, run once from the coarsest
+ * level (harmonic Ritz vectors of the coarsest operator interpolated to the
+ * fine level, smoothed by S(lambda), merged with the part-1 vectors by the
+ * (DV)^dagger DV reduction; P and D_c rebuilt; with three levels, level 1 is
+ * then rebuilt from the new vectors as part 1 builds it), and allocates all
+ * solve workspace.  Synchronises.  *out receives the context.
  * Errors: MG_ERR_ARG (dims, params), MG_ERR_NONFINITE (U), MG_ERR_OOM, MG_ERR_CUDA. */
 int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx** out);
 
@@ -286,6 +293,11 @@ int mg_precondition(mg_ctx* ctx, const void* v, void* z, int prec);
  * including an antiperiodic t sign if the context has one.  Gradients follow
  * G_z = dL/dRe z + i dL/dIm z.  Asynchronous except mg_net_loss. */
 int mg_net_layer_forward(mg_ctx* ctx, int cin, int cout, const void* W, const void* x, void* y);
+/* The same layer for inference with BF16 storage: W device BF16 complex pairs
+ * [cout][cin][9][4][4] (re, im), the context's BF16 links (a context of
+ * precision MG_BF16; MG_ERR_STATE otherwise), FP32 activations x, y and FP32
+ * accumulation. */
+int mg_net_layer_forward_bf16(mg_ctx* ctx, int cin, int cout, const void* W, const void* x, void* y);
 /* gx = sum_h T_h^dagger sum_a W[a][b][h]^dagger gy_a (skipped if gx is NULL);
  * gW[a][b][h] = sum_x gy_a(x) (T_h x_b)(x)^dagger (skipped if gW is NULL;
  * a fixed-order reduction, deterministic). */
@@ -322,6 +334,18 @@ int mg_reset_profile(mg_ctx* ctx);
 
 /* Number of kernel launches the library has issued in this process. */
 long long mg_launch_count(void);
+
+/* The launch shapes a context uses (no paper counterpart): out[0] = how they
+ * were chosen (0 defaults, 1 timed by the autotuner at set-up, 2 taken from
+ * the autotuner's cache of an earlier context with the same lattice, N,
+ * nrhs_max, precision and levels), out[1] = Schwarz launch shape (0: two CTAs
+ * per SM, rho re-read for the update; 1: rho in registers; 2: one CTA per SM;
+ * 3: one CTA per block with the block's fields in shared memory, every pair
+ * of right-hand sides in turn; 4: shape 3 with branch-free hops), out[2] = right-hand sides per transfer
+ * launch, out[3] = ring depth, out[4] = CTA-per-SM cap (0: none) and out[5] =
+ * right-hand sides per launch of the FP16 tensor-core coarse stencil.  Every
+ * choice computes the same results bit for bit; only the time differs. */
+int mg_get_tuning(mg_ctx* ctx, int* out);
 
 /* Wait for the context's stream and report a device-side wait that gave up
  * since the last check (MG_ERR_TIMEOUT; the flag is then cleared).  The

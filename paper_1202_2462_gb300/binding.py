@@ -55,6 +55,7 @@ class MgParams(ctypes.Structure):
         ("verbose", ctypes.c_int),
         ("setup2_iters", ctypes.c_int),
         ("setup2_start", ctypes.c_void_p),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -102,10 +103,12 @@ _SIGNATURES = {
     "mg_reset_profile": (_I, [_VP]),
     "mg_launch_count": (ctypes.c_longlong, []),
     "mg_sync": (_I, [_VP]),
+    "mg_get_tuning": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "mg_set_wait_limit": (_I, [_VP, _I]),
     "mg_probe_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double)]),
     "mg_net_layer_forward": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
+    "mg_net_layer_forward_bf16": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "mg_net_layer_backward": (_I, [_VP, _I, _I, _VP, _VP, _VP, _VP, _VP]),
     "mg_net_gate_forward": (_I, [_VP, _I, _VP, _VP]),
     "mg_net_gate_backward": (_I, [_VP, _I, _VP, _VP, _VP]),
@@ -294,6 +297,12 @@ def mg_net_layer_forward(ctx, cin, cout, w, x, y):
     return _check(lib().mg_net_layer_forward(ctx, cin, cout, _ptr(w), _ptr(x), _ptr(y)), "mg_net_layer_forward")
 
 
+def mg_net_layer_forward_bf16(ctx, cin, cout, W, x, y):
+    """W: a device tensor of BF16 (re, im) pairs [cout][cin][9][4][4][2]."""
+    return _check(lib().mg_net_layer_forward_bf16(ctx, cin, cout, _ptr(W), _ptr(x), _ptr(y)),
+                  "mg_net_layer_forward_bf16")
+
+
 def mg_net_layer_backward(ctx, cin, cout, w, x, gy, gx, gw):
     return _check(lib().mg_net_layer_backward(ctx, cin, cout, _ptr(w), _ptr(x), _ptr(gy), _ptr(gx), _ptr(gw)),
                   "mg_net_layer_backward")
@@ -324,6 +333,14 @@ def mg_reset_profile(ctx):
 
 def mg_launch_count():
     return lib().mg_launch_count()
+
+
+def mg_get_tuning(ctx):
+    """The context's launch shapes (see include/sapmg.h): a dict."""
+    a = (ctypes.c_int * 6)()
+    _check(lib().mg_get_tuning(ctx, a), "mg_get_tuning")
+    return {"source": ("default", "tuned", "cached")[a[0]], "sap_shape": a[1], "xfer_batch": a[2],
+            "coarse_stages": a[3], "coarse_ctas_per_sm": a[4], "coarse_batch": a[5]}
 
 
 def mg_sync(ctx):

@@ -76,6 +76,9 @@ int launch_cgn_rr(const double* part_r, int G, int R, CgnState* st, cudaStream_t
 // learned.cu: the set-up network's layers, gate and optimiser
 int launch_gconv_forward(const Geom& g, const void* U, const void* W, const void* x, void* y, int cin, int cout,
                          cudaStream_t s);
+// The same with BF16 links and BF16 weights (inference), FP32 activations and accumulation.
+int launch_gconv_forward_bf16(const Geom& g, const void* U, const void* W, const void* x, void* y, int cin, int cout,
+                              cudaStream_t s);
 int launch_gconv_backward(const Geom& g, const void* U, const void* W, const void* x, const void* gy, void* gx,
                           void* gW, int cin, int cout, cudaStream_t s);
 int launch_gate(const Geom& g, const void* x, const void* gy, void* out, int channels, cudaStream_t s);
@@ -90,8 +93,9 @@ int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const voi
 // The paired kernels: two right-hand sides per thread (sap2.cu).  shape 0: two
 // CTAs per SM, rho re-read from shared memory for the update; 1: two CTAs per
 // SM, rho kept in registers; 2: one CTA per SM, rho kept in registers; 3: one
-// CTA per block holding the block's fields in shared memory for every pair
-// (err: the device flag a bounded wait that gives up raises; needed by shape 3).
+// CTA per block holding the block's fields in shared memory for every pair;
+// 4: shape 3 with the x, y, z hops of the MR steps computed without branches
+// (err: the device flag a bounded wait that gives up raises; needed by shapes 3, 4).
 int launch_sap_colour_pair(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
                            int n_mr, int nrhs, cudaStream_t s, int shape, int* err);
 // sap_shift.cu: the same pass for D - shift[r] (per right-hand side r; device

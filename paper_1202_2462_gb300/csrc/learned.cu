@@ -21,8 +21,9 @@ namespace sapmg {
 
 namespace {
 
-// T_h psi_b at (blk, loc) into v (4 spins x 3 colours)
-__device__ __forceinline__ void transport_at(const Geom& g, const float2* __restrict__ U,
+// T_h psi_b at (blk, loc) into v (4 spins x 3 colours); links in storage type TG
+template <class TG = float2>
+__device__ __forceinline__ void transport_at(const Geom& g, const TG* __restrict__ U,
                                              const float2* __restrict__ f, int blk, int loc, int h,
                                              Cplx<float> (&v)[12]) {
   if (h == 0) {
@@ -66,14 +67,20 @@ __device__ __forceinline__ int adjoint_hop(int h) { return h == 0 ? 0 : (((h - 1
 }  // namespace
 
 // y_a = sum_b sum_h W[a][b][h] T_h x_b; grid (nblocks, cout), W[a] staged in shared memory.
-__global__ void __launch_bounds__(256) gconv_forward_kernel(Geom g, const float2* __restrict__ U,
-                                                            const float2* __restrict__ W,
+// TG, TW: storage of the links and of the weights (FP32, or BF16 for inference);
+// activations and accumulation in FP32.
+template <class TG, class TW>
+__global__ void __launch_bounds__(256) gconv_forward_kernel(Geom g, const TG* __restrict__ U,
+                                                            const TW* __restrict__ W,
                                                             const float2* __restrict__ x, float2* __restrict__ y,
                                                             int cin) {
   extern __shared__ float2 ws[];                                // [cin][9][16]
   const int blk = blockIdx.x, a = blockIdx.y, loc = threadIdx.x;
   const size_t fs = (size_t)g.V * 12;
-  for (int e = loc; e < cin * 9 * 16; e += 256) ws[e] = W[(size_t)a * cin * 9 * 16 + e];
+  for (int e = loc; e < cin * 9 * 16; e += 256) {
+    const Cplx<float> w = Io<float, TW>::ldc(W + (size_t)a * cin * 9 * 16 + e);
+    ws[e] = make_float2(w.re, w.im);
+  }
   __syncthreads();
   Cplx<float> acc[12];
 #pragma unroll
@@ -81,7 +88,7 @@ __global__ void __launch_bounds__(256) gconv_forward_kernel(Geom g, const float2
   for (int b = 0; b < cin; ++b) {
     for (int h = 0; h < 9; ++h) {
       Cplx<float> v[12];
-      transport_at(g, U, x + (size_t)b * fs, blk, loc, h, v);
+      transport_at<TG>(g, U, x + (size_t)b * fs, blk, loc, h, v);
       const float2* w = ws + (b * 9 + h) * 16;
 #pragma unroll
       for (int s = 0; s < 4; ++s)
@@ -269,20 +276,31 @@ __global__ void adam_kernel(size_t n, float* __restrict__ p, const float* __rest
   }
 }
 
-int launch_gconv_forward(const Geom& g, const void* U, const void* W, const void* x, void* y, int cin, int cout,
+template <class TG, class TW>
+static int gconv_forward(const Geom& g, const void* U, const void* W, const void* x, void* y, int cin, int cout,
                          cudaStream_t s) {
   const size_t smem = sizeof(float2) * cin * 9 * 16;
   if (smem > 200 * 1024) return MG_ERR_ARG;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(gconv_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(gconv_forward_kernel<TG, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  gconv_forward_kernel<<<dim3(g.nblocks, cout), 256, smem, s>>>(g, (const float2*)U, (const float2*)W,
-                                                               (const float2*)x, (float2*)y, cin);
+  gconv_forward_kernel<TG, TW><<<dim3(g.nblocks, cout), 256, smem, s>>>(g, (const TG*)U, (const TW*)W,
+                                                                         (const float2*)x, (float2*)y, cin);
   count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
+}
+
+int launch_gconv_forward(const Geom& g, const void* U, const void* W, const void* x, void* y, int cin, int cout,
+                         cudaStream_t s) {
+  return gconv_forward<float2, float2>(g, U, W, x, y, cin, cout, s);
+}
+
+int launch_gconv_forward_bf16(const Geom& g, const void* U, const void* W, const void* x, void* y, int cin, int cout,
+                              cudaStream_t s) {
+  return gconv_forward<__nv_bfloat162, __nv_bfloat162>(g, U, W, x, y, cin, cout, s);
 }
 
 int launch_gconv_backward(const Geom& g, const void* U, const void* W, const void* x, const void* gy, void* gx,

@@ -117,10 +117,10 @@ __device__ __forceinline__ void project2(LD ld, P2 (&h)[6]) {
 }
 
 // acc_u[a] += k g0, acc_u[3+a] += k g1, acc_l += k S X_MU^dagger (g0, g1) for colour a,
-// with k = -1/2 (the hopping term's coefficient): kp = (k, k), km = (-k, -k).
+// with k = -1/2 (the hopping term's coefficient; 0 drops the hop): kp = (k, k), km = (-k, -k).
 template <int MU, int S>
-__device__ __forceinline__ void reconstruct2(const P2& g0, const P2& g1, int a, P2 (&acc)[12]) {
-  const float2 kp = f2(-0.5f), km = f2(0.5f);
+__device__ __forceinline__ void reconstruct2(const P2& g0, const P2& g1, int a, P2 (&acc)[12], float k = -0.5f) {
+  const float2 kp = f2(k), km = f2(-k);
   acc[a].re = fma2(g0.re, kp, acc[a].re); acc[a].im = fma2(g0.im, kp, acc[a].im);
   acc[3 + a].re = fma2(g1.re, kp, acc[3 + a].re); acc[3 + a].im = fma2(g1.im, kp, acc[3 + a].im);
   // the lower components receive S * X^dagger g scaled by k; k S = -S/2
@@ -146,7 +146,7 @@ __device__ __forceinline__ void reconstruct2(const P2& g0, const P2& g1, int a, 
 // U_MU(x - MU)^dagger (S = +1, backward); fl(k) returns entry k = 3 a + b of
 // that link as a broadcast pair, ld(c) component c of the neighbour.
 template <int MU, int S, class LD, class FL>
-__device__ __forceinline__ void hop2(LD ld, FL fl, P2 (&acc)[12]) {
+__device__ __forceinline__ void hop2(LD ld, FL fl, P2 (&acc)[12], float k = -0.5f) {
   P2 h[6];
   project2<MU, S>(ld, h);
 #pragma unroll
@@ -164,7 +164,7 @@ __device__ __forceinline__ void hop2(LD ld, FL fl, P2 (&acc)[12]) {
         else { cmac_conj(g0, u, h[bb]); cmac_conj(g1, u, h[3 + bb]); }
       }
     }
-    reconstruct2<MU, S>(g0, g1, a, acc);
+    reconstruct2<MU, S>(g0, g1, a, acc, k);
   }
 }
 

@@ -211,6 +211,22 @@ __device__ __forceinline__ void global_hops2s(const Geom& g, const float2* __res
   hop2<MU, 1>([&](int k) { return ldg2(z, stride, ((size_t)nb * 12 + k) * 256 + nl); }, LinkP<MU, TG>(lp), acc);
 }
 
+// Both hops of direction MU without a branch: a hop that leaves the block is
+// computed from the site itself and weighted by 0 (acc + 0 * g = acc), so the
+// two hops' loads and products are independent work the scheduler can
+// interleave.  Used for x, y, z, whose block faces cut through every warp
+// (a branch there runs both hops anyway); t keeps the branch (warp-uniform).
+template <int MU, class TG>
+__device__ __forceinline__ void block_hops2s_both(const TG* Us, const float4* __restrict__ rs, int loc,
+                                                  P2 (&acc)[12]) {
+  const int ls = 1 << (2 * MU);
+  const int c = (loc >> (2 * MU)) & 3;
+  const int lf = c < 3 ? loc + ls : loc, lb = c > 0 ? loc - ls : loc;
+  const float kf = c < 3 ? -0.5f : 0.f, kb = c > 0 ? -0.5f : 0.f;
+  hop2<MU, -1>([&](int k) { return lds2(rs, k * 256 + lf); }, LinkS<MU, TG>(Us, loc), acc, kf);
+  hop2<MU, 1>([&](int k) { return lds2(rs, k * 256 + lb); }, LinkS<MU, TG>(Us, lb), acc, kb);
+}
+
 template <int MU, class TG>
 __device__ __forceinline__ void block_hops2s(const TG* Us, const float4* __restrict__ rs, int loc, P2 (&acc)[12]) {
   const int ls = 1 << (2 * MU);
@@ -258,7 +274,7 @@ __device__ __forceinline__ void residual_pair(const Geom& g, const float2* __res
   }
 }
 
-template <class TG>
+template <class TG, bool BF>
 __global__ void __launch_bounds__(256, 1)
     sap_block_kernel(float2* __restrict__ z, const float2* __restrict__ b, const TG* __restrict__ U,
                      const TG* __restrict__ A, Geom g, int colour, int n_mr, int npairs, int* __restrict__ err) {
@@ -302,13 +318,20 @@ __global__ void __launch_bounds__(256, 1)
       __syncthreads();                                 // rho of every site written
       P2 p[12];
       clover2s<TG>(As, loc, [&](int k) { return lds2(rs, k * 256 + loc); }, p);
-      block_hops2s<0>(Us, rs, loc, p);
-      asm volatile("" ::: "memory");
-      block_hops2s<1>(Us, rs, loc, p);
-      asm volatile("" ::: "memory");
-      block_hops2s<2>(Us, rs, loc, p);
-      asm volatile("" ::: "memory");
-      block_hops2s<3>(Us, rs, loc, p);
+      if (BF) {                                        // BF: branch-free x, y, z hops
+        block_hops2s_both<0>(Us, rs, loc, p);
+        block_hops2s_both<1>(Us, rs, loc, p);
+        block_hops2s_both<2>(Us, rs, loc, p);
+        block_hops2s<3>(Us, rs, loc, p);
+      } else {
+        block_hops2s<0>(Us, rs, loc, p);
+        asm volatile("" ::: "memory");
+        block_hops2s<1>(Us, rs, loc, p);
+        asm volatile("" ::: "memory");
+        block_hops2s<2>(Us, rs, loc, p);
+        asm volatile("" ::: "memory");
+        block_hops2s<3>(Us, rs, loc, p);
+      }
       P2 ro[12];
       float2 pr_re = f2(0.f), pr_im = f2(0.f), pp = f2(0.f);
 #pragma unroll
@@ -351,17 +374,17 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
-template <class TG>
+template <class TG, bool BF>
 static int run_block(const Geom& g, void* z, const void* b, const void* U, const void* A, int colour, int n_mr,
                      int nrhs, int* err, cudaStream_t s) {
   const size_t smem = 2 * 36 * 256 * sizeof(TG) + sizeof(float4) * (12 * 256 + 16) + 16;
   static bool attr = false;
   if (!attr) {
-    SAPMG_CUDA_TRY(cudaFuncSetAttribute(sap_block_kernel<TG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SAPMG_CUDA_TRY(cudaFuncSetAttribute(sap_block_kernel<TG, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     attr = true;
   }
-  sap_block_kernel<TG><<<(unsigned)(g.nblocks / 2), 256, smem, s>>>(
+  sap_block_kernel<TG, BF><<<(unsigned)(g.nblocks / 2), 256, smem, s>>>(
       (float2*)z, (const float2*)b, (const TG*)U, (const TG*)A, g, colour, n_mr, nrhs / 2, err);
   count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
@@ -390,10 +413,11 @@ static int run_pair(const Geom& g, void* z, const void* b, const void* U, const 
 
 int launch_sap_colour_pair(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
                            int n_mr, int nrhs, cudaStream_t s, int shape, int* err) {
-  if (shape == 3 && !err) return MG_ERR_ARG;
+  if (shape >= 3 && !err) return MG_ERR_ARG;
   if (nrhs < 2 || nrhs % 2 != 0 || n_mr < 1) return MG_ERR_ARG;
 #define SAPMG_PAIR_CASE(T)                                                                   \
-  return shape == 3 ? run_block<T>(g, z, b, U, A, colour, n_mr, nrhs, err, s)                \
+  return shape == 4 ? run_block<T, true>(g, z, b, U, A, colour, n_mr, nrhs, err, s)          \
+       : shape == 3 ? run_block<T, false>(g, z, b, U, A, colour, n_mr, nrhs, err, s)         \
        : shape == 2 ? run_pair<T, true, 1>(g, z, b, U, A, colour, n_mr, nrhs, s)             \
        : shape == 1 ? run_pair<T, true, 2>(g, z, b, U, A, colour, n_mr, nrhs, s)             \
                     : run_pair<T, false, 2>(g, z, b, U, A, colour, n_mr, nrhs, s)

@@ -148,6 +148,9 @@ struct mg_ctx {
   int coarse_tf32 = 1;    // tensor-core (TF32) coarse stencil in the mixed form (SAPMG_COARSE_TF32=0 disables)
   int sap_shape = 0;      // Schwarz launch shape for an even number of RHS (SAPMG_SAP_SHAPE; -1: one RHS per CTA)
   int dirac_pair = 1;     // paired Dirac kernel for an even number of FP32-arithmetic RHS (SAPMG_DIRAC_PAIR=0: off)
+  int xfer_batch = 16;    // right-hand sides per level-0 transfer launch (autotuned)
+  CoarseTune ctune;       // launch shape of the FP16 tensor-core coarse stencil (autotuned)
+  int tune_source = 0;    // 0: default launch shapes, 1: chosen by the autotuner, 2: taken from its cache
   int restrict_tf32 = 1;  // tensor-core (TF32) multi-RHS level-0 transfers in the mixed form (SAPMG_RESTRICT_TF32=0 disables)
   int coarse_fp16 = 1;    // FP16-stored operator for the tensor-core coarse stencil (SAPMG_COARSE_FP16=0: FP32)
   int dc_prec = P64; // storage of the coarse operators (FP32 in the mixed form)
@@ -159,6 +162,7 @@ struct mg_ctx {
   int N0 = 0;
   void* V64 = nullptr;                     // locally orthonormal test vectors, FP64 vector-major
   void* Vs64 = nullptr;                    // set-up only: the smoothed vectors before local orthonormalisation
+  void* part2_buf = nullptr;               // set-up only (three levels): part-1 vectors kept for set-up part 2
   void* Pv = nullptr;                      // P in cycle storage, block-major
   CoarseLevel c1;
   // three levels: level-1 Schwarz boxes, level-2 aggregates, level-1 vectors, level 2
@@ -273,7 +277,8 @@ static int coarse_apply(mg_ctx* c, CoarseLevel& L, const void* x, void* out, int
   count_bytes((double)L.cg.nsites * (9.0 * L.cg.n2 * L.cg.n2 * complex_bytes(store) +
                                      R * L.cg.n2 * (complex_bytes(c->vt) + (xh ? 4.0 : complex_bytes(c->vt)))));
   if (mma)
-    return launch_coarse_apply_mma(L.cg, store, store == P16 ? L.Mh : L.M, x, out, R, c->dev_err, xh, c->s);
+    return launch_coarse_apply_mma(L.cg, store, store == P16 ? L.Mh : L.M, x, out, R, c->dev_err, xh, c->s,
+                                   store == P16 ? c->ctune : CoarseTune());
   if (L.store == P32 && c->vt == P32 && L.cg.n2 % 2 == 0 && L.cg.n2 <= 64 && !c->generic_coarse)
     return launch_coarse_apply_tma(L.cg, L.M, x, out, R, c->dev_err, c->s);
   return launch_coarse_apply(L.store, L.cg, L.M, x, out, R, c->s);
@@ -294,6 +299,24 @@ static Scal32 scal_all(double re, int R) {
   Scal32 s;
   for (int r = 0; r < 32; ++r) s.v[r] = make_double2(r < R ? re : 0.0, 0.0);
   return s;
+}
+
+// The level-0 transfers of R right-hand sides in launches of at most
+// xfer_batch of them (mixed form; each launch reads P once for its batch).
+// A batch of one would take the one-vector kernel, which rounds differently,
+// so a last batch of one joins the previous one.
+static int transfer0(mg_ctx* c, bool restrict_, const void* in, void* out, int R) {
+  int bsz = (c->vt == P32 && c->xfer_batch > 0) ? std::min(c->xfer_batch, R) : R;
+  const size_t fb = c->fine_n() * complex_bytes(c->vt), cb = c->c1.n() * complex_bytes(c->vt);
+  for (int r0 = 0; r0 < R;) {
+    int nr = std::min(bsz, R - r0);
+    if (R - r0 - nr == 1) nr += 1;
+    const char* src = (const char*)in + (size_t)r0 * (restrict_ ? fb : cb);
+    char* dst = (char*)out + (size_t)r0 * (restrict_ ? cb : fb);
+    TRY(launch_transfer0(restrict_, c->pv_prec, c->g, src, dst, c->Pv, c->N0, nr, c->restrict_tf32, c->s));
+    r0 += nr;
+  }
+  return MG_OK;
 }
 
 // Fixed-step GMRES from zero on a coarse level for R right-hand sides at once
@@ -443,13 +466,13 @@ static int cycle(mg_ctx* c, const void* v, void* z, int R) {
   {
     ProfScope ps(c->prof, FAM_RESTRICT, c->s);
     count_bytes(tbytes);
-    TRY(launch_transfer0(true, c->pv_prec, c->g, v, c->c1.b, c->Pv, c->N0, R, c->restrict_tf32, c->s));
+    TRY(transfer0(c, true, v, c->c1.b, R));
   }
   TRY(coarse_solve(c, 1, R));
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
     count_bytes(tbytes);
-    TRY(launch_transfer0(false, c->pv_prec, c->g, c->c1.x, z, c->Pv, c->N0, R, c->restrict_tf32, c->s));
+    TRY(transfer0(c, false, c->c1.x, z, R));
   }
   return smoother_sweeps(c, v, z, c->p.nu_post, R);
 }
@@ -1053,18 +1076,22 @@ static int build_level0_operators(mg_ctx* c) {
 //  4. the N eigenvectors y_k of (DV)^dagger DV (= V^dagger D^dagger D V) with
 //     the smallest eigenvalues give the new test vectors V y_k;
 //  5. P and D_c rebuilt from them.
+static int setup_level1(mg_ctx* c);
+
 static int setup_part2(mg_ctx* c, void* V2) {
   const mg_params& p = c->p;
   const size_t n = c->fine_n();
   const int N = c->N0;
-  CoarseLevel& L = c->c1;
+  const bool three = p.n_levels == 3;        // the Ritz pairs come from the coarsest operator
+  CoarseLevel& L = three ? c->c2 : c->c1;
   const size_t nc = L.n();
   const int m = (int)std::min<size_t>((size_t)2 * N, nc);
   const BVec bc = bvec(nc, 1, nc), bf = bvec(n, 1, n);
   cudaStream_t s = c->s;
   void* Q = c->alloc((size_t)(m + 2) * nc * 16);            // basis q_0..q_m and phi
   double2* d = (double2*)c->alloc(sizeof(double2) * 320);   // device scalars
-  if (!Q || !d) return fail(MG_ERR_OOM, "set-up part 2 workspace");
+  void* phi1 = three ? c->alloc(c->c1.n() * 16) : nullptr;  // three levels: phi interpolated to level 1
+  if (!Q || !d || (three && !phi1)) return fail(MG_ERR_OOM, "set-up part 2 workspace");
   double2 *h1 = d, *h2 = d + 72, *coef = d + 144, *nrm = d + 216, *shift = d + 224;
   auto Qj = [&](int j) { return (void*)((char*)Q + (size_t)j * nc * 16); };
   auto Vk = [&](int k) { return (void*)((char*)V2 + (size_t)k * n * 16); };
@@ -1146,7 +1173,12 @@ static int setup_part2(mg_ctx* c, void* V2) {
     SAPMG_CUDA_TRY(cudaMemsetAsync(phi, 0, nc * 16, s));
     TRY(blas_multiaxpy(P64, bc, phi, vl.data(), steps, coef, 1, 1.0, s));
     void* xi = Vk(i);
-    TRY(launch_prolong_v64(c->g, c->V64, N, phi, xi, s));
+    if (three) {
+      TRY(launch_transfer1(false, P64, c->c1.cg, c->agg1, phi, phi1, c->W64, c->N1, 1, s));
+      TRY(launch_prolong_v64(c->g, c->V64, N, phi1, xi, s));
+    } else {
+      TRY(launch_prolong_v64(c->g, c->V64, N, phi, xi, s));
+    }
     TRY(to_dev(shift, std::vector<double2>{make_double2(th[2 * i], th[2 * i + 1])}));
     if (c->vt == P64) {
       for (int it = 0; it < p.setup2_iters; ++it)
@@ -1200,10 +1232,17 @@ static int setup_part2(mg_ctx* c, void* V2) {
     SAPMG_CUDA_TRY(cudaMemsetAsync(vk, 0, n * 16, s));
     TRY(blas_multiaxpy(P64, bf, vk, vall.data(), nv, coef, 1, 1.0, s));
   }
+  if (three) {                               // the new vectors also start level 1 again (restricted)
+    c->Vs64 = c->alloc((size_t)N * n * 16);
+    if (!c->Vs64) return fail(MG_ERR_OOM, "set-up vectors");
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->Vs64, c->V64, (size_t)N * n * 16, cudaMemcpyDeviceToDevice, s));
+  }
   TRY(build_level0_operators(c));
+  if (three) TRY(setup_level1(c));           // level 1 rebuilt as part 1 builds it
   SAPMG_CUDA_TRY(cudaStreamSynchronize(s));
   c->release(Q);
   c->release(d);
+  if (phi1) c->release(phi1);
   return MG_OK;
 }
 
@@ -1246,10 +1285,12 @@ static int setup_level0(mg_ctx* c) {
                                    cudaMemcpyDeviceToDevice, c->s));
   }
   TRY(build_level0_operators(c));
-  if (p.setup2_iters > 0) {
+  if (p.setup2_iters > 0 && p.n_levels == 2) {
     TRY(setup_part2(c, V2));
     SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
     c->release(V2);
+  } else if (p.setup2_iters > 0) {
+    c->part2_buf = V2;                     // three levels: part 2 runs once level 2 exists
   }
   return MG_OK;
 }
@@ -1269,7 +1310,7 @@ static int setup_level1(mg_ctx* c) {
   c->agg1 = make_box(L1.cg, p.agg2);
   // FP64 P0 (block-major) to restrict the smoothed fine vectors
   void* p0buf = c->alloc((size_t)N0 * nf * 16);
-  c->W64 = c->alloc((size_t)N1 * n1 * 16);
+  if (!c->W64) c->W64 = c->alloc((size_t)N1 * n1 * 16);         // reused when set-up part 2 rebuilds level 1
   if (!p0buf || !c->W64) return fail(MG_ERR_OOM, "level-1 vectors");
   TRY(launch_store_p0(P64, c->g, c->V64, p0buf, N0, c->s));
   for (int k = 0; k < N1; ++k)
@@ -1305,7 +1346,7 @@ static int setup_level1(mg_ctx* c) {
   if (c->vt == P64) {
     c->W = c->W64;
   } else {
-    c->W = c->alloc((size_t)N1 * n1 * 8);
+    if (!c->W) c->W = c->alloc((size_t)N1 * n1 * 8);
     if (!c->W) return fail(MG_ERR_OOM, "level-1 vectors");
     TRY(launch_convert(P64, c->W64, P32, c->W, (size_t)N1 * n1, c->s));
   }
@@ -1315,18 +1356,18 @@ static int setup_level1(mg_ctx* c) {
   L2.cg.nsites = c->agg1.nboxes;
   L2.cg.n2 = 2 * N1;
   const size_t msz = (size_t)L2.cg.nsites * 9 * L2.cg.n2 * L2.cg.n2;
-  L2.M64 = c->alloc(msz * 16);
+  if (!L2.M64) L2.M64 = c->alloc(msz * 16);
   if (!L2.M64) return fail(MG_ERR_OOM, "level-2 operator");
   TRY(launch_assemble1(L1.cg, L2.cg, c->agg1, c->W64, L1.M64, L2.M64, N1, c->s));
   L2.store = c->dc_prec;
   if (c->dc_prec == P64) {
     L2.M = L2.M64;
   } else {
-    L2.M = c->alloc(msz * complex_bytes(c->dc_prec));
+    if (!L2.M) L2.M = c->alloc(msz * complex_bytes(c->dc_prec));
     if (!L2.M) return fail(MG_ERR_OOM, "level-2 operator");
     TRY(launch_convert(P64, L2.M64, c->dc_prec, L2.M, msz, c->s));
     if (c->dc_prec == P32 && c->coarse_fp16 && L2.cg.n2 % 8 == 0 && L2.cg.n2 <= 64) {
-      L2.Mh = c->alloc(msz * complex_bytes(P16));
+      if (!L2.Mh) L2.Mh = c->alloc(msz * complex_bytes(P16));
       if (!L2.Mh) return fail(MG_ERR_OOM, "level-2 operator");
       TRY(launch_convert(P64, L2.M64, P16, L2.Mh, msz, c->s));
     }
@@ -1400,9 +1441,11 @@ static int validate(const mg_params* p) {
   if (p->precision < MG_FP64 || p->precision > MG_BF16) return fail(MG_ERR_ARG, "unknown precision");
   if (p->nrhs_max < 1 || p->nrhs_max > 32) return fail(MG_ERR_ARG, "nrhs_max must be in 1..32");
   if (p->setup2_iters < 0) return fail(MG_ERR_ARG, "negative iteration count");
-  if (p->setup2_iters > 0 && p->n_levels != 2) return fail(MG_ERR_ARG, "set-up part 2 is built for two levels");
+  if (p->setup2_iters > 0 && p->n_levels < 2) return fail(MG_ERR_ARG, "set-up part 2 needs a coarse level");
   return MG_OK;
 }
+
+static int autotune(mg_ctx* c);
 
 static int do_setup(mg_ctx* c, const double* U) {
   const mg_params& p = c->p;
@@ -1483,10 +1526,135 @@ static int do_setup(mg_ctx* c, const double* U) {
   if (p.n_levels == 3) {
     c->N1 = p.n_vec[1];
     TRY(setup_level1(c));
+    if (c->part2_buf) {
+      TRY(setup_part2(c, c->part2_buf));
+      c->release(c->part2_buf);
+      c->part2_buf = nullptr;
+    }
     TRY(alloc_coarse_ws(c, c->c2, p.coarse_iters, R));
     TRY(alloc_fgmres1_ws(c, p.inner_iters, R));
   }
+  if (p.autotune) TRY(autotune(c));
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  return MG_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+// The launch shapes of the mixed form's multi-RHS kernels, chosen by timing
+// every candidate on the context's own fields, P and D_c with nrhs_max
+// right-hand sides (CUDA events on the context's stream, best of three after a
+// warm-up launch), one knob at a time: the Schwarz pass's launch shape, the
+// right-hand sides per transfer launch, and the coarse stencil's ring depth,
+// CTAs per SM and right-hand sides per launch.  Every candidate of a knob
+// computes each output with the same operations in the same order, so a tuned
+// context gives the default's results bit for bit.  The choice is cached per
+// (lattice, N, nrhs_max, precision, levels) for the life of the process; a
+// later context with the same key takes it without timing.
+struct TuneChoice {
+  int sap_shape, xfer_batch;
+  CoarseTune ct;
+};
+static std::mutex g_tune_mutex;
+static std::vector<std::pair<std::vector<int>, TuneChoice>> g_tune_cache;
+
+static std::vector<int> tune_key(const mg_ctx* c) {
+  const mg_params& p = c->p;
+  return {p.dims[0], p.dims[1], p.dims[2], p.dims[3], p.n_vec[0], p.nrhs_max, p.precision, p.n_levels};
+}
+
+static int autotune(mg_ctx* c) {
+  if (c->vt != P32 || c->p.n_levels < 2 || !c->Pv) return MG_OK;       // the knobs exist in the mixed form only
+  const std::vector<int> key = tune_key(c);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (const auto& e : g_tune_cache)
+      if (e.first == key) {
+        c->sap_shape = e.second.sap_shape;
+        c->xfer_batch = e.second.xfer_batch;
+        c->ctune = e.second.ct;
+        c->tune_source = 2;
+        return MG_OK;
+      }
+  }
+  const int R = c->p.nrhs_max;
+  const size_t n = c->fine_n();
+  // scratch vectors: the outer solver's flexible basis and w (free until the first solve)
+  void* b = c->Z;
+  void* z = c->w;
+  SAPMG_CUDA_TRY(cudaMemsetAsync(b, 0, (size_t)R * n * 8, c->s));
+  SAPMG_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)R * n * 8, c->s));
+  cudaEvent_t e0, e1;
+  SAPMG_CUDA_TRY(cudaEventCreate(&e0));
+  SAPMG_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = MG_OK;
+  auto timed = [&](auto&& fn) -> float {
+    float best = 1e30f;
+    if (rc != MG_OK) return best;
+    if ((rc = fn()) != MG_OK) return best;
+    for (int rep = 0; rep < 3 && rc == MG_OK; ++rep) {
+      cudaEventRecord(e0, c->s);
+      rc = fn();
+      cudaEventRecord(e1, c->s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, ms);
+    }
+    return best;
+  };
+  // 1. Schwarz launch shape (the paired kernels: an even number of right-hand sides)
+  if (R >= 2 && R % 2 == 0 && c->sap_shape >= 0) {
+    int best_shape = c->sap_shape;
+    float best = 1e30f;
+    for (int shape = 0; shape <= 4; ++shape) {
+      c->sap_shape = shape;
+      const float ms = timed([&] { return smoother_sweeps(c, b, z, 1, R); });
+      if (ms < best) { best = ms; best_shape = shape; }
+    }
+    c->sap_shape = best_shape;
+  }
+  // 2. right-hand sides per transfer launch (restriction and interpolation)
+  if (R >= 2) {
+    int best_b = c->xfer_batch;
+    float best = 1e30f;
+    for (int bsz : {16, 12, 8, 6, 4}) {
+      if (bsz > R && bsz != 16) continue;
+      c->xfer_batch = bsz;
+      const float ms = timed([&] {
+        const int r = transfer0(c, true, b, c->c1.b, R);
+        return r != MG_OK ? r : transfer0(c, false, c->c1.b, z, R);
+      });
+      if (ms < best) { best = ms; best_b = bsz; }
+    }
+    c->xfer_batch = best_b;
+  }
+  // 3. coarse stencil: ring depth, CTAs per SM, right-hand sides per launch (the
+  //    form the coarse GMRES uses: FP16 basis vectors when that basis exists)
+  CoarseLevel& L = c->c1;
+  if (L.Mh) {
+    const bool xh = L.Vh != nullptr;
+    const void* x = xh ? L.Vh : L.b;
+    CoarseTune best_t = c->ctune;
+    float best = 1e30f;
+    for (int st : {2, 3}) {
+      if (st == 3 && L.cg.n2 != 40) continue;
+      for (int ctas : {0, 8, 4})
+        for (int bsz : {16, 8, 4}) {
+          if (bsz > R && bsz != 16) continue;
+          c->ctune = CoarseTune{bsz, st, ctas};
+          const float ms = timed([&] { return coarse_apply(c, L, x, L.w, R, xh); });
+          if (ms < best) { best = ms; best_t = c->ctune; }
+        }
+    }
+    c->ctune = best_t;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != MG_OK) return rc;
+  TRY(check_device_error(c));
+  c->tune_source = 1;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache.push_back({key, TuneChoice{c->sap_shape, c->xfer_batch, c->ctune}});
   return MG_OK;
 }
 
@@ -1570,6 +1738,11 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
   c->sap_shape = std::getenv("SAPMG_SAP_SHAPE") ? std::atoi(std::getenv("SAPMG_SAP_SHAPE")) : 0;
   c->dirac_pair = std::getenv("SAPMG_DIRAC_PAIR") ? std::atoi(std::getenv("SAPMG_DIRAC_PAIR")) : 1;
+  c->xfer_batch = std::getenv("SAPMG_XFER_BATCH") ? std::max(1, std::atoi(std::getenv("SAPMG_XFER_BATCH"))) : 16;
+  if (const char* ct = std::getenv("SAPMG_COARSE_TUNE")) {        // "batch,stages,ctas"
+    int b = 16, st = 2, k = 0;
+    if (std::sscanf(ct, "%d,%d,%d", &b, &st, &k) == 3) c->ctune = CoarseTune{std::max(1, b), st == 3 ? 3 : 2, k};
+  }
   c->restrict_tf32 = std::getenv("SAPMG_RESTRICT_TF32") ? std::atoi(std::getenv("SAPMG_RESTRICT_TF32")) : 1;
   c->outer_dcgs2 = std::getenv("SAPMG_DCGS2") ? std::atoi(std::getenv("SAPMG_DCGS2")) : 1;
   c->coarse_fp16 = std::getenv("SAPMG_COARSE_FP16") ? std::atoi(std::getenv("SAPMG_COARSE_FP16")) : 1;
@@ -1766,7 +1939,7 @@ int mg_restrict_batch(mg_ctx* c, int level, const void* in, void* out, int prec,
   const void* src;
   TRY(stage_in(c, in, prec, blocked, nrhs, &src));
   ProfScope ps(c->prof, FAM_RESTRICT, c->s);
-  return launch_transfer0(true, c->pv_prec, c->g, src, out, c->Pv, c->N0, nrhs, c->restrict_tf32, c->s);
+  return transfer0(c, true, src, out, nrhs);
 }
 
 int mg_prolong_batch(mg_ctx* c, int level, const void* in, void* out, int prec, int nrhs) {
@@ -1783,7 +1956,7 @@ int mg_prolong_batch(mg_ctx* c, int level, const void* in, void* out, int prec, 
   void* dst = blocked ? out : c->io_b;
   {
     ProfScope ps(c->prof, FAM_PROLONG, c->s);
-    TRY(launch_transfer0(false, c->pv_prec, c->g, in, dst, c->Pv, c->N0, nrhs, c->restrict_tf32, c->s));
+    TRY(transfer0(c, false, in, dst, nrhs));
   }
   if (!blocked) {
     const int t = prec == P64 ? P64 : P32;
@@ -1914,6 +2087,13 @@ int mg_net_layer_forward(mg_ctx* c, int cin, int cout, const void* W, const void
   return launch_gconv_forward(c->g, c->U32, W, x, y, cin, cout, c->s);
 }
 
+int mg_net_layer_forward_bf16(mg_ctx* c, int cin, int cout, const void* W, const void* x, void* y) {
+  TRY(net_state(c, cin, cout));
+  if (!W || !x || !y) return fail(MG_ERR_ARG, "bad argument");
+  if (c->prec != MG_BF16) return fail(MG_ERR_STATE, "BF16 inference needs a BF16 context (BF16 links)");
+  return launch_gconv_forward_bf16(c->g, c->Us, W, x, y, cin, cout, c->s);
+}
+
 int mg_net_layer_backward(mg_ctx* c, int cin, int cout, const void* W, const void* x, const void* gy, void* gx,
                           void* gW) {
   TRY(net_state(c, cin, cout));
@@ -1972,6 +2152,17 @@ int mg_set_wait_limit(mg_ctx* c, int spins) {
   const int v = spins < 0 ? kMaxSpins : spins;
   SAPMG_CUDA_TRY(cudaMemcpyAsync(c->dev_err + 1, &v, sizeof(int), cudaMemcpyHostToDevice, c->s));
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  return MG_OK;
+}
+
+int mg_get_tuning(mg_ctx* c, int* out) {
+  if (!c || !out) return fail(MG_ERR_ARG, "bad argument");
+  out[0] = c->tune_source;
+  out[1] = c->sap_shape;
+  out[2] = c->xfer_batch;
+  out[3] = c->ctune.stages;
+  out[4] = c->ctune.ctas;
+  out[5] = c->ctune.batch;
   return MG_OK;
 }
 

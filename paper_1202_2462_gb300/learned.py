@@ -54,6 +54,24 @@ class GaugeNet:
                 x = y
         return x, cache
 
+    def forward_bf16(self, s, eta):
+        """Inference with BF16 storage: the weights rounded to BF16 and the
+        context's BF16 links (a BF16 context), FP32 activations."""
+        fs = eta.numel()
+        x = eta
+        last = len(self.shapes) - 1
+        for i, ((cout, cin), w) in enumerate(zip(self.shapes, self.weights)):
+            wb = torch.view_as_real(w).to(torch.bfloat16).contiguous()
+            y = torch.empty(cout * fs, dtype=torch.complex64, device="cuda")
+            B.mg_net_layer_forward_bf16(s.ctx, cin, cout, wb, x, y)
+            if i < last:
+                z = torch.empty_like(y)
+                B.mg_net_gate_forward(s.ctx, cout, y, z)
+                x = z
+            else:
+                x = y
+        return x
+
     def backward(self, s, out, cache, target):
         """Loss ||out - target||^2 / ||target||^2 and the weight gradients."""
         g = torch.empty_like(out)
@@ -105,21 +123,28 @@ class GaugeNet:
         s.smooth(b, z, sweeps)
         return z * (torch.linalg.vector_norm(eta_canonical) / torch.linalg.vector_norm(z))
 
-    def propose(self, s, eta_canonical):
-        """Network output for canonical noise fields (N, ...) as canonical complex64."""
+    def propose(self, s, eta_canonical, bf16=False):
+        """Network output for canonical noise fields (N, ...) as canonical
+        complex64; bf16: BF16 inference (s a BF16 context)."""
         outs = []
         for k in range(eta_canonical.shape[0]):
-            out, _ = self.forward(s, self.blocked(s, eta_canonical[k]))
+            x = self.blocked(s, eta_canonical[k])
+            out = self.forward_bf16(s, x) if bf16 else self.forward(s, x)[0]
             outs.append(self.canonical(s, out)[0])
         return torch.stack(outs)
 
 
 def study(train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5, eval_workload="32^3x64", n_vec=24,
-          sweeps=2, channels=16, layers=3, epochs=4, lr=1e-2, setup_iters=(2, 8), seed=1000):
-    """Train on seeded fields (noise -> bootstrap-smoothed noise), propose the
-    evaluation lattice's test vectors, and compare set-up time and outer
-    iterations of hierarchies built from the proposals and from plain noise
-    with the same number of bootstrap sweeps.  Returns a dict."""
+          sweeps=2, channels=16, layers=3, epochs=4, lr=1e-2, setup_iters=(1, 2, 4, 8), seed=1000):
+    """Train on seeded fields (noise -> bootstrap-smoothed noise, FP32), propose
+    the evaluation lattice's test vectors (BF16 inference), and compare
+    hierarchies built from the proposals and from plain noise, each refined by
+    the same number of bootstrap sweeps: set-up time (with the inference time
+    for the network), outer iterations per right-hand side of the 12
+    point-source solve, and the average residual reduction per outer
+    iteration rho = relres^(1 / iterations).  Returns a dict; 'equal_time'
+    pairs each network row with the noise row whose set-up took at least as
+    long."""
     import time
     import synth
     from .solver import Solver
@@ -147,13 +172,15 @@ def study(train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5, eval_work
     dims = tuple(wl["dims"])
     u = torch.from_numpy(synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"])).cuda()
     noise = torch.from_numpy(synth.test_vector_draw(dims, n_vec, seed + 7)).to(torch.complex64).cuda()
-    s = Solver(u, wl["c_sw"], wl["m0"], n_levels=1, precision="fp32", fgmres_m=2)
+    s = Solver(u, wl["c_sw"], wl["m0"], n_levels=1, precision="bf16", fgmres_m=2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    prop = net.propose(s, noise)
+    prop = net.propose(s, noise, bf16=True)
     torch.cuda.synchronize()
     t_infer = time.perf_counter() - t0
     s.close()
+    if not bool(torch.isfinite(torch.view_as_real(prop)).all()):
+        raise RuntimeError("the network's proposals are not finite")
     import numpy as np
     b = torch.from_numpy(np.ascontiguousarray(synth.point_sources(dims))).cuda()
     rows = []
@@ -163,18 +190,37 @@ def study(train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5, eval_work
             t0 = time.perf_counter()
             sol = Solver(u, wl["c_sw"], wl["m0"], n_levels=2, n_vec=(n_vec,), setup_iters=k, n_mr=wl["n_mr"],
                          nu_post=wl["nu_post"], coarse_iters=wl["coarse_iters"], fgmres_m=wl["fgmres_m"],
-                         precision=wl["precision"], nrhs_max=12, init_vectors=iv.to(torch.complex128).contiguous())
+                         precision=wl["precision"], nrhs_max=12, init_vectors=iv.to(torch.complex128).contiguous(),
+                         maxiter=2000)
             torch.cuda.synchronize()
-            ts = time.perf_counter() - t0
+            ts = time.perf_counter() - t0 + (t_infer if name == "network" else 0.0)
             t0 = time.perf_counter()
-            z, info, code = sol.solve(b)
+            try:
+                z, info, code = sol.solve(b)
+            except B.MgError as e:                       # recorded, not fatal: the row reports the failure
+                sol.close()
+                rows.append(dict(init=name, setup_iters=k, setup_s=ts, status=e.code, error=str(e)))
+                continue
             torch.cuda.synchronize()
             tsol = time.perf_counter() - t0
             sol.close()
-            rows.append(dict(init=name, setup_iters=k, setup_s=ts, solve_s=tsol, iterations_per_rhs=info.iterations / 12,
+            its = info.iterations / 12
+            rows.append(dict(init=name, setup_iters=k, setup_s=ts, solve_s=tsol, iterations_per_rhs=its,
+                             rho=float(info.relres ** (1.0 / its)) if its > 0 else None,
                              relres=info.relres, status=code))
+    equal = []
+    for r in rows:
+        if r["init"] != "network" or r["status"] != 0:
+            continue
+        slower = [q for q in rows if q["init"] == "noise" and q["status"] == 0 and q["setup_s"] >= r["setup_s"]]
+        if slower:
+            q = min(slower, key=lambda q: q["setup_s"])
+            equal.append(dict(network_sweeps=r["setup_iters"], noise_sweeps=q["setup_iters"],
+                              network_setup_s=r["setup_s"], noise_setup_s=q["setup_s"],
+                              network_its=r["iterations_per_rhs"], noise_its=q["iterations_per_rhs"]))
     return dict(train_loss_first=float(sum(losses[:8]) / 8), train_loss_last=float(sum(losses[-8:]) / 8),
-                train_s=t_train, inference_s=t_infer, n_vec=n_vec, sweeps_imitated=sweeps, rows=rows)
+                train_s=t_train, inference_s=t_infer, inference="bf16", n_vec=n_vec, sweeps_imitated=sweeps,
+                m0=wl["m0"], rows=rows, equal_time=equal)
 
 
 if __name__ == "__main__":

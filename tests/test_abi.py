@@ -54,7 +54,7 @@ def test_params_layout_and_defaults():
     ("tol", 0.0),
     ("precision", 9),
     ("setup2_iters", -1),
-    ("setup2_iters", 1),           # set-up part 2 needs two levels (default: one)
+    ("setup2_iters", 1),           # set-up part 2 needs a coarse level (default: one level)
 ])
 def test_setup_rejects_bad_params_on_host(field, value):
     b = _lib()

@@ -170,7 +170,7 @@ def test_sap_multi_rhs_matches_single(prec):
     s.close()
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("prec,n_mr", [("fp32", 4), ("fp16", 1), ("bf16", 4), ("bf16", 2)])
 def test_sap_pair_kernel_parity(prec, n_mr, shape, monkeypatch):
     """The paired Schwarz kernel (two right-hand sides per thread, packed

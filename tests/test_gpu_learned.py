@@ -153,3 +153,43 @@ def test_training_imitates_the_smoother_and_the_hierarchy_converges(ctx):
         assert code == 0
         its[name] = info.iterations
     print("learned set-up, outer iterations:", its)
+
+
+def test_bf16_inference_layer_parity():
+    """Inference with BF16 storage: the layer with BF16 weights and BF16 links
+    (FP32 activations and accumulation) against the oracle's layer on the
+    identically rounded weights and links, and the whole network's BF16
+    output against the oracle's forward pass on the rounded weights and
+    links."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    from paper_1202_2462_gb300.learned import GaugeNet
+    from tests.gpu_util import round_storage
+    u = synth.random_gauge_field(DIMS, 0.3, 111)
+    s = G.Solver(dev(torch, u), CSW, M0, n_levels=1, precision="bf16", fgmres_m=2)
+    ub = round_storage(u, "bf16")
+    cin, cout = 3, 2
+    w = _weights(cout, cin, 112)
+    wb = round_storage(w, "bf16")
+    x = synth.random_spinor(DIMS, 113, nvec=cin).astype(np.complex64).astype(np.complex128)
+    xd = _blocked(torch, G, s, x)
+    yd = torch.empty(cout * xd.numel() // cin, dtype=torch.complex64, device="cuda")
+    wdev = torch.view_as_real(dev(torch, w, torch.complex64)).to(torch.bfloat16).contiguous()
+    G.mg_net_layer_forward_bf16(s.ctx, cin, cout, wdev, xd, yd)
+    ref = L.layer(ub, wb, x)
+    got = _canonical(torch, G, s, yd, cout)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 2e-6
+    net = GaugeNet(channels=4, layers=3, seed=114)
+    ws = [round_storage(host(w).astype(np.complex128), "bf16") for w in net.weights]
+    eta = synth.random_spinor(DIMS, 115).astype(np.complex64).astype(np.complex128)
+    out = net.forward_bf16(s, _blocked(torch, G, s, eta[None]))
+    ref_out, _ = L.forward(ub, ws, eta)
+    got = _canonical(torch, G, s, out, 1)[0]
+    assert np.max(np.abs(got - ref_out)) / np.max(np.abs(ref_out)) < 1e-5
+    with pytest.raises(G.MgError):                     # an FP32 context has no BF16 links
+        t = G.Solver(dev(torch, u), CSW, M0, n_levels=1, precision="fp32", fgmres_m=2)
+        try:
+            G.mg_net_layer_forward_bf16(t.ctx, cin, cout, wdev, xd, yd)
+        finally:
+            t.close()
+    s.close()
