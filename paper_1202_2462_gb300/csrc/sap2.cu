@@ -127,9 +127,11 @@ __global__ void __launch_bounds__(256, MINB)
       pp = fma2(p[c].re, p[c].re, pp); pp = fma2(p[c].im, p[c].im, pp);
     }
     block_reduce6(pr_re, pr_im, pp, red);             // its barrier follows every neighbour read of rho
+    // alpha = <p, rho> / <p, p> by division (a reciprocal of a tiny denormal <p, p>
+    // overflows, and 0 * inf would be NaN; the quotient is scale-invariant)
     float2 al_re = f2(0.f), al_im = f2(0.f);
-    if (pp.x > 0.f) { const float q = 1.f / pp.x; al_re.x = pr_re.x * q; al_im.x = pr_im.x * q; }
-    if (pp.y > 0.f) { const float q = 1.f / pp.y; al_re.y = pr_re.y * q; al_im.y = pr_im.y * q; }
+    if (pp.x > 0.f) { al_re.x = pr_re.x / pp.x; al_im.x = pr_im.x / pp.x; }
+    if (pp.y > 0.f) { al_re.y = pr_re.y / pp.y; al_im.y = pr_im.y / pp.y; }
     const float2 nal_im = make_float2(-al_im.x, -al_im.y);
     const bool first = it == 0, last = it == n_mr - 1;
 #pragma unroll
@@ -342,9 +344,10 @@ __global__ void __launch_bounds__(256, 1)
         pp = fma2(p[c].re, p[c].re, pp); pp = fma2(p[c].im, p[c].im, pp);
       }
       block_reduce6(pr_re, pr_im, pp, red);           // its barrier follows every neighbour read of rho
+      // alpha by division, as in the pair kernel above
       float2 al_re = f2(0.f), al_im = f2(0.f);
-      if (pp.x > 0.f) { const float q = 1.f / pp.x; al_re.x = pr_re.x * q; al_im.x = pr_im.x * q; }
-      if (pp.y > 0.f) { const float q = 1.f / pp.y; al_re.y = pr_re.y * q; al_im.y = pr_im.y * q; }
+      if (pp.x > 0.f) { al_re.x = pr_re.x / pp.x; al_im.x = pr_im.x / pp.x; }
+      if (pp.y > 0.f) { al_re.y = pr_re.y / pp.y; al_im.y = pr_im.y / pp.y; }
       const float2 nal_im = make_float2(-al_im.x, -al_im.y);
       const float2 nal_re = make_float2(-al_re.x, -al_re.y);
       const bool last = it == n_mr - 1;

@@ -256,3 +256,32 @@ def test_dirac_pair_kernel_matches_single_kernel(monkeypatch):
         outs.append(host(s.dirac(psi, MG_FP32)))
         s.close()
     assert np.max(np.abs(outs[0] - outs[1])) / np.max(np.abs(outs[1])) < 2e-6
+
+
+@pytest.mark.parametrize("shape", [0, 3])
+def test_sap_pair_kernel_tiny_blocks_stay_finite(shape, monkeypatch):
+    """Blocks whose residual is ~1e-21 make <p, p> a denormal FP32 number: the
+    MR coefficient must still be finite (alpha by division; a reciprocal of
+    the denormal overflows to inf and 0 * inf gives NaN).  Two right-hand
+    sides with a block-wise scale from 1 down to 1e-21, one sweep from zero,
+    against the oracle."""
+    monkeypatch.setenv("SAPMG_SAP_SHAPE", str(shape))
+    torch = torch_cuda()
+    dims = (8, 8, 8, 16)
+    u = synth.random_gauge_field(dims, 0.5, 41)
+    m0 = 0.05
+    op = WilsonClover(round_storage(u, "bf16"), m0, 1.0)
+    op.a = round_storage(WilsonClover(u, m0, 1.0).a, "bf16")
+    bl = BlockDecomposition(dims, (4, 4, 4, 4))
+    scale = 10.0 ** (-(bl.block_id % 8) * 3)                    # 1, 1e-3, ..., 1e-21 per block
+    b = synth.random_spinor(dims, 42, nvec=2) * scale[None, ..., None, None]
+    b = b.astype(np.complex64).astype(np.complex128)
+    s = _solver(torch, u, 1.0, m0, False, n_mr=4, precision="bf16", nrhs_max=2)
+    z = torch.zeros((2,) + dims[::-1] + (4, 3), dtype=torch.complex64, device="cuda")
+    s.smooth(dev(torch, b, torch.complex64), z, 1)
+    out = host(z).astype(np.complex128)
+    s.close()
+    assert np.all(np.isfinite(out))
+    for k in range(2):
+        ref = sap_sweep(op, bl, b[k], np.zeros_like(b[k]), 4)
+        assert np.max(np.abs(out[k] - ref)) / np.max(np.abs(ref)) < 5e-6, k
