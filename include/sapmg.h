@@ -195,6 +195,20 @@ int mg_harmonic_ritz(int m, const double* hbar, double* theta, double* y);
 int mg_eigh(int n, const double* a, double* w, double* v);
 
 /* Free every device buffer the context owns. */
+/* Checkpoint of a set-up (no paper counterpart; Sec. 3's set-up is built
+ * once and serves every later solve): write the context's test vectors --
+ * the locally orthonormal vectors defining P on level 0 and, with three
+ * levels, on level 1, in FP64 -- with the lattice, levels, N, blocking, m0 and
+ * c_sw they belong to and a checksum, to the file `path`.  Synchronises. */
+int mg_save(mg_ctx* ctx, const char* path);
+/* Build a context as mg_setup does, except that the test vectors come from a
+ * file written by mg_save instead of the bootstrap set-up (both parts): P and
+ * the coarse operators are rebuilt from them and the links U given here.
+ * The file's lattice, levels, N, blocking, m0 and c_sw must equal the
+ * arguments (MG_ERR_ARG otherwise, also for a truncated or corrupted file);
+ * precision, nrhs_max and the solver parameters may differ.  Synchronises. */
+int mg_setup_load(const double* U, double c_sw, double m0, const mg_params* p, const char* path, mg_ctx** out);
+
 void mg_destroy(mg_ctx* ctx);
 
 /* Message of the last error (thread-local, valid until the next call). */
@@ -341,7 +355,8 @@ long long mg_launch_count(void);
  * nrhs_max, precision and levels), out[1] = Schwarz launch shape (0: two CTAs
  * per SM, rho re-read for the update; 1: rho in registers; 2: one CTA per SM;
  * 3: one CTA per block with the block's fields in shared memory, every pair
- * of right-hand sides in turn; 4: shape 3 with branch-free hops), out[2] = right-hand sides per transfer
+ * of right-hand sides in turn; 4, 5: shape 3 with the x, y, z (4) or all (5)
+ * hops computed without branches), out[2] = right-hand sides per transfer
  * launch, out[3] = ring depth, out[4] = CTA-per-SM cap (0: none) and out[5] =
  * right-hand sides per launch of the FP16 tensor-core coarse stencil.  Every
  * choice computes the same results bit for bit; only the time differs. */

@@ -81,6 +81,9 @@ _SIGNATURES = {
     "mg_harmonic_ritz": (_I, [_I, _VP, _VP, _VP]),
     "mg_eigh": (_I, [_I, _VP, _VP, _VP]),
     "mg_destroy": (None, [_VP]),
+    "mg_save": (_I, [_VP, ctypes.c_char_p]),
+    "mg_setup_load": (_I, [_VP, ctypes.c_double, ctypes.c_double, ctypes.POINTER(MgParams), ctypes.c_char_p,
+                           ctypes.POINTER(_VP)]),
     "mg_last_error": (ctypes.c_char_p, []),
     "mg_sizeof_params": (ctypes.c_ulong, []),
     "mg_pack_spinor": (_I, [_VP, _VP, _VP, _I, _I]),
@@ -170,6 +173,18 @@ def mg_default_params():
 def mg_setup(U, c_sw, m0, params):
     ctx = ctypes.c_void_p()
     _check(lib().mg_setup(_ptr(U), float(c_sw), float(m0), ctypes.byref(params), ctypes.byref(ctx)), "mg_setup")
+    return ctx
+
+
+def mg_save(ctx, path):
+    return _check(lib().mg_save(ctx, os.fsencode(path)), "mg_save")
+
+
+def mg_setup_load(U, c_sw, m0, params, path):
+    """A context whose test vectors come from a file written by mg_save."""
+    ctx = _VP()
+    _check(lib().mg_setup_load(_ptr(U), float(c_sw), float(m0), ctypes.byref(params), os.fsencode(path),
+                               ctypes.byref(ctx)), "mg_setup_load")
     return ctx
 
 

@@ -163,6 +163,8 @@ struct mg_ctx {
   void* V64 = nullptr;                     // locally orthonormal test vectors, FP64 vector-major
   void* Vs64 = nullptr;                    // set-up only: the smoothed vectors before local orthonormalisation
   void* part2_buf = nullptr;               // set-up only (three levels): part-1 vectors kept for set-up part 2
+  const std::vector<double2>* load_v0 = nullptr;  // mg_setup_load: the saved level-0 vectors (host)
+  const std::vector<double2>* load_w1 = nullptr;  // mg_setup_load: the saved level-1 vectors (host, three levels)
   void* Pv = nullptr;                      // P in cycle storage, block-major
   CoarseLevel c1;
   // three levels: level-1 Schwarz boxes, level-2 aggregates, level-1 vectors, level 2
@@ -1077,6 +1079,7 @@ static int build_level0_operators(mg_ctx* c) {
 //     the smallest eigenvalues give the new test vectors V y_k;
 //  5. P and D_c rebuilt from them.
 static int setup_level1(mg_ctx* c);
+static int finish_level1(mg_ctx* c);
 
 static int setup_part2(mg_ctx* c, void* V2) {
   const mg_params& p = c->p;
@@ -1252,6 +1255,10 @@ static int setup_level0(mg_ctx* c) {
   const mg_params& p = c->p;
   c->V64 = c->alloc((size_t)N * n * 16);
   if (!c->V64) return fail(MG_ERR_OOM, "test vectors");
+  if (c->load_v0) {                        // a saved set-up: its vectors replace both bootstrap parts
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->V64, c->load_v0->data(), (size_t)N * n * 16, cudaMemcpyHostToDevice, c->s));
+    return build_level0_operators(c);
+  }
   if (p.init_vectors) {
     TRY(launch_pack_spinor(P64, p.init_vectors, P64, c->V64, c->g, N, c->s));
   } else {
@@ -1312,6 +1319,11 @@ static int setup_level1(mg_ctx* c) {
   void* p0buf = c->alloc((size_t)N0 * nf * 16);
   if (!c->W64) c->W64 = c->alloc((size_t)N1 * n1 * 16);         // reused when set-up part 2 rebuilds level 1
   if (!p0buf || !c->W64) return fail(MG_ERR_OOM, "level-1 vectors");
+  if (c->load_w1) {                        // a saved set-up: the level-1 vectors as saved
+    SAPMG_CUDA_TRY(cudaMemcpyAsync(c->W64, c->load_w1->data(), (size_t)N1 * n1 * 16, cudaMemcpyHostToDevice, c->s));
+    c->release(p0buf);
+    return finish_level1(c);
+  }
   TRY(launch_store_p0(P64, c->g, c->V64, p0buf, N0, c->s));
   for (int k = 0; k < N1; ++k)
     TRY(launch_transfer0(true, P64, c->g, (char*)c->Vs64 + (size_t)k * nf * 16, (char*)c->W64 + (size_t)k * n1 * 16,
@@ -1342,6 +1354,15 @@ static int setup_level1(mg_ctx* c) {
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
   c->release(zero1);
   c->release(t32);
+  return finish_level1(c);
+}
+
+// Level 1's local orthonormalisation on the level-2 aggregates, its vectors in
+// the cycle's type and the level-2 Galerkin operator D_c2 = P1^dagger D_c1 P1.
+static int finish_level1(mg_ctx* c) {
+  CoarseLevel& L1 = c->c1;
+  const size_t n1 = L1.n();
+  const int N1 = c->N1;
   TRY(launch_block_gs1(L1.cg, c->agg1, c->W64, N1, c->s));
   if (c->vt == P64) {
     c->W = c->W64;
@@ -1606,7 +1627,7 @@ static int autotune(mg_ctx* c) {
   if (R >= 2 && R % 2 == 0 && c->sap_shape >= 0) {
     int best_shape = c->sap_shape;
     float best = 1e30f;
-    for (int shape = 0; shape <= 4; ++shape) {
+    for (int shape = 0; shape <= 5; ++shape) {
       c->sap_shape = shape;
       const float ms = timed([&] { return smoother_sweeps(c, b, z, 1, R); });
       if (ms < best) { best = ms; best_shape = shape; }
@@ -1693,6 +1714,67 @@ static int noalloc_scratch(void** out) {
   return MG_OK;
 }
 
+// ------------------------------------------------------------ saved set-ups
+// File layout (little-endian, as the host writes it): 8-byte magic, then the
+// int32 header below, the doubles m0 and c_sw, the int64 counts of complex
+// numbers in the level-0 and level-1 vector sets, the FP64 vectors (level 0:
+// the locally orthonormal test vectors, N0 x V x 12 in the blocked layout;
+// level 1 when there are three levels: N1 x n1), and an FNV-1a 64-bit hash of
+// everything before it.
+static const char kSaveMagic[8] = {'S', 'A', 'P', 'M', 'G', 'S', 'U', '1'};
+struct SaveHeader {
+  int32_t dims[4], antiperiodic_t, n_levels, n_vec[2], agg2[4], sap_block2[4];
+};
+
+static uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* p = (const unsigned char*)data;
+  for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 0x100000001b3ull; }
+  return h;
+}
+
+static SaveHeader save_header(const mg_params& p) {
+  SaveHeader h;
+  std::memset(&h, 0, sizeof(h));
+  for (int mu = 0; mu < 4; ++mu) {
+    h.dims[mu] = p.dims[mu];
+    h.agg2[mu] = p.n_levels == 3 ? p.agg2[mu] : 0;
+    h.sap_block2[mu] = p.n_levels == 3 ? p.sap_block2[mu] : 0;
+  }
+  h.antiperiodic_t = p.antiperiodic_t;
+  h.n_levels = p.n_levels;
+  h.n_vec[0] = p.n_vec[0];
+  h.n_vec[1] = p.n_levels == 3 ? p.n_vec[1] : 0;
+  return h;
+}
+
+// Everything mg_setup does once the parameters are valid (also the body of
+// mg_setup_load, whose context carries the saved vectors).
+static int setup_context(mg_ctx* c, const double* U, double c_sw, double m0, const mg_params* p) {
+  c->p = *p;
+  c->g = make_geom(p->dims);
+  c->s = (cudaStream_t)p->stream;
+  c->prec = p->precision;
+  c->vt = p->precision == MG_FP64 ? P64 : P32;
+  c->pv_prec = p->precision == MG_BF16 ? P16 : p->precision;
+  c->dc_prec = p->precision == MG_FP64 ? P64 : P32;
+  c->coarse_reorth = std::getenv("SAPMG_COARSE_REORTH") ? std::atoi(std::getenv("SAPMG_COARSE_REORTH")) : 0;
+  c->generic_coarse = std::getenv("SAPMG_GENERIC_COARSE") ? std::atoi(std::getenv("SAPMG_GENERIC_COARSE")) : 0;
+  c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
+  c->sap_shape = std::getenv("SAPMG_SAP_SHAPE") ? std::atoi(std::getenv("SAPMG_SAP_SHAPE")) : 0;
+  c->dirac_pair = std::getenv("SAPMG_DIRAC_PAIR") ? std::atoi(std::getenv("SAPMG_DIRAC_PAIR")) : 1;
+  c->xfer_batch = std::getenv("SAPMG_XFER_BATCH") ? std::max(1, std::atoi(std::getenv("SAPMG_XFER_BATCH"))) : 16;
+  if (const char* ct = std::getenv("SAPMG_COARSE_TUNE")) {        // "batch,stages,ctas"
+    int b = 16, st = 2, k = 0;
+    if (std::sscanf(ct, "%d,%d,%d", &b, &st, &k) == 3) c->ctune = CoarseTune{std::max(1, b), st == 3 ? 3 : 2, k};
+  }
+  c->restrict_tf32 = std::getenv("SAPMG_RESTRICT_TF32") ? std::atoi(std::getenv("SAPMG_RESTRICT_TF32")) : 1;
+  c->outer_dcgs2 = std::getenv("SAPMG_DCGS2") ? std::atoi(std::getenv("SAPMG_DCGS2")) : 1;
+  c->coarse_fp16 = std::getenv("SAPMG_COARSE_FP16") ? std::atoi(std::getenv("SAPMG_COARSE_FP16")) : 1;
+  c->m0 = m0;
+  c->csw = c_sw;
+  return do_setup(c, U);
+}
+
 // ============================================================ C-ABI
 extern "C" {
 
@@ -1726,29 +1808,97 @@ int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx
   *out = nullptr;
   TRY(validate(p));
   mg_ctx* c = new mg_ctx();
-  c->p = *p;
-  c->g = make_geom(p->dims);
-  c->s = (cudaStream_t)p->stream;
-  c->prec = p->precision;
-  c->vt = p->precision == MG_FP64 ? P64 : P32;
-  c->pv_prec = p->precision == MG_BF16 ? P16 : p->precision;
-  c->dc_prec = p->precision == MG_FP64 ? P64 : P32;
-  c->coarse_reorth = std::getenv("SAPMG_COARSE_REORTH") ? std::atoi(std::getenv("SAPMG_COARSE_REORTH")) : 0;
-  c->generic_coarse = std::getenv("SAPMG_GENERIC_COARSE") ? std::atoi(std::getenv("SAPMG_GENERIC_COARSE")) : 0;
-  c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
-  c->sap_shape = std::getenv("SAPMG_SAP_SHAPE") ? std::atoi(std::getenv("SAPMG_SAP_SHAPE")) : 0;
-  c->dirac_pair = std::getenv("SAPMG_DIRAC_PAIR") ? std::atoi(std::getenv("SAPMG_DIRAC_PAIR")) : 1;
-  c->xfer_batch = std::getenv("SAPMG_XFER_BATCH") ? std::max(1, std::atoi(std::getenv("SAPMG_XFER_BATCH"))) : 16;
-  if (const char* ct = std::getenv("SAPMG_COARSE_TUNE")) {        // "batch,stages,ctas"
-    int b = 16, st = 2, k = 0;
-    if (std::sscanf(ct, "%d,%d,%d", &b, &st, &k) == 3) c->ctune = CoarseTune{std::max(1, b), st == 3 ? 3 : 2, k};
+  const int rc = setup_context(c, U, c_sw, m0, p);
+  if (rc < 0) {
+    cudaStreamSynchronize(c->s);
+    delete c;
+    return rc;
   }
-  c->restrict_tf32 = std::getenv("SAPMG_RESTRICT_TF32") ? std::atoi(std::getenv("SAPMG_RESTRICT_TF32")) : 1;
-  c->outer_dcgs2 = std::getenv("SAPMG_DCGS2") ? std::atoi(std::getenv("SAPMG_DCGS2")) : 1;
-  c->coarse_fp16 = std::getenv("SAPMG_COARSE_FP16") ? std::atoi(std::getenv("SAPMG_COARSE_FP16")) : 1;
-  c->m0 = m0;
-  c->csw = c_sw;
-  const int rc = do_setup(c, U);
+  *out = c;
+  return MG_OK;
+}
+
+int mg_save(mg_ctx* c, const char* path) {
+  if (!c || !path) return fail(MG_ERR_ARG, "bad argument");
+  if (!c->V64 || c->p.n_levels < 2) return fail(MG_ERR_STATE, "no multilevel set-up to save");
+  const SaveHeader h = save_header(c->p);
+  const int64_t n0 = (int64_t)c->N0 * (int64_t)c->fine_n();
+  const int64_t n1 = c->p.n_levels == 3 ? (int64_t)c->N1 * (int64_t)c->c1.n() : 0;
+  std::vector<double2> v0((size_t)n0), w1((size_t)n1);
+  SAPMG_CUDA_TRY(cudaMemcpyAsync(v0.data(), c->V64, (size_t)n0 * 16, cudaMemcpyDeviceToHost, c->s));
+  if (n1) SAPMG_CUDA_TRY(cudaMemcpyAsync(w1.data(), c->W64, (size_t)n1 * 16, cudaMemcpyDeviceToHost, c->s));
+  SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(MG_ERR_ARG, std::string("cannot open ") + path + " for writing");
+  uint64_t hash = 0xcbf29ce484222325ull;
+  bool ok = true;
+  auto put = [&](const void* d, size_t bytes) {
+    hash = fnv1a(hash, d, bytes);
+    ok = ok && std::fwrite(d, 1, bytes, f) == bytes;
+  };
+  put(kSaveMagic, sizeof(kSaveMagic));
+  put(&h, sizeof(h));
+  put(&c->m0, sizeof(double));
+  put(&c->csw, sizeof(double));
+  put(&n0, sizeof(n0));
+  put(&n1, sizeof(n1));
+  put(v0.data(), (size_t)n0 * 16);
+  if (n1) put(w1.data(), (size_t)n1 * 16);
+  ok = ok && std::fwrite(&hash, 1, sizeof(hash), f) == sizeof(hash);
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? MG_OK : fail(MG_ERR_ARG, std::string("writing ") + path + " failed");
+}
+
+int mg_setup_load(const double* U, double c_sw, double m0, const mg_params* p, const char* path, mg_ctx** out) {
+  if (!U || !p || !path || !out) return fail(MG_ERR_ARG, "null argument");
+  *out = nullptr;
+  TRY(validate(p));
+  if (p->n_levels < 2) return fail(MG_ERR_ARG, "a saved set-up needs n_levels 2 or 3");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(MG_ERR_ARG, std::string("cannot open ") + path);
+  uint64_t hash = 0xcbf29ce484222325ull;
+  bool ok = true;
+  auto get = [&](void* d, size_t bytes) {
+    ok = ok && std::fread(d, 1, bytes, f) == bytes;
+    if (ok) hash = fnv1a(hash, d, bytes);
+  };
+  char magic[8];
+  SaveHeader h;
+  double fm0 = 0, fcsw = 0;
+  int64_t n0 = 0, n1 = 0;
+  get(magic, sizeof(magic));
+  get(&h, sizeof(h));
+  get(&fm0, sizeof(double));
+  get(&fcsw, sizeof(double));
+  get(&n0, sizeof(n0));
+  get(&n1, sizeof(n1));
+  const SaveHeader want = save_header(*p);
+  const Geom g = make_geom(p->dims);
+  const int64_t want0 = (int64_t)p->n_vec[0] * g.V * 12;
+  std::string why;
+  if (!ok || std::memcmp(magic, kSaveMagic, sizeof(magic)) != 0) why = "not a saved set-up";
+  else if (std::memcmp(&h, &want, sizeof(h)) != 0) why = "lattice, levels, N or blocking differ from the parameters";
+  else if (fm0 != m0 || fcsw != c_sw) why = "m0 or c_sw differ from the saved set-up";
+  else if (n0 != want0 || n1 < 0 || (p->n_levels == 2 && n1 != 0)) why = "vector counts do not match";
+  std::vector<double2> v0, w1;
+  if (why.empty()) {
+    v0.resize((size_t)n0);
+    w1.resize((size_t)n1);
+    get(v0.data(), (size_t)n0 * 16);
+    if (n1) get(w1.data(), (size_t)n1 * 16);
+    uint64_t stored = 0;
+    const uint64_t computed = hash;
+    ok = ok && std::fread(&stored, 1, sizeof(stored), f) == sizeof(stored);
+    if (!ok) why = "the file is truncated";
+    else if (stored != computed) why = "checksum mismatch (the file is corrupted)";
+  }
+  std::fclose(f);
+  if (!why.empty()) return fail(MG_ERR_ARG, std::string(path) + ": " + why);
+  mg_ctx* c = new mg_ctx();
+  c->load_v0 = &v0;
+  c->load_w1 = n1 ? &w1 : nullptr;
+  const int rc = setup_context(c, U, c_sw, m0, p);
+  c->load_v0 = c->load_w1 = nullptr;
   if (rc < 0) {
     cudaStreamSynchronize(c->s);
     delete c;

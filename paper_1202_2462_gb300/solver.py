@@ -36,7 +36,7 @@ class Solver:
     (used with ``setup2_iters`` > 0).
     """
 
-    def __init__(self, U, c_sw, m0, init_vectors=None, setup2_start=None, stream=None, **params):
+    def __init__(self, U, c_sw, m0, init_vectors=None, setup2_start=None, stream=None, load=None, **params):
         if not (U.is_cuda and U.dtype == torch.complex128 and U.is_contiguous()):
             raise ValueError("U must be a contiguous complex128 CUDA tensor")
         lt, lz, ly, lx = U.shape[:4]
@@ -56,7 +56,9 @@ class Solver:
             self._start = setup2_start.contiguous()
             self.params.setup2_start = self._start.data_ptr()
         self.prec = self.params.precision
-        self.ctx = B.mg_setup(U, c_sw, m0, self.params)
+        # load: a file written by save(); its test vectors replace the bootstrap set-up
+        self.ctx = B.mg_setup(U, c_sw, m0, self.params) if load is None else \
+            B.mg_setup_load(U, c_sw, m0, self.params, load)
         self._init = None
         self._start = None
 
@@ -87,6 +89,10 @@ class Solver:
         z = torch.empty_like(b)
         code, info = B.mg_cgn_solve(self.ctx, b, z, nrhs, prec, tol, maxiter)
         return z, info, code
+
+    def save(self, path):
+        """Write the set-up's test vectors to `path` (mg_save)."""
+        B.mg_save(self.ctx, path)
 
     def close(self):
         if self.ctx is not None:
