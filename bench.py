@@ -43,7 +43,8 @@ FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (nominal)
 SAP_DRAM_BYTES_PER_UNIT = {0: (266.179328e6 + 66.372352e6) / (65536 * 12),
                            3: (263.003904e6 + 52.152320e6) / (65536 * 12)}
 SAP_KERNEL = {-1: "sap_colour_kernel", 0: "sap_colour_pair_kernel", 1: "sap_colour_pair_kernel",
-              2: "sap_colour_pair_kernel", 3: "sap_block_kernel", 4: "sap_block_kernel"}
+              2: "sap_colour_pair_kernel", 3: "sap_block_kernel", 4: "sap_block_kernel",
+              5: "sap_block_kernel"}
 
 
 def flops_dirac_site():
@@ -481,6 +482,14 @@ def run_ours(a, wl):
         torch.distributed.barrier()
     launches = G.mg_launch_count() - l0
     clk = clocks.stop()
+    if a.history and rank == 0:
+        # the last timed solve's residual history as JSON lines (one per entry, then rho per RHS)
+        with open(a.history, "w") as f:
+            for q, d in sorted(s.history().items()):
+                for kind in ("estimates", "fp64"):
+                    for it, r in d[kind]:
+                        f.write(json.dumps({"rhs": q, "iteration": it, "relres": r, "kind": kind}) + "\n")
+                f.write(json.dumps({"rhs": q, "rho": d["rho"], "kind": "convergence_factor"}) + "\n")
     ms = ev0.elapsed_time(ev1) / a.steps
     n_prof, ms_prof = G.mg_get_profile(s.ctx, G.PROFILE_FAMILIES[dominant])
     bytes_prof = G.mg_get_profile_bytes(s.ctx, G.PROFILE_FAMILIES[dominant])
@@ -751,6 +760,8 @@ def main():
     ap.add_argument("--kernel", choices=["dirac", "sap"], default=None,
                     help="instead of the bench line: time one kernel family alone (see run_kernel)")
     ap.add_argument("--nrhs", type=int, default=1, help="with --kernel: right-hand sides per launch")
+    ap.add_argument("--history", default=None,
+                    help="write the last timed solve's residual history to this file as JSON lines")
     ap.add_argument("--oracle-study", action="store_true",
                     help="instead of the bench line: oracle kernel timings at every size and the 8^4 oracle solve")
     ap.add_argument("--fp64-rhs", type=int, default=None,

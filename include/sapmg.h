@@ -362,6 +362,17 @@ long long mg_launch_count(void);
  * choice computes the same results bit for bit; only the time differs. */
 int mg_get_tuning(mg_ctx* ctx, int* out);
 
+/* Residual history of the context's last mg_solve (no paper counterpart;
+ * metrics): entries of three doubles (iteration, right-hand side, relative
+ * residual).  iteration >= 1: the least-squares residual estimate of the
+ * flexible GMRES after that many preconditioned iterations of that
+ * right-hand side, scaled to ||b - D x|| / ||b|| (in the mixed form through
+ * the FP64 correction's ||r||); iteration = -(k + 1): the FP64-recomputed
+ * ||b - D x|| / ||b|| after k iterations (every restart or defect
+ * correction, and the final one).  Copies at most max_entries entries to out
+ * (out may be NULL) and returns the number stored. */
+int mg_get_history(mg_ctx* ctx, double* out, int max_entries);
+
 /* Wait for the context's stream and report a device-side wait that gave up
  * since the last check (MG_ERR_TIMEOUT; the flag is then cleared).  The
  * asynchronous entry points (sap_smooth, dirac_apply, the transfers) leave

@@ -16,7 +16,7 @@ from .binding import (
     MgError, mg_default_params, mg_setup, mg_save, mg_setup_load, dirac_apply, sap_smooth, mg_solve, mg_cgn_solve, mg_harmonic_ritz, mg_eigh, mg_destroy, mg_pack_spinor,
     mg_unpack_spinor, mg_clover_export, mg_get_vectors, mg_get_coarse_op, mg_restrict, mg_prolong,
     mg_coarse_apply, mg_coarse_apply_batch, mg_restrict_batch, mg_prolong_batch, mg_coarse_solve, mg_coarse_solve_noalloc, mg_precondition, mg_set_profiling, mg_get_profile, mg_get_profile_bytes, mg_reset_profile,
-    mg_launch_count, mg_probe_peaks, mg_sync, mg_set_wait_limit, mg_get_tuning, profile_mask, PROFILE_FAMILIES, mg_net_layer_forward, mg_net_layer_forward_bf16, mg_net_layer_backward,
+    mg_launch_count, mg_probe_peaks, mg_sync, mg_set_wait_limit, mg_get_tuning, mg_get_history, profile_mask, PROFILE_FAMILIES, mg_net_layer_forward, mg_net_layer_forward_bf16, mg_net_layer_backward,
     mg_net_gate_forward, mg_net_gate_backward, mg_net_loss, mg_adam_step,
 )
 from .solver import Solver

@@ -106,6 +106,7 @@ _SIGNATURES = {
     "mg_reset_profile": (_I, [_VP]),
     "mg_launch_count": (ctypes.c_longlong, []),
     "mg_sync": (_I, [_VP]),
+    "mg_get_history": (_I, [_VP, _VP, _I]),
     "mg_get_tuning": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "mg_set_wait_limit": (_I, [_VP, _I]),
     "mg_probe_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -356,6 +357,14 @@ def mg_get_tuning(ctx):
     _check(lib().mg_get_tuning(ctx, a), "mg_get_tuning")
     return {"source": ("default", "tuned", "cached")[a[0]], "sap_shape": a[1], "xfer_batch": a[2],
             "coarse_stages": a[3], "coarse_ctas_per_sm": a[4], "coarse_batch": a[5]}
+
+
+def mg_get_history(ctx):
+    """The last solve's residual history: a list of (iteration, rhs, relative residual)."""
+    n = _check(lib().mg_get_history(ctx, None, 0), "mg_get_history")
+    buf = (ctypes.c_double * (3 * max(n, 1)))()
+    _check(lib().mg_get_history(ctx, buf, n), "mg_get_history")
+    return [(int(buf[3 * k]), int(buf[3 * k + 1]), buf[3 * k + 2]) for k in range(n)]
 
 
 def mg_sync(ctx):

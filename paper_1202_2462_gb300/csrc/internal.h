@@ -94,8 +94,9 @@ int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const voi
 // CTAs per SM, rho re-read from shared memory for the update; 1: two CTAs per
 // SM, rho kept in registers; 2: one CTA per SM, rho kept in registers; 3: one
 // CTA per block holding the block's fields in shared memory for every pair;
-// 4: shape 3 with the x, y, z hops of the MR steps computed without branches
-// (err: the device flag a bounded wait that gives up raises; needed by shapes 3, 4).
+// 4: shape 3 with the x, y, z hops of the MR steps computed without branches;
+// 5: all four directions without branches (err: the device flag a bounded
+// wait that gives up raises; needed by shapes 3-5).
 int launch_sap_colour_pair(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
                            int n_mr, int nrhs, cudaStream_t s, int shape, int* err);
 // sap_shift.cu: the same pass for D - shift[r] (per right-hand side r; device

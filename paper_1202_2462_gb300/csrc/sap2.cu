@@ -276,7 +276,7 @@ __device__ __forceinline__ void residual_pair(const Geom& g, const float2* __res
   }
 }
 
-template <class TG, bool BF>
+template <class TG, int BF>
 __global__ void __launch_bounds__(256, 1)
     sap_block_kernel(float2* __restrict__ z, const float2* __restrict__ b, const TG* __restrict__ U,
                      const TG* __restrict__ A, Geom g, int colour, int n_mr, int npairs, int* __restrict__ err) {
@@ -320,11 +320,12 @@ __global__ void __launch_bounds__(256, 1)
       __syncthreads();                                 // rho of every site written
       P2 p[12];
       clover2s<TG>(As, loc, [&](int k) { return lds2(rs, k * 256 + loc); }, p);
-      if (BF) {                                        // BF: branch-free x, y, z hops
+      if (BF) {                                        // BF 1: branch-free x, y, z hops; 2: also t
         block_hops2s_both<0>(Us, rs, loc, p);
         block_hops2s_both<1>(Us, rs, loc, p);
         block_hops2s_both<2>(Us, rs, loc, p);
-        block_hops2s<3>(Us, rs, loc, p);
+        if (BF == 2) block_hops2s_both<3>(Us, rs, loc, p);
+        else block_hops2s<3>(Us, rs, loc, p);
       } else {
         block_hops2s<0>(Us, rs, loc, p);
         asm volatile("" ::: "memory");
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
-template <class TG, bool BF>
+template <class TG, int BF>
 static int run_block(const Geom& g, void* z, const void* b, const void* U, const void* A, int colour, int n_mr,
                      int nrhs, int* err, cudaStream_t s) {
   const size_t smem = 2 * 36 * 256 * sizeof(TG) + sizeof(float4) * (12 * 256 + 16) + 16;
@@ -419,8 +420,9 @@ int launch_sap_colour_pair(int prec, const Geom& g, void* z, const void* b, cons
   if (shape >= 3 && !err) return MG_ERR_ARG;
   if (nrhs < 2 || nrhs % 2 != 0 || n_mr < 1) return MG_ERR_ARG;
 #define SAPMG_PAIR_CASE(T)                                                                   \
-  return shape == 4 ? run_block<T, true>(g, z, b, U, A, colour, n_mr, nrhs, err, s)          \
-       : shape == 3 ? run_block<T, false>(g, z, b, U, A, colour, n_mr, nrhs, err, s)         \
+  return shape == 5 ? run_block<T, 2>(g, z, b, U, A, colour, n_mr, nrhs, err, s)             \
+       : shape == 4 ? run_block<T, 1>(g, z, b, U, A, colour, n_mr, nrhs, err, s)             \
+       : shape == 3 ? run_block<T, 0>(g, z, b, U, A, colour, n_mr, nrhs, err, s)             \
        : shape == 2 ? run_pair<T, true, 1>(g, z, b, U, A, colour, n_mr, nrhs, s)             \
        : shape == 1 ? run_pair<T, true, 2>(g, z, b, U, A, colour, n_mr, nrhs, s)             \
                     : run_pair<T, false, 2>(g, z, b, U, A, colour, n_mr, nrhs, s)

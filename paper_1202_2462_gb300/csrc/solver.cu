@@ -150,6 +150,10 @@ struct mg_ctx {
   int dirac_pair = 1;     // paired Dirac kernel for an even number of FP32-arithmetic RHS (SAPMG_DIRAC_PAIR=0: off)
   int xfer_batch = 16;    // right-hand sides per level-0 transfer launch (autotuned)
   CoarseTune ctune;       // launch shape of the FP16 tensor-core coarse stencil (autotuned)
+  // residual history of the last mg_solve: (iteration, right-hand side, relative residual) triples;
+  // the cycles add their least-squares estimates times hist_scale[q] at hist_base + step
+  std::vector<double> hist, hist_scale;
+  int hist_base = 0, hist_r0 = 0;
   int tune_source = 0;    // 0: default launch shapes, 1: chosen by the autotuner, 2: taken from its cache
   int restrict_tf32 = 1;  // tensor-core (TF32) multi-RHS level-0 transfers in the mixed form (SAPMG_RESTRICT_TF32=0 disables)
   int coarse_fp16 = 1;    // FP16-stored operator for the tensor-core coarse stencil (SAPMG_COARSE_FP16=0: FP32)
@@ -479,6 +483,15 @@ static int cycle(mg_ctx* c, const void* v, void* z, int R) {
   return smoother_sweeps(c, v, z, c->p.nu_post, R);
 }
 
+// One entry of the residual history: the least-squares residual estimate of a
+// cycle's system q scaled to ||b - D x|| / ||b|| of the solve's system.
+static void record_history(mg_ctx* c, int q, int iteration, double est) {
+  if (q >= (int)c->hist_scale.size()) return;
+  c->hist.push_back((double)iteration);
+  c->hist.push_back((double)(c->hist_r0 + q));
+  c->hist.push_back(est * c->hist_scale[q]);
+}
+
 // Least squares min || g0 e1 - H y || for the (n+1) x n upper Hessenberg H
 // (column-major, leading dimension ld) by Givens rotations applied from
 // scratch; returns the residual norm and, if y != nullptr, the solution.
@@ -594,6 +607,7 @@ static int fgmres_cycle_dcgs2(mg_ctx* c, int ft, int aprec, int R, const void* r
       Hq(q, j + 1, j) = hn;
       done[q] = j + 1;
       est[q] = hessenberg_lsq(&Hq(q, 0, 0), lh, j + 1, rnorm[q], nullptr);
+      record_history(c, q, c->hist_base + j + 1, est[q]);
       if (est[q] <= abs_tol[q] || hn == 0.0 || ac[j].x == 0.0) { active[q] = 0; continue; }
       a.v[q].x = 1.0 / hn;
       ++n_active;
@@ -714,6 +728,7 @@ static int fgmres_cycle(mg_ctx* c, int ft, int aprec, int R, const void* r, cons
       gq[j] = csq[j] * gq[j];
       done[q] = j + 1;
       est[q] = std::abs(gq[j + 1]);
+      record_history(c, q, c->hist_base + j + 1, est[q]);
       if (est[q] <= abs_tol[q] || hq == 0.0) { active[q] = 0; continue; }
       a.v[q].x = 1.0 / hq;
       ++n_active;
@@ -782,14 +797,26 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
       relres = std::max(relres, rel);
       if (rn[q] > tol[q]) all = false;
     }
+    // the FP64 residual of every system at this restart / defect correction (entries
+    // with a negative iteration mark the recomputed residuals)
+    for (int q = 0; q < R; ++q) {
+      c->hist.push_back(-(double)iters - 1.0);
+      c->hist.push_back((double)(c->hist_r0 + q));
+      c->hist.push_back(bn[q] > 0 ? rn[q] / bn[q] : 0.0);
+    }
     if (c->p.verbose) std::fprintf(stderr, "[sapmg] outer %d iters %d max relres %.3e\n", restarts, iters, relres);
     if (all) return MG_OK;
     if (iters >= c->p.maxiter) return MG_NOT_CONVERGED;
     std::vector<double> act(R);
     for (int q = 0; q < R; ++q) act[q] = rn[q] > tol[q] ? rn[q] : 0.0;
+    c->hist_base = iters;
+    c->hist_scale.assign(R, 0.0);
     if (c->prec == P64) {
+      for (int q = 0; q < R; ++q) c->hist_scale[q] = bn[q] > 0 ? 1.0 / bn[q] : 0.0;
       TRY(fgmres_cycle(c, P64, P64, R, c->r64, act, c->x64, tol, c->p.maxiter - iters, done, est));
     } else {
+      // the inner systems D e = r / ||r|| scale back by ||r|| / ||b||
+      for (int q = 0; q < R; ++q) c->hist_scale[q] = bn[q] > 0 ? act[q] / bn[q] : 0.0;
       // FP64 defect correction: flexible GMRES in FP32 on D e = t, t = the
       // normalised residual, restarted on its own FP32 residual t - D e until
       // that is below the inner tolerance (or no longer falls), then x and r
@@ -813,6 +840,7 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
           any = any || aim[q] > 0;
         }
         if (!any || iters + step >= c->p.maxiter) break;
+        c->hist_base = iters + step;
         TRY(fgmres_cycle(c, P32, P32, R, rcur, aim, c->e32, inner, c->p.maxiter - iters - step, done, est));
         int cs = 0;
         for (int q = 0; q < R; ++q) cs = std::max(cs, done[q]);
@@ -1955,8 +1983,10 @@ int mg_solve(mg_ctx* c, const double* b, double* z, int nrhs, mg_solve_info* inf
   const size_t n = c->fine_n();
   int status = MG_OK, it_sum = 0, rs_sum = 0;
   double worst = 0;
+  c->hist.clear();
   for (int r0 = 0; r0 < nrhs; r0 += c->p.nrhs_max) {
     const int R = std::min(c->p.nrhs_max, nrhs - r0);
+    c->hist_r0 = r0;
     TRY(launch_pack_spinor(P64, b + (size_t)r0 * n * 2, P64, c->b64, c->g, R, c->s));
     int it = 0, rs = 0;
     double rel = 0;
@@ -1990,8 +2020,10 @@ int mg_cgn_solve(mg_ctx* c, const double* b, double* z, int nrhs, int prec, doub
   const size_t n = c->fine_n();
   int status = MG_OK, it_sum = 0, up_sum = 0;
   double worst = 0;
+  c->hist.clear();
   for (int r0 = 0; r0 < nrhs; r0 += c->p.nrhs_max) {
     const int R = std::min(c->p.nrhs_max, nrhs - r0);
+    c->hist_r0 = r0;
     TRY(launch_pack_spinor(P64, b + (size_t)r0 * n * 2, P64, c->b64, c->g, R, c->s));
     int it = 0, up = 0;
     double rel = 0;
@@ -2314,6 +2346,13 @@ int mg_get_tuning(mg_ctx* c, int* out) {
   out[4] = c->ctune.ctas;
   out[5] = c->ctune.batch;
   return MG_OK;
+}
+
+int mg_get_history(mg_ctx* c, double* out, int max_entries) {
+  if (!c || max_entries < 0) return fail(MG_ERR_ARG, "bad argument");
+  const int n = (int)(c->hist.size() / 3);
+  if (out) std::memcpy(out, c->hist.data(), sizeof(double) * 3 * (size_t)std::min(n, max_entries));
+  return n;
 }
 
 int mg_sync(mg_ctx* c) {

@@ -90,6 +90,22 @@ class Solver:
         code, info = B.mg_cgn_solve(self.ctx, b, z, nrhs, prec, tol, maxiter)
         return z, info, code
 
+    def history(self):
+        """The last solve's residual history (mg_get_history) per right-hand side:
+        {rhs: {"estimates": [(iteration, relres)], "fp64": [(iteration, relres)],
+        "rho": the average residual reduction per iteration, (final relres)^(1/iterations)}}."""
+        out = {}
+        for it, q, r in B.mg_get_history(self.ctx):
+            d = out.setdefault(q, {"estimates": [], "fp64": []})
+            if it > 0:
+                d["estimates"].append((it, r))
+            else:
+                d["fp64"].append((-it - 1, r))
+        for d in out.values():
+            k, r = d["fp64"][-1] if d["fp64"] else (0, 1.0)
+            d["rho"] = r ** (1.0 / k) if k > 0 and r > 0 else None
+        return out
+
     def save(self, path):
         """Write the set-up's test vectors to `path` (mg_save)."""
         B.mg_save(self.ctx, path)

@@ -42,7 +42,7 @@ def test_tuned_and_cached_contexts_match_the_default_bit_for_bit(base):
     torch, G, u, b, z0, its0 = base
     z1, its1, t1 = _solve(torch, G, u, b, autotune=1)
     assert t1["source"] in ("tuned", "cached")
-    assert 0 <= t1["sap_shape"] <= 4 and t1["coarse_stages"] in (2, 3) and 1 <= t1["coarse_batch"] <= 16
+    assert 0 <= t1["sap_shape"] <= 5 and t1["coarse_stages"] in (2, 3) and 1 <= t1["coarse_batch"] <= 16
     assert torch.equal(z1, z0) and its1 == its0
     z2, its2, t2 = _solve(torch, G, u, b, autotune=1)      # same key: the cached choice
     assert t2["source"] == "cached" and {k: v for k, v in t2.items() if k != "source"} == \
@@ -51,7 +51,7 @@ def test_tuned_and_cached_contexts_match_the_default_bit_for_bit(base):
 
 
 @pytest.mark.parametrize("env", [
-    {"SAPMG_SAP_SHAPE": "1"}, {"SAPMG_SAP_SHAPE": "2"}, {"SAPMG_SAP_SHAPE": "3"}, {"SAPMG_SAP_SHAPE": "4"},
+    {"SAPMG_SAP_SHAPE": "1"}, {"SAPMG_SAP_SHAPE": "2"}, {"SAPMG_SAP_SHAPE": "3"}, {"SAPMG_SAP_SHAPE": "4"}, {"SAPMG_SAP_SHAPE": "5"},
     {"SAPMG_XFER_BATCH": "4"}, {"SAPMG_XFER_BATCH": "8"}, {"SAPMG_XFER_BATCH": "6"},
     {"SAPMG_COARSE_TUNE": "4,3,8"}, {"SAPMG_COARSE_TUNE": "8,2,4"}, {"SAPMG_COARSE_TUNE": "16,3,0"},
 ])

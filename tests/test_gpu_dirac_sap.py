@@ -170,7 +170,7 @@ def test_sap_multi_rhs_matches_single(prec):
     s.close()
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("prec,n_mr", [("fp32", 4), ("fp16", 1), ("bf16", 4), ("bf16", 2)])
 def test_sap_pair_kernel_parity(prec, n_mr, shape, monkeypatch):
     """The paired Schwarz kernel (two right-hand sides per thread, packed
@@ -258,7 +258,7 @@ def test_dirac_pair_kernel_matches_single_kernel(monkeypatch):
     assert np.max(np.abs(outs[0] - outs[1])) / np.max(np.abs(outs[1])) < 2e-6
 
 
-@pytest.mark.parametrize("shape", [0, 3])
+@pytest.mark.parametrize("shape", [0, 3, 5])
 def test_sap_pair_kernel_tiny_blocks_stay_finite(shape, monkeypatch):
     """Blocks whose residual is ~1e-21 make <p, p> a denormal FP32 number: the
     MR coefficient must still be finite (alpha by division; a reciprocal of

@@ -438,3 +438,31 @@ def test_coarse_stencil_tensor_core_parity(tf32, fp16, monkeypatch):
         ref = c.apply(rnd_x(x[:nr].astype(np.complex128))).reshape(nr, 16, 16)
         assert rel(host(out), ref) < 5e-6, nr
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_solve_residual_history(field, prec):
+    """mg_get_history: for every right-hand side the FP64-recomputed residuals
+    end below the tolerance at the reported iteration count and match the
+    solve's final relres (the systems run in lockstep, so the count is the
+    batch's); each system's least-squares estimates start at iteration 1 and
+    stop at or before it."""
+    torch = torch_cuda()
+    u, op = field
+    s = _solver(torch, u, n_levels=2, n_vec=(8,), precision=prec, nrhs_max=2, seed=3)
+    b = dev(torch, synth.random_spinor(DIMS, 43, nvec=2))
+    z, info, code = s.solve(b)
+    h = s.history()
+    s.close()
+    assert code == 0 and sorted(h) == [0, 1]
+    total = 0
+    worst = 0.0
+    for q, d in h.items():
+        k, r = d["fp64"][-1]
+        assert r <= 1e-10
+        worst = max(worst, r)
+        total += k
+        its = [it for it, _ in d["estimates"]]
+        assert its and max(its) <= k and min(its) == 1
+        assert 0 < d["rho"] < 1
+    assert total == info.iterations and abs(worst - info.relres) <= 1e-12
