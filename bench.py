@@ -37,14 +37,15 @@ import synth  # noqa: E402
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # FP32 FMA lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 1.25                                # GB300 FP64 (nominal)
 # DRAM bytes per (site of the colour, right-hand side) of one BF16 Schwarz colour pass,
-# from ncu captures of the 16^3x32 lattice with 12 right-hand sides (traffic grows with
-# the units), per launch shape of the paired kernels: shape 0 (sap_colour_pair_kernel)
-# and shape 3 (sap_block_kernel); none for the other shapes
+# from ncu captures with 12 right-hand sides (traffic grows with the units), per
+# launch shape of the paired kernels: shapes 0 (sap_colour_pair_kernel) and 3
+# (sap_block_kernel) on the 16^3x32 lattice, shape 5 on 32^3x32; none for the others
 SAP_DRAM_BYTES_PER_UNIT = {0: (266.179328e6 + 66.372352e6) / (65536 * 12),
-                           3: (263.003904e6 + 52.152320e6) / (65536 * 12)}
+                           3: (263.003904e6 + 52.152320e6) / (65536 * 12),
+                           5: (2440.573e6 + 584.692736e6) / (524288 * 12)}
 SAP_KERNEL = {-1: "sap_colour_kernel", 0: "sap_colour_pair_kernel", 1: "sap_colour_pair_kernel",
               2: "sap_colour_pair_kernel", 3: "sap_block_kernel", 4: "sap_block_kernel",
-              5: "sap_block_kernel"}
+              5: "sap_block_kernel", 6: "sap_split_kernel"}
 
 
 def flops_dirac_site():
@@ -77,7 +78,7 @@ def bytes_dirac_site(prec):
 
 # the kernels behind each timed family (a family call may issue several launches)
 FAMILY_KERNELS = {
-    "dirac": "dirac_pair_kernel + dirac_kernel", "sap": "sap_colour_pair_kernel + sap_block_kernel",
+    "dirac": "dirac_pair_kernel + dirac_kernel", "sap": "sap_colour_pair_kernel + sap_block_kernel + sap_split_kernel",
     "coarse": "coarse_apply_mma16_kernel",
     "restrict": "restrict0_mma_kernel", "prolong": "prolong0_mma_kernel",
     "blas": "dots2h_partial + dcgs2_coeff_kernel + axpy2h_kernel (outer Arnoldi, FP16 basis)",
@@ -174,7 +175,7 @@ def solver_kwargs(wl, precision, nrhs):
     return dict(n_levels=wl["n_levels"], n_vec=tuple(wl["n_vec"]), setup_iters=wl["setup_iters"],
                 n_mr=wl["n_mr"], nu_post=wl["nu_post"], coarse_iters=wl["coarse_iters"],
                 fgmres_m=wl["fgmres_m"], tol=wl["tol"], maxiter=wl.get("maxiter", 500),
-                precision=precision, nrhs_max=nrhs, seed=wl.get("vec_seed", 1),
+                precision=precision, nrhs_max=min(nrhs, wl.get("nrhs_max", nrhs)), seed=wl.get("vec_seed", 1),
                 autotune=int(precision != "fp64"))
 
 
@@ -409,6 +410,27 @@ def wl_config(wl, name, precision):
 
 
 # ----------------------------------------------------------------------------- our arm
+def learned_init(wl, u):
+    """Initial test vectors for workloads with init='learned': the gauge-
+    covariant network trained on seeded 16^4 fields of the workload's eps at
+    its bare mass (the library's training kernels), then BF16 inference on the
+    workload's field from seeded device noise.  Returns (vectors as complex128
+    on the device, a record of the training and inference)."""
+    import torch
+    from paper_1202_2462_gb300 import learned
+    net, losses, t_train = learned.train(wl["c_sw"], wl["m0"], eps_train=wl["eps"])
+    g = torch.Generator(device="cuda")
+    g.manual_seed(wl.get("vec_seed", 1))
+    noise = torch.randn((wl["n_vec"][0],) + tuple(u.shape[:4]) + (4, 3), dtype=torch.complex64, device="cuda",
+                        generator=g)
+    prop, t_infer = learned.infer(net, u, wl["c_sw"], wl["m0"], noise)
+    del noise
+    torch.cuda.empty_cache()
+    return prop, {"train_s": t_train, "inference_s": t_infer, "inference": "bf16",
+                  "train_fields": 20, "train_lattice": [16, 16, 16, 16], "train_eps": wl["eps"],
+                  "train_loss_first": float(sum(losses[:8]) / 8), "train_loss_last": float(sum(losses[-8:]) / 8)}
+
+
 def run_ours(a, wl):
     import torch
     import paper_1202_2462_gb300 as G
@@ -425,18 +447,23 @@ def run_ours(a, wl):
     gen_s = time.perf_counter() - t0
     nrhs = rhs_h.shape[0]
     u = torch.from_numpy(u_h).cuda()
-    b = torch.from_numpy(rhs_h).cuda()
-    b_pinned = torch.from_numpy(rhs_h).pin_memory()
-    z_pinned = torch.empty_like(b_pinned).pin_memory()
     stream = torch.cuda.current_stream()
+    init, learned = None, None
+    if wl.get("init") == "learned":
+        init, learned = learned_init(wl, u)
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s = G.Solver(u, wl["c_sw"], wl["m0"], **solver_kwargs(wl, prec, nrhs))
+    s = G.Solver(u, wl["c_sw"], wl["m0"], init_vectors=init, **solver_kwargs(wl, prec, nrhs))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     tuning = G.mg_get_tuning(s.ctx)
-    del u
+    del u, init
+    torch.cuda.empty_cache()
+    # the right-hand sides reach the device after the set-up, whose peak they would raise
+    b = torch.from_numpy(rhs_h).cuda()
+    b_pinned = torch.from_numpy(rhs_h).pin_memory()
+    z_pinned = torch.empty_like(b_pinned).pin_memory()
 
     # warm-up steps, profiled per kernel family to find the dominant one
     G.mg_set_profiling(s.ctx, 1)
@@ -497,6 +524,8 @@ def run_ours(a, wl):
     ms = max_over_ranks(ms, world, "cuda")
 
     # end to end through the public API with host buffers
+    del z
+    torch.cuda.empty_cache()
     e2e_steps = max(1, min(a.steps, 2))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -541,9 +570,9 @@ def run_ours(a, wl):
         roof = {"kernel": SAP_KERNEL[shape], "bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS if tflops else None,
                 "traffic": per_unit * units if per_unit else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one colour pass of the "
-                                  "16^3x32 12-RHS case with this launch shape, per site and RHS, scaled to this "
-                                  "launch's units",
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one colour pass of a "
+                                  "12-RHS case with this launch shape (16^3x32, or 32^3x32 for shape 5), per site "
+                                  "and RHS, scaled to this launch's units",
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "peak_probe": probe,
                 "hbm_gbs": alg_bytes / avg_s / 1e9 if n_prof else None,
@@ -572,6 +601,10 @@ def run_ours(a, wl):
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(b_pinned.numel() * 16),
                 "d2h_bytes_per_step": int(z_pinned.numel() * 16)},
     }
+    if learned:
+        line["learned_setup"] = learned
+    if wl.get("nrhs_max", nrhs) < nrhs:
+        line["config"]["rhs_batch"] = wl["nrhs_max"]
     if a.fp64_form and rank == 0:
         line["fp64_form"] = fp64_form(a, wl, u_h, rhs_h)
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -632,8 +665,6 @@ def run_cgn(a, wl):
     import torch
     import paper_1202_2462_gb300 as G
     torch.cuda.set_device(0)
-    if a.m0 is not None:
-        wl["m0"] = a.m0
     dims = tuple(wl["dims"])
     prec = a.precision or wl["precision"]
     u_h = synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"])
@@ -769,11 +800,13 @@ def main():
     ap.add_argument("--cgn", action="store_true",
                     help="instead of the bench line: the multilevel solve against CG on the normal equations")
     ap.add_argument("--cgn-fp64", action="store_true", help="with --cgn: also CGN in FP64 on one right-hand side")
-    ap.add_argument("--m0", type=float, default=None, help="with --cgn: bare mass instead of the workload's")
+    ap.add_argument("--m0", type=float, default=None, help="bare mass instead of the workload's")
     ap.add_argument("--sigma", action="store_true",
                     help="with --cgn: also sigma_min(D) by inverse iteration (16 solves of one right-hand side)")
     a = ap.parse_args()
     wl = synth.workload(a.workload)
+    if a.m0 is not None:
+        wl["m0"] = a.m0
     if a.oracle_study:
         return oracle_study(a)
     if a.kernel:

@@ -134,27 +134,21 @@ class GaugeNet:
         return torch.stack(outs)
 
 
-def study(train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5, eval_workload="32^3x64", n_vec=24,
-          sweeps=2, channels=16, layers=3, epochs=4, lr=1e-2, setup_iters=(1, 2, 4, 8), seed=1000):
-    """Train on seeded fields (noise -> bootstrap-smoothed noise, FP32), propose
-    the evaluation lattice's test vectors (BF16 inference), and compare
-    hierarchies built from the proposals and from plain noise, each refined by
-    the same number of bootstrap sweeps: set-up time (with the inference time
-    for the network), outer iterations per right-hand side of the 12
-    point-source solve, and the average residual reduction per outer
-    iteration rho = relres^(1 / iterations).  Returns a dict; 'equal_time'
-    pairs each network row with the noise row whose set-up took at least as
-    long."""
+def train(c_sw, m0, train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5, sweeps=2, channels=16,
+          layers=3, epochs=4, lr=1e-2, seed=1000):
+    """Train a GaugeNet on seeded fields U = exp(i eps_train H) of train_dims
+    (four noise fields each, `epochs` passes): input noise, target the
+    bootstrap-smoothed noise at (c_sw, m0).  Returns (net, losses, seconds of
+    training on the device)."""
     import time
     import synth
     from .solver import Solver
-    wl = synth.workload(eval_workload)
     net = GaugeNet(channels=channels, layers=layers, seed=seed)
     losses = []
     t_train = 0.0
     for f in range(train_fields):
         u = torch.from_numpy(synth.random_gauge_field(train_dims, eps_train, seed + f)).cuda()
-        s = Solver(u, wl["c_sw"], wl["m0"], n_levels=1, precision="fp32", fgmres_m=2)
+        s = Solver(u, c_sw, m0, n_levels=1, precision="fp32", fgmres_m=2)
         eta = torch.from_numpy(synth.random_spinor(train_dims, seed + 100 + f, nvec=4)).to(torch.complex64).cuda()
         inputs = [GaugeNet.blocked(s, eta[k]) for k in range(4)]
         targets = [GaugeNet.blocked(s, GaugeNet.smoothed(s, eta[k], sweeps)) for k in range(4)]
@@ -169,18 +163,52 @@ def study(train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5, eval_work
         torch.cuda.synchronize()
         t_train += time.perf_counter() - t0
         s.close()
-    dims = tuple(wl["dims"])
-    u = torch.from_numpy(synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"])).cuda()
-    noise = torch.from_numpy(synth.test_vector_draw(dims, n_vec, seed + 7)).to(torch.complex64).cuda()
-    s = Solver(u, wl["c_sw"], wl["m0"], n_levels=1, precision="bf16", fgmres_m=2)
+    return net, losses, t_train
+
+
+def infer(net, u, c_sw, m0, noise):
+    """BF16 inference of the network's proposals for the noise fields (N, ...)
+    on the gauge field u (device, canonical); returns (proposals as complex128,
+    the layout mg_params.init_vectors takes, and seconds).  One field at a
+    time, written straight into the output.  Raises if a proposal is not
+    finite."""
+    import time
+    from .solver import Solver
+    s = Solver(u, c_sw, m0, n_levels=1, precision="bf16", fgmres_m=2)
+    out = torch.empty(noise.shape, dtype=torch.complex128, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    prop = net.propose(s, noise, bf16=True)
+    for k in range(noise.shape[0]):
+        out[k] = net.propose(s, noise[k:k + 1].to(torch.complex64), bf16=True)[0]
     torch.cuda.synchronize()
     t_infer = time.perf_counter() - t0
     s.close()
-    if not bool(torch.isfinite(torch.view_as_real(prop)).all()):
+    if not bool(torch.isfinite(torch.view_as_real(out)).all()):
         raise RuntimeError("the network's proposals are not finite")
+    return out, t_infer
+
+
+def study(train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5, eval_workload="32^3x64", n_vec=24,
+          sweeps=2, channels=16, layers=3, epochs=4, lr=1e-2, setup_iters=(1, 2, 4, 8, 20), seed=1000):
+    """Train on seeded fields (noise -> bootstrap-smoothed noise, FP32), propose
+    the evaluation lattice's test vectors (BF16 inference), and compare
+    hierarchies built from the proposals and from plain noise, each refined by
+    the same number of bootstrap sweeps: set-up time (with the inference time
+    for the network), outer iterations per right-hand side of the 12
+    point-source solve, and the average residual reduction per outer
+    iteration rho = relres^(1 / iterations).  Returns a dict; 'equal_time'
+    pairs each network row with the noise row whose set-up took at least as
+    long."""
+    import time
+    import synth
+    from .solver import Solver
+    wl = synth.workload(eval_workload)
+    net, losses, t_train = train(wl["c_sw"], wl["m0"], train_dims, train_fields, eps_train, sweeps, channels,
+                                 layers, epochs, lr, seed)
+    dims = tuple(wl["dims"])
+    u = torch.from_numpy(synth.random_gauge_field(dims, wl["eps"], wl["gauge_seed"])).cuda()
+    noise = torch.from_numpy(synth.test_vector_draw(dims, n_vec, seed + 7)).cuda()
+    prop, t_infer = infer(net, u, wl["c_sw"], wl["m0"], noise)
     import numpy as np
     b = torch.from_numpy(np.ascontiguousarray(synth.point_sources(dims))).cuda()
     rows = []
@@ -190,8 +218,7 @@ def study(train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5, eval_work
             t0 = time.perf_counter()
             sol = Solver(u, wl["c_sw"], wl["m0"], n_levels=2, n_vec=(n_vec,), setup_iters=k, n_mr=wl["n_mr"],
                          nu_post=wl["nu_post"], coarse_iters=wl["coarse_iters"], fgmres_m=wl["fgmres_m"],
-                         precision=wl["precision"], nrhs_max=12, init_vectors=iv.to(torch.complex128).contiguous(),
-                         maxiter=2000)
+                         precision=wl["precision"], nrhs_max=12, init_vectors=iv, maxiter=2000)
             torch.cuda.synchronize()
             ts = time.perf_counter() - t0 + (t_infer if name == "network" else 0.0)
             t0 = time.perf_counter()
