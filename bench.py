@@ -83,6 +83,7 @@ FAMILY_KERNELS = {
     "restrict": "restrict0_mma_kernel", "prolong": "prolong0_mma_kernel",
     "blas": "dots2h_partial + dcgs2_coeff_kernel + axpy2h_kernel (outer Arnoldi, FP16 basis)",
     "coarse_blas": "multidot_h_partial + multiaxpy_h_kernel + normalize_h_kernel + hessenberg_solve_kernel",
+    "sap1": "coarse_sap_mrhs_kernel (level-1 Schwarz of three levels)",
 }
 
 
@@ -460,6 +461,7 @@ def run_ours(a, wl):
     tuning = G.mg_get_tuning(s.ctx)
     del u, init
     torch.cuda.empty_cache()
+    free_b, total_b = torch.cuda.mem_get_info()
     # the right-hand sides reach the device after the set-up, whose peak they would raise
     b = torch.from_numpy(rhs_h).cuda()
     b_pinned = torch.from_numpy(rhs_h).pin_memory()
@@ -601,6 +603,7 @@ def run_ours(a, wl):
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(b_pinned.numel() * 16),
                 "d2h_bytes_per_step": int(z_pinned.numel() * 16)},
     }
+    line["device_memory_gb"] = {"in_use_after_setup": (total_b - free_b) / 1e9, "total": total_b / 1e9}
     if learned:
         line["learned_setup"] = learned
     if wl.get("nrhs_max", nrhs) < nrhs:

@@ -99,6 +99,9 @@ typedef struct {
                                launch shapes of the mixed form's multi-RHS
                                kernels for nrhs_max right-hand sides and keep
                                the fastest (see mg_get_tuning); 0 = defaults */
+  int init_vectors_prec;    /* type of init_vectors: MG_FP64 (complex128,
+                               the default) or MG_FP32 (complex64, half the
+                               caller's memory; widened to FP64 on entry) */
 } mg_params;
 
 typedef struct {
@@ -332,7 +335,8 @@ int mg_adam_step(mg_ctx* ctx, size_t n, float* p, const float* g, float* m, floa
  * around every launch of the selected kernel families.  mask: 0 = off, 1 = all
  * families, otherwise bit (f + 1) selects family f (0 dirac, 1 Schwarz colour
  * pass, 2 coarse apply, 3 restrict, 4 prolong, 5 fine-level vector kernels
- * of the outer solver, 6 vector kernels of the coarse-level solves).  mg_get_profile
+ * of the outer solver, 6 vector kernels of the coarse-level solves, 7 the
+ * level-1 Schwarz colour pass of a three-level hierarchy).  mg_get_profile
  * returns a family's timed launch count and summed milliseconds (it
  * synchronises on the pending events). */
 int mg_set_profiling(mg_ctx* ctx, int mask);
@@ -341,8 +345,10 @@ int mg_get_profile(mg_ctx* ctx, int family, long long* launches, double* ms);
  * operand read once and every result written once: fields in storage
  * precision, the right-hand sides' vectors, P, the coarse operator), summed
  * like mg_get_profile's milliseconds; their ratio is the family's achieved
- * bandwidth.  The level-1 Schwarz sweeps and transfers of a three-level
- * hierarchy add no bytes. */
+ * bandwidth.  The level-1 Schwarz passes count their operator reads (every
+ * MR step reads the box's operator; once for all right-hand sides in the
+ * multi-RHS form, once per right-hand side otherwise); the level-1 transfers
+ * add no bytes. */
 int mg_get_profile_bytes(mg_ctx* ctx, int family, double* bytes);
 int mg_reset_profile(mg_ctx* ctx);
 
@@ -356,10 +362,13 @@ long long mg_launch_count(void);
  * per SM, rho re-read for the update; 1: rho in registers; 2: one CTA per SM;
  * 3: one CTA per block with the block's fields in shared memory, every pair
  * of right-hand sides in turn; 4, 5: shape 3 with the x, y, z (4) or all (5)
- * hops computed without branches), out[2] = right-hand sides per transfer
- * launch, out[3] = ring depth, out[4] = CTA-per-SM cap (0: none) and out[5] =
- * right-hand sides per launch of the FP16 tensor-core coarse stencil.  Every
- * choice computes the same results bit for bit; only the time differs. */
+ * hops computed without branches; 6: shape 5 with two threads per site, each
+ * one chirality and two directions, FP16/BF16 fields only), out[2] =
+ * right-hand sides per transfer launch, out[3] = ring depth, out[4] =
+ * CTA-per-SM cap (0: none) and out[5] = right-hand sides per launch of the
+ * FP16 tensor-core coarse stencil.  Every choice computes the same results bit
+ * for bit, except Schwarz shape 6, which adds a site's hops in another order
+ * (the results agree to FP32 rounding); only the time differs. */
 int mg_get_tuning(mg_ctx* ctx, int* out);
 
 /* Residual history of the context's last mg_solve (no paper counterpart;

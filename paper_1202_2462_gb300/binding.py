@@ -56,6 +56,7 @@ class MgParams(ctypes.Structure):
         ("setup2_iters", ctypes.c_int),
         ("setup2_start", ctypes.c_void_p),
         ("autotune", ctypes.c_int),
+        ("init_vectors_prec", ctypes.c_int),
     ]
 
 
@@ -391,4 +392,5 @@ def profile_mask(*families):
     return m
 
 
-PROFILE_FAMILIES = {"dirac": 0, "sap": 1, "coarse": 2, "restrict": 3, "prolong": 4, "blas": 5, "coarse_blas": 6}
+PROFILE_FAMILIES = {"dirac": 0, "sap": 1, "coarse": 2, "restrict": 3, "prolong": 4, "blas": 5, "coarse_blas": 6,
+                    "sap1": 7}

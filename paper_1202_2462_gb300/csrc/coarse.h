@@ -63,6 +63,11 @@ int launch_coarse_apply_mma(const CGeom& c, int store, const void* M, const void
                             bool x_half, cudaStream_t s, const CoarseTune& t = CoarseTune());
 
 // Intermediate level of a three-level hierarchy (coarse1.cu).
+// The colour pass of launch_coarse_sap for 1 <= nrhs <= 12 right-hand sides in one
+// CTA per box (FP32 operator and vectors; each operator entry loaded once for all
+// of them); bit for bit the one-RHS-per-CTA results.
+int launch_coarse_sap_mrhs(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
+                           int n_mr, int nrhs, cudaStream_t s);
 int launch_coarse_sap(int prec, const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
                       int n_mr, int nrhs, cudaStream_t s);
 int launch_transfer1(bool restrict_, int prec, const CGeom& c, const Box4& ag, const void* in, void* out,

@@ -55,6 +55,33 @@ __device__ __forceinline__ int stencil_nb(const CGeom& c, int site, int d) {
   return site + (((x + step + c.L[mu]) % c.L[mu]) - x) * stride;
 }
 
+// The MR step's scalar products and updates with every product and sum rounded
+// on its own (no contraction into FMAs), so that the one-RHS and all-RHS forms
+// of the coarse Schwarz pass give the same bits whatever the compiler fuses.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+// (re <p, rho>, im <p, rho>, <p, p>) of one element
+template <class R>
+__device__ __forceinline__ void mr_dots(const Cplx<R>& p, const Cplx<R>& ro, R (&v)[3]) {
+  v[0] = add_rn(mul_rn(p.re, ro.re), mul_rn(p.im, ro.im));
+  v[1] = sub_rn(mul_rn(p.re, ro.im), mul_rn(p.im, ro.re));
+  v[2] = add_rn(mul_rn(p.re, p.re), mul_rn(p.im, p.im));
+}
+// e += alpha rho, rho -= alpha p
+template <class R>
+__device__ __forceinline__ void mr_update(const Cplx<R>& alpha, const Cplx<R>& p, Cplx<R>& e, Cplx<R>& ro) {
+  const R ar = sub_rn(mul_rn(alpha.re, ro.re), mul_rn(alpha.im, ro.im));
+  const R ai = add_rn(mul_rn(alpha.re, ro.im), mul_rn(alpha.im, ro.re));
+  const R pr = sub_rn(mul_rn(alpha.re, p.re), mul_rn(alpha.im, p.im));
+  const R pi = add_rn(mul_rn(alpha.re, p.im), mul_rn(alpha.im, p.re));
+  e = cmk(add_rn(e.re, ar), add_rn(e.im, ai));
+  ro = cmk(sub_rn(ro.re, pr), sub_rn(ro.im, pi));
+}
+
 template <class R>
 __device__ __forceinline__ void block_reduce_n(R (&v)[3], R (*red)[4]) {
   const int nw = (blockDim.x + 31) >> 5;
@@ -124,18 +151,16 @@ __global__ void __launch_bounds__(1024) coarse_sap_kernel(const TM* __restrict__
         const Cplx<R>* rn = rs + ln * n2;
         for (int j = 0; j < n2; ++j) cfma(p, Io<R, TM>::ld(m + (size_t)j * n2), rn[j]);
       }
-      const Cplx<R> ro = rs[tid];
-      v[0] = p.re * ro.re + p.im * ro.im;
-      v[1] = p.re * ro.im - p.im * ro.re;
-      v[2] = p.re * p.re + p.im * p.im;
+      mr_dots(p, rs[tid], v);
     }
     block_reduce_n(v, red);
     Cplx<R> alpha = cmk<R>(0, 0);
     if (v[2] > (R)0) alpha = cmk(v[0] / v[2], v[1] / v[2]);
     if (act) {
-      const Cplx<R> ro = rs[tid];
-      es[tid] = es[tid] + alpha * ro;
-      rs[tid] = ro - alpha * p;
+      Cplx<R> e = es[tid], ro = rs[tid];
+      mr_update(alpha, p, e, ro);
+      es[tid] = e;
+      rs[tid] = ro;
     }
     __syncthreads();                      // red reused by the next reduction
   }
@@ -160,6 +185,154 @@ static int coarse_sap_t(const CGeom& c, const Box4& bx, const void* M, void* z, 
       (const TM*)M, (TX*)z, (const TX*)b, c, bx, colour, n_mr, nrhs); count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
+}
+
+// The same colour pass for all right-hand sides in one CTA per box (FP32
+// operator and vectors): each operator entry is loaded once for every
+// right-hand side, where the one-RHS-per-CTA form above reads the box's
+// operator (16 sites x 9 x n2^2 entries) once per right-hand side and MR step
+// from memory.  Per right-hand side every sum runs in the order of the kernel
+// above (the same residual and MR sums, the same block reduction), so the two
+// give the same results bit for bit.  rho and e in shared memory as
+// [box site][n2][NR]; NR >= nrhs, a compile-time bound on the right-hand sides.
+template <int NR>
+__global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const float2* __restrict__ M, float2* __restrict__ z,
+                                                               const float2* __restrict__ b, CGeom c, Box4 bx,
+                                                               int colour, int n_mr, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n2 = c.n2, bs = bx.sites;
+  Cplx<float>* rs = reinterpret_cast<Cplx<float>*>(smem_raw);
+  Cplx<float>* es = rs + bs * n2 * NR;
+  float (*red)[3 * NR] = reinterpret_cast<float (*)[3 * NR]>(es + bs * n2 * NR);
+  int bc[4];
+  colour_box(bx, blockIdx.x, colour, bc);
+  const size_t fs = (size_t)c.nsites * n2;
+  const int tid = threadIdx.x;
+  const bool act = tid < bs * n2;
+  const int s = act ? tid / n2 : 0, i = act ? tid % n2 : 0;
+  int lc[4];
+  const int site = box_site(c, bx, bc, s, lc);
+  const int nw = (blockDim.x + 31) >> 5, w = tid >> 5, lane = tid & 31;
+
+  // residual of every right-hand side, four at a time (registers)
+  if (act) {
+#pragma unroll
+    for (int r0 = 0; r0 < NR; r0 += 4) {
+      Cplx<float> acc[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        acc[r] = r0 + r < nrhs ? Io<float, float2>::ldc(b + (r0 + r) * fs + (size_t)site * n2 + i) : cmk(0.f, 0.f);
+      for (int d = 0; d < 9; ++d) {
+        const size_t xo = (size_t)stencil_nb(c, site, d) * n2;
+        const float2* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
+        Cplx<float> t[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) t[r] = cmk(0.f, 0.f);
+        for (int j = 0; j < n2; ++j) {
+          const Cplx<float> mv = Io<float, float2>::ld(m + (size_t)j * n2);
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            if (r0 + r < nrhs) cfma(t[r], mv, Io<float, float2>::ldc(z + (r0 + r) * fs + xo + j));
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] = acc[r] - t[r];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (r0 + r < NR) {
+          rs[tid * NR + r0 + r] = acc[r];
+          es[tid * NR + r0 + r] = cmk(0.f, 0.f);
+        }
+    }
+  }
+  for (int it = 0; it < n_mr; ++it) {
+    __syncthreads();
+    Cplx<float> p[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) p[r] = cmk(0.f, 0.f);
+    if (act) {
+      for (int d = 0; d < 9; ++d) {
+        int ln = s;
+        if (d > 0) {
+          const int mu = (d - 1) >> 1, step = (d & 1) ? 1 : -1;
+          const int l2 = lc[mu] + step;
+          if (l2 < 0 || l2 >= bx.b[mu]) continue;                 // coupling leaves the box
+          int stride = 1;
+          for (int m = 0; m < mu; ++m) stride *= bx.b[m];
+          ln = s + step * stride;
+        }
+        const float2* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
+        const Cplx<float>* rn = rs + (size_t)ln * n2 * NR;
+        for (int j = 0; j < n2; ++j) {
+          const Cplx<float> mv = Io<float, float2>::ld(m + (size_t)j * n2);
+#pragma unroll
+          for (int r = 0; r < NR; ++r) cfma(p[r], mv, rn[j * NR + r]);
+        }
+      }
+    }
+    // block sums, per right-hand side as block_reduce_n forms them
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      float v[3] = {0.f, 0.f, 0.f};
+      if (act) mr_dots(p[r], rs[tid * NR + r], v);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[q] = warp_sum(v[q]);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) red[w][3 * r + q] = v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      float a0 = 0, a1 = 0, a2 = 0;
+      for (int k = 0; k < nw; ++k) { a0 += red[k][3 * r]; a1 += red[k][3 * r + 1]; a2 += red[k][3 * r + 2]; }
+      Cplx<float> alpha = cmk(0.f, 0.f);
+      if (a2 > 0.f) alpha = cmk(a0 / a2, a1 / a2);
+      if (act) {
+        Cplx<float> e = es[tid * NR + r], ro = rs[tid * NR + r];
+        mr_update(alpha, p[r], e, ro);
+        es[tid * NR + r] = e;
+        rs[tid * NR + r] = ro;
+      }
+    }
+    __syncthreads();                      // red reused by the next reduction
+  }
+  if (act)
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+      if (r < nrhs) {
+        float2* zq = z + r * fs + (size_t)site * n2 + i;
+        Io<float, float2>::st(zq, Io<float, float2>::ldc(zq) + es[tid * NR + r]);
+      }
+}
+
+template <int NR>
+static int coarse_sap_mrhs_t(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
+                             int n_mr, int nrhs, cudaStream_t s) {
+  const int threads = ((bx.sites * c.n2 + 31) / 32) * 32;
+  if (threads > 1024 || nrhs > NR) return MG_ERR_ARG;
+  const size_t smem = sizeof(Cplx<float>) * 2 * bx.sites * c.n2 * NR + sizeof(float) * 3 * NR * 32;
+  if (smem > 227 * 1024) return MG_ERR_ARG;
+  static bool attr = false;
+  if (!attr) {
+    SAPMG_CUDA_TRY(cudaFuncSetAttribute(coarse_sap_mrhs_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024));
+    attr = true;
+  }
+  coarse_sap_mrhs_kernel<NR><<<(unsigned)(bx.nboxes / 2), threads, smem, s>>>(
+      (const float2*)M, (float2*)z, (const float2*)b, c, bx, colour, n_mr, nrhs);
+  count_launches(1);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
+int launch_coarse_sap_mrhs(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
+                           int n_mr, int nrhs, cudaStream_t s) {
+  if (nrhs <= 2) return coarse_sap_mrhs_t<2>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+  if (nrhs <= 4) return coarse_sap_mrhs_t<4>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+  if (nrhs <= 8) return coarse_sap_mrhs_t<8>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+  if (nrhs <= 12) return coarse_sap_mrhs_t<12>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+  return MG_ERR_ARG;
 }
 
 int launch_coarse_sap(int prec, const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,

@@ -42,6 +42,7 @@ int launch_dirac_ex(int prec, const Geom& g, void* out, const void* in, const vo
 // setup2.cu: out = P phi with the FP64 vector-major test vectors v64 (N fine
 // fields, blocked layout) and an FP64 coarse vector phi [nblocks][2N]
 int launch_prolong_v64(const Geom& g, const void* v64, int N, const void* phi, void* out, cudaStream_t s);
+int launch_restrict_v64(const Geom& g, const void* v64, int N, const void* x, void* out, cudaStream_t s);
 
 // dense_eig.cu: host eigen-solvers of the set-up's second part (column-major
 // complex, re/im interleaved)
@@ -95,8 +96,11 @@ int launch_sap_colour(int prec, const Geom& g, void* z, const void* b, const voi
 // SM, rho kept in registers; 2: one CTA per SM, rho kept in registers; 3: one
 // CTA per block holding the block's fields in shared memory for every pair;
 // 4: shape 3 with the x, y, z hops of the MR steps computed without branches;
-// 5: all four directions without branches (err: the device flag a bounded
-// wait that gives up raises; needed by shapes 3-5).
+// 5: all four directions without branches; 6: shape 5 with two threads per
+// site (512 per CTA, each thread one chirality and two directions; FP16/BF16
+// fields only, MG_ERR_ARG for FP32 fields, whose copy would not fit in shared
+// memory) (err: the device flag a bounded wait that gives up raises; needed by
+// shapes 3-6).
 int launch_sap_colour_pair(int prec, const Geom& g, void* z, const void* b, const void* U, const void* A, int colour,
                            int n_mr, int nrhs, cudaStream_t s, int shape, int* err);
 // sap_shift.cu: the same pass for D - shift[r] (per right-hand side r; device

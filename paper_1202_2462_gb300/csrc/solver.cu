@@ -56,7 +56,7 @@ static int fail(int code, const std::string& m) {
 
 enum {
   FAM_DIRAC = 0, FAM_SAP = 1, FAM_COARSE = 2, FAM_RESTRICT = 3, FAM_PROLONG = 4, FAM_BLAS = 5, FAM_CBLAS = 6,
-  FAM_N = 7
+  FAM_SAP1 = 7, FAM_N = 8
 };
 
 struct Prof {
@@ -148,6 +148,12 @@ struct mg_ctx {
   int coarse_tf32 = 1;    // tensor-core (TF32) coarse stencil in the mixed form (SAPMG_COARSE_TF32=0 disables)
   int sap_shape = 0;      // Schwarz launch shape for an even number of RHS (SAPMG_SAP_SHAPE; -1: one RHS per CTA)
   int dirac_pair = 1;     // paired Dirac kernel for an even number of FP32-arithmetic RHS (SAPMG_DIRAC_PAIR=0: off)
+  int graphs = 1;         // coarse solves of the mixed form replayed as CUDA graphs (SAPMG_GRAPHS=0: plain launches)
+  int coarse_sap_mrhs = 1; // level-1 Schwarz with all RHS per CTA (SAPMG_COARSE_SAP_MRHS=0: one RHS per CTA)
+  cudaStream_t cap_s = nullptr;            // stream the coarse-solve graphs are captured on
+  cudaGraphExec_t cgraph[3][33] = {};      // [level][right-hand sides]: the captured fixed-step coarse GMRES
+  int cgraph_kernels[3][33] = {};          // kernels in each graph (for the launch counter)
+  unsigned char cgraph_state[3][33] = {};  // 0: not run yet, 1: ran once with plain launches
   int xfer_batch = 16;    // right-hand sides per level-0 transfer launch (autotuned)
   CoarseTune ctune;       // launch shape of the FP16 tensor-core coarse stencil (autotuned)
   // residual history of the last mg_solve: (iteration, right-hand side, relative residual) triples;
@@ -225,6 +231,10 @@ struct mg_ctx {
     return ptr;
   }
   ~mg_ctx() {
+    for (auto& row : cgraph)
+      for (auto& x : row)
+        if (x) cudaGraphExecDestroy(x);
+    if (cap_s) cudaStreamDestroy(cap_s);
     for (void* q : allocs)
       if (q) cudaFree(q);
     if (hh) cudaFreeHost(hh);
@@ -424,22 +434,72 @@ static int fgmres_fixed1(mg_ctx* c, int k, int R) {
   return MG_OK;
 }
 
+// The FP16-basis coarse GMRES as a CUDA graph: its ~4k+3 launches use fixed
+// buffers and no host synchronisation, so after one run with plain launches
+// (which also sets every kernel attribute) the sequence is captured once per
+// (level, R) on a stream of the context's own and replayed on the context's
+// stream, saving the launch gaps between the short dependent kernels.  The
+// replay computes what the plain launches compute, bit for bit.  Plain
+// launches while the coarse families are being profiled (the profile times
+// every launch with events on the host's side).
+static int coarse_gmres_h_graph(mg_ctx* c, int level, CoarseLevel& L, int k, int R) {
+  const bool prof = c->prof.on && ((((c->prof.mask >> FAM_COARSE) | (c->prof.mask >> FAM_CBLAS)) & 1u) != 0);
+  if (!c->graphs || prof || R < 1 || R > 32) return coarse_gmres_h(c, L, k, R);
+  if (c->cgraph_state[level][R] == 0) {
+    c->cgraph_state[level][R] = 1;
+    return coarse_gmres_h(c, L, k, R);
+  }
+  if (!c->cgraph[level][R]) {
+    if (!c->cap_s) SAPMG_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_s, cudaStreamNonBlocking));
+    const cudaStream_t s0 = c->s;
+    const long long l0 = mg_launch_count();
+    SAPMG_CUDA_TRY(cudaStreamBeginCapture(c->cap_s, cudaStreamCaptureModeThreadLocal));
+    c->s = c->cap_s;
+    const int rc = coarse_gmres_h(c, L, k, R);
+    c->s = s0;
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_s, &gr);
+    const long long nk = mg_launch_count() - l0;
+    count_launches(-(int)nk);                           // captured, not launched
+    if (rc < 0 || e != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      if (rc < 0) return rc;
+      return fail(MG_ERR_CUDA, std::string("coarse-solve graph capture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t x = nullptr;
+    const cudaError_t e2 = cudaGraphInstantiate(&x, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e2 != cudaSuccess) return fail(MG_ERR_CUDA, std::string("coarse-solve graph: ") + cudaGetErrorString(e2));
+    c->cgraph[level][R] = x;
+    c->cgraph_kernels[level][R] = (int)nk;
+  }
+  SAPMG_CUDA_TRY(cudaGraphLaunch(c->cgraph[level][R], c->s));
+  count_launches(c->cgraph_kernels[level][R]);
+  return MG_OK;
+}
+
 static int coarse_solve(mg_ctx* c, int level, int R) {
-  if (level == 1 && c->p.n_levels == 2 && c->c1.Vh) return coarse_gmres_h(c, c->c1, c->p.coarse_iters, R);
+  if (level == 1 && c->p.n_levels == 2 && c->c1.Vh) return coarse_gmres_h_graph(c, 1, c->c1, c->p.coarse_iters, R);
   if (level == 1 && c->p.n_levels == 2) return coarse_gmres(c, c->c1, c->p.coarse_iters, R);
   if (level == 1 && c->p.n_levels == 3) return fgmres_fixed1(c, c->p.inner_iters, R);
-  if (level == 2 && c->p.n_levels == 3 && c->c2.Vh) return coarse_gmres_h(c, c->c2, c->p.coarse_iters, R);
+  if (level == 2 && c->p.n_levels == 3 && c->c2.Vh) return coarse_gmres_h_graph(c, 2, c->c2, c->p.coarse_iters, R);
   if (level == 2 && c->p.n_levels == 3) return coarse_gmres(c, c->c2, c->p.coarse_iters, R);
   return fail(MG_ERR_ARG, "coarse level out of range");
 }
 
 // Schwarz sweeps on level 1 (boxes of coarse sites, red-black as on the fine level).
+// FP32 operator: all right-hand sides in one CTA per box (each operator entry
+// loaded once for all of them), unless SAPMG_COARSE_SAP_MRHS=0.
 static int smoother_sweeps1(mg_ctx* c, const void* b, void* z, int n_sweeps, int R) {
+  const bool mrhs = c->coarse_sap_mrhs && c->c1.store == P32 && R >= 2 && R <= 12;
   for (int it = 0; it < n_sweeps; ++it)
     for (int col = 0; col < 2; ++col) {
-      ProfScope ps(c->prof, FAM_SAP, c->s);
-      TRY(launch_coarse_sap(c->c1.store == P64 ? P64 : P32, c->c1.cg, c->sap1, c->c1.M, z, b, col, c->p.n_mr, R,
-                            c->s));
+      ProfScope ps(c->prof, FAM_SAP1, c->s);
+      count_bytes((double)c->c1.cg.nsites / 2 * 9.0 * c->c1.cg.n2 * c->c1.cg.n2 * complex_bytes(c->c1.store) *
+                  (mrhs ? 1.0 : R) * (c->p.n_mr + 1));
+      if (mrhs) TRY(launch_coarse_sap_mrhs(c->c1.cg, c->sap1, c->c1.M, z, b, col, c->p.n_mr, R, c->s));
+      else TRY(launch_coarse_sap(c->c1.store == P64 ? P64 : P32, c->c1.cg, c->sap1, c->c1.M, z, b, col, c->p.n_mr, R,
+                                 c->s));
     }
   return MG_OK;
 }
@@ -1288,7 +1348,7 @@ static int setup_level0(mg_ctx* c) {
     return build_level0_operators(c);
   }
   if (p.init_vectors) {
-    TRY(launch_pack_spinor(P64, p.init_vectors, P64, c->V64, c->g, N, c->s));
+    TRY(launch_pack_spinor(p.init_vectors_prec == P32 ? P32 : P64, p.init_vectors, P64, c->V64, c->g, N, c->s));
   } else {
     TRY(launch_draw_vectors(c->g, c->V64, N, p.seed, 3ull /* test-vector stream */, c->s));
   }
@@ -1343,21 +1403,17 @@ static int setup_level1(mg_ctx* c) {
   const int N0 = c->N0, N1 = c->N1;
   c->sap1 = make_box(L1.cg, p.sap_block2);
   c->agg1 = make_box(L1.cg, p.agg2);
-  // FP64 P0 (block-major) to restrict the smoothed fine vectors
-  void* p0buf = c->alloc((size_t)N0 * nf * 16);
   if (!c->W64) c->W64 = c->alloc((size_t)N1 * n1 * 16);         // reused when set-up part 2 rebuilds level 1
-  if (!p0buf || !c->W64) return fail(MG_ERR_OOM, "level-1 vectors");
+  if (!c->W64) return fail(MG_ERR_OOM, "level-1 vectors");
   if (c->load_w1) {                        // a saved set-up: the level-1 vectors as saved
     SAPMG_CUDA_TRY(cudaMemcpyAsync(c->W64, c->load_w1->data(), (size_t)N1 * n1 * 16, cudaMemcpyHostToDevice, c->s));
-    c->release(p0buf);
     return finish_level1(c);
   }
-  TRY(launch_store_p0(P64, c->g, c->V64, p0buf, N0, c->s));
+  // the smoothed fine vectors restricted with the FP64 P0, read in place
   for (int k = 0; k < N1; ++k)
-    TRY(launch_transfer0(true, P64, c->g, (char*)c->Vs64 + (size_t)k * nf * 16, (char*)c->W64 + (size_t)k * n1 * 16,
-                         p0buf, N0, 1, false, c->s));
+    TRY(launch_restrict_v64(c->g, c->V64, N0, (char*)c->Vs64 + (size_t)k * nf * 16,
+                            (char*)c->W64 + (size_t)k * n1 * 16, c->s));
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
-  c->release(p0buf);
   c->release(c->Vs64);
   c->Vs64 = nullptr;
   // level-1 smoothing of the vectors (S^nu on D_c1 x = 0), kept orthonormal
@@ -1489,6 +1545,8 @@ static int validate(const mg_params* p) {
   if (p->maxiter < 1) return fail(MG_ERR_ARG, "maxiter must be positive");
   if (p->precision < MG_FP64 || p->precision > MG_BF16) return fail(MG_ERR_ARG, "unknown precision");
   if (p->nrhs_max < 1 || p->nrhs_max > 32) return fail(MG_ERR_ARG, "nrhs_max must be in 1..32");
+  if (p->init_vectors_prec != P64 && p->init_vectors_prec != P32)
+    return fail(MG_ERR_ARG, "init_vectors_prec must be MG_FP64 or MG_FP32");
   if (p->setup2_iters < 0) return fail(MG_ERR_ARG, "negative iteration count");
   if (p->setup2_iters > 0 && p->n_levels < 2) return fail(MG_ERR_ARG, "set-up part 2 needs a coarse level");
   return MG_OK;
@@ -1596,7 +1654,9 @@ static int do_setup(mg_ctx* c, const double* U) {
 // right-hand sides per transfer launch, and the coarse stencil's ring depth,
 // CTAs per SM and right-hand sides per launch.  Every candidate of a knob
 // computes each output with the same operations in the same order, so a tuned
-// context gives the default's results bit for bit.  The choice is cached per
+// context gives the default's results bit for bit, except Schwarz shape 6
+// (two threads per site), whose sums of a site's hops run in another order
+// and agree to FP32 rounding.  The choice is cached per
 // (lattice, N, nrhs_max, precision, levels) for the life of the process; a
 // later context with the same key takes it without timing.
 struct TuneChoice {
@@ -1655,7 +1715,8 @@ static int autotune(mg_ctx* c) {
   if (R >= 2 && R % 2 == 0 && c->sap_shape >= 0) {
     int best_shape = c->sap_shape;
     float best = 1e30f;
-    for (int shape = 0; shape <= 5; ++shape) {
+    for (int shape = 0; shape <= 6; ++shape) {
+      if (shape == 6 && c->prec == P32) continue;     // shape 6 holds FP16/BF16 fields only
       c->sap_shape = shape;
       const float ms = timed([&] { return smoother_sweeps(c, b, z, 1, R); });
       if (ms < best) { best = ms; best_shape = shape; }
@@ -1790,6 +1851,8 @@ static int setup_context(mg_ctx* c, const double* U, double c_sw, double m0, con
   c->coarse_tf32 = std::getenv("SAPMG_COARSE_TF32") ? std::atoi(std::getenv("SAPMG_COARSE_TF32")) : 1;
   c->sap_shape = std::getenv("SAPMG_SAP_SHAPE") ? std::atoi(std::getenv("SAPMG_SAP_SHAPE")) : 0;
   c->dirac_pair = std::getenv("SAPMG_DIRAC_PAIR") ? std::atoi(std::getenv("SAPMG_DIRAC_PAIR")) : 1;
+  c->graphs = std::getenv("SAPMG_GRAPHS") ? std::atoi(std::getenv("SAPMG_GRAPHS")) : 1;
+  c->coarse_sap_mrhs = std::getenv("SAPMG_COARSE_SAP_MRHS") ? std::atoi(std::getenv("SAPMG_COARSE_SAP_MRHS")) : 1;
   c->xfer_batch = std::getenv("SAPMG_XFER_BATCH") ? std::max(1, std::atoi(std::getenv("SAPMG_XFER_BATCH"))) : 16;
   if (const char* ct = std::getenv("SAPMG_COARSE_TUNE")) {        // "batch,stages,ctas"
     int b = 16, st = 2, k = 0;

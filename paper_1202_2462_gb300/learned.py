@@ -168,14 +168,14 @@ def train(c_sw, m0, train_dims=(16, 16, 16, 16), train_fields=20, eps_train=0.5,
 
 def infer(net, u, c_sw, m0, noise):
     """BF16 inference of the network's proposals for the noise fields (N, ...)
-    on the gauge field u (device, canonical); returns (proposals as complex128,
-    the layout mg_params.init_vectors takes, and seconds).  One field at a
-    time, written straight into the output.  Raises if a proposal is not
-    finite."""
+    on the gauge field u (device, canonical); returns (proposals as complex64
+    in the canonical layout, which mg_params.init_vectors takes, and seconds).
+    One field at a time, written straight into the output.  Raises if a
+    proposal is not finite."""
     import time
     from .solver import Solver
     s = Solver(u, c_sw, m0, n_levels=1, precision="bf16", fgmres_m=2)
-    out = torch.empty(noise.shape, dtype=torch.complex128, device="cuda")
+    out = torch.empty(noise.shape, dtype=torch.complex64, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(noise.shape[0]):

@@ -30,8 +30,8 @@ class Solver:
 
     U: complex128 CUDA tensor (Lt, Lz, Ly, Lx, 4, 3, 3) of forward links.
     Keyword arguments are mg_params fields (precision may be 'fp64', 'fp32',
-    'fp16', 'bf16'); ``init_vectors`` is an optional complex128 CUDA tensor of
-    initial test vectors (N, Lt, Lz, Ly, Lx, 4, 3); ``setup2_start`` an optional
+    'fp16', 'bf16'); ``init_vectors`` is an optional complex128 or complex64
+    CUDA tensor of initial test vectors (N, Lt, Lz, Ly, Lx, 4, 3); ``setup2_start`` an optional
     complex128 CUDA tensor (coarse sites, 2N), the start vector of set-up part 2
     (used with ``setup2_iters`` > 0).
     """
@@ -49,8 +49,11 @@ class Solver:
         self.params.stream = stream.cuda_stream
         self._init = None
         if init_vectors is not None:
+            if init_vectors.dtype not in (torch.complex128, torch.complex64) or not init_vectors.is_cuda:
+                raise ValueError("init_vectors must be a complex128 or complex64 CUDA tensor")
             self._init = init_vectors.contiguous()
             self.params.init_vectors = self._init.data_ptr()
+            self.params.init_vectors_prec = B.MG_FP32 if init_vectors.dtype == torch.complex64 else B.MG_FP64
         self._start = None
         if setup2_start is not None:
             self._start = setup2_start.contiguous()

@@ -56,13 +56,14 @@ WORKLOADS = {
         precision="bf16", metric=METRIC, fp64_iterations_per_rhs=63),
     # Full form at scale: three levels, 24 test vectors proposed by the learned
     # set-up (trained on 16^4 fields of this eps at this m0) and refined by the
-    # bootstrap; the 12 point sources in batches of two (the flexible basis of
-    # 12 systems in lockstep would not fit beside the hierarchy).  m0 from
-    # paper_1202_2462_gb300.tune.find_m0 (sigma_min ~ 1e-3).
+    # bootstrap; the 12 point sources in batches of two with FGMRES(12) (the
+    # flexible basis of 12 systems in lockstep would not fit beside the
+    # hierarchy).  m0 from paper_1202_2462_gb300.tune.find_m0: sigma_min =
+    # 9.3e-4 by inverse iteration (critical mass of this field about -0.9762).
     "48^3x96": dict(
-        dims=(48, 48, 48, 96), eps=0.7, gauge_seed=105, c_sw=1.0, m0=-0.97,
+        dims=(48, 48, 48, 96), eps=0.7, gauge_seed=105, c_sw=1.0, m0=-0.9752,
         rhs="point12", rhs_seed=0, n_levels=3, agg=((4, 4, 4, 4), (2, 2, 2, 2)), n_vec=(24, 24),
-        n_mr=5, nu_post=1, setup_iters=20, coarse_iters=20, fgmres_m=16, tol=1e-10, maxiter=2000,
+        n_mr=5, nu_post=1, setup_iters=20, coarse_iters=20, fgmres_m=12, tol=1e-10, maxiter=2000,
         nrhs_max=2, init="learned", precision="bf16", metric=METRIC, fp64_iterations_per_rhs=None),
     # Mid-size case for Nsight Compute captures: fields larger than L2, a few GB on the device.
     "32^3x32": dict(

@@ -170,7 +170,7 @@ def test_sap_multi_rhs_matches_single(prec):
     s.close()
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("prec,n_mr", [("fp32", 4), ("fp16", 1), ("bf16", 4), ("bf16", 2)])
 def test_sap_pair_kernel_parity(prec, n_mr, shape, monkeypatch):
     """The paired Schwarz kernel (two right-hand sides per thread, packed
@@ -178,9 +178,20 @@ def test_sap_pair_kernel_parity(prec, n_mr, shape, monkeypatch):
     right-hand sides from a nonzero start, with FP32/FP16/BF16 fields, against
     the oracle's sweeps with the identically rounded fields.  n_MR = 1 takes
     the kernel's first-and-last MR step path, n_MR = 2 its first and last
-    without a middle step."""
+    without a middle step.  Shape 6 (two threads per site) holds FP16/BF16
+    fields only and refuses FP32 fields."""
     monkeypatch.setenv("SAPMG_SAP_SHAPE", str(shape))
     torch = torch_cuda()
+    if shape == 6 and prec == "fp32":
+        import paper_1202_2462_gb300 as G
+        dims = (8, 8, 8, 16)
+        s = _solver(torch, synth.random_gauge_field(dims, 0.5, 32), 1.0, 0.05, False, precision=prec, nrhs_max=2)
+        b = dev(torch, synth.random_spinor(dims, 33, nvec=2), torch.complex64)
+        with pytest.raises(G.MgError) as e:
+            s.smooth(b, torch.zeros_like(b), 1)
+        s.close()
+        assert e.value.code == G.MG_ERR_ARG
+        return
     dims = (8, 8, 16, 8)
     u = synth.random_gauge_field(dims, 0.5, 32)
     m0 = 0.05
@@ -258,7 +269,7 @@ def test_dirac_pair_kernel_matches_single_kernel(monkeypatch):
     assert np.max(np.abs(outs[0] - outs[1])) / np.max(np.abs(outs[1])) < 2e-6
 
 
-@pytest.mark.parametrize("shape", [0, 3, 5])
+@pytest.mark.parametrize("shape", [0, 3, 5, 6])
 def test_sap_pair_kernel_tiny_blocks_stay_finite(shape, monkeypatch):
     """Blocks whose residual is ~1e-21 make <p, p> a denormal FP32 number: the
     MR coefficient must still be finite (alpha by division; a reciprocal of

@@ -466,3 +466,82 @@ def test_solve_residual_history(field, prec):
         assert its and max(its) <= k and min(its) == 1
         assert 0 < d["rho"] < 1
     assert total == info.iterations and abs(worst - info.relres) <= 1e-12
+
+
+def test_complex64_initial_vectors_match_complex128():
+    """mg_params.init_vectors_prec = MG_FP32: initial test vectors given as
+    complex64 are widened exactly, so the hierarchy equals the one built from
+    the same values in complex128, bit for bit."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    dims = (8, 8, 8, 8)
+    u = dev(torch, synth.random_gauge_field(dims, 0.4, 171))
+    iv = torch.from_numpy(synth.test_vector_draw(dims, 6, 172).astype(np.complex64))
+    ops = []
+    for dt in (torch.complex64, torch.complex128):
+        s = G.Solver(u, 1.0, -0.2, n_levels=2, n_vec=(6,), setup_iters=1, precision="fp64",
+                     init_vectors=iv.to(dt).cuda())
+        m = torch.empty((16, 9, 12, 12), dtype=torch.complex128, device="cuda")
+        G.mg_get_coarse_op(s.ctx, 1, m)
+        ops.append(m.cpu())
+        s.close()
+    assert torch.equal(ops[0], ops[1])
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_coarse_solve_graphs_match_plain_launches(levels, monkeypatch):
+    """The mixed form replays its FP16-basis coarse GMRES as a captured CUDA
+    graph (after one run with plain launches): two solves with graphs give
+    the solution of the plain launches (SAPMG_GRAPHS=0) bit for bit, and the
+    launch counter counts the graphs' kernels as launches."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    dims = (8, 8, 8, 16) if levels == 2 else (16, 8, 8, 16)
+    kw = dict(n_levels=levels, n_vec=(12, 8) if levels == 3 else (12,), setup_iters=2, precision="bf16",
+              nrhs_max=4, seed=6, coarse_iters=8, fgmres_m=10)
+    if levels == 3:
+        kw.update(sap_block2=(2, 1, 1, 2), agg2=(2, 2, 2, 2), inner_iters=3)
+    u = dev(torch, synth.random_gauge_field(dims, 0.4, 181))
+    b = dev(torch, synth.random_spinor(dims, 182, nvec=4))
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("SAPMG_GRAPHS", flag)
+        s = G.Solver(u, 1.0, -0.1, **kw)
+        zs, counts = [], []
+        for _ in range(2):                       # the first solve runs plain, then the graphs
+            torch.cuda.synchronize()
+            l0 = G.mg_launch_count()
+            z, info, code = s.solve(b)
+            torch.cuda.synchronize()
+            counts.append(G.mg_launch_count() - l0)
+            assert code == 0
+            zs.append(z)
+        s.close()
+        assert torch.equal(zs[0], zs[1])
+        out[flag] = (zs[1], counts)
+    assert torch.equal(out["0"][0], out["1"][0])
+    assert out["0"][1] == out["1"][1]
+
+
+@pytest.mark.parametrize("nrhs", [2, 3, 6, 12])
+def test_level1_schwarz_all_rhs_per_cta_matches_one_rhs_per_cta(nrhs, monkeypatch):
+    """Three levels, mixed form: the level-1 Schwarz pass with every
+    right-hand side in one CTA per box (each operator entry loaded once for
+    all) gives the one-RHS-per-CTA solve bit for bit (same sums in the same
+    order per right-hand side), for batch widths across its template bounds."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    dims = (16, 8, 8, 16)
+    kw = dict(n_levels=3, n_vec=(12, 8), setup_iters=2, precision="bf16", nrhs_max=nrhs, seed=7, coarse_iters=8,
+              fgmres_m=10, sap_block2=(2, 1, 1, 2), agg2=(2, 2, 2, 2), inner_iters=3)
+    u = dev(torch, synth.random_gauge_field(dims, 0.4, 191))
+    b = dev(torch, synth.random_spinor(dims, 192, nvec=nrhs))
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("SAPMG_COARSE_SAP_MRHS", flag)
+        s = G.Solver(u, 1.0, -0.1, **kw)
+        z, info, code = s.solve(b)
+        s.close()
+        assert code == 0
+        out[flag] = (z, info.iterations)
+    assert torch.equal(out["0"][0], out["1"][0]) and out["0"][1] == out["1"][1]
