@@ -173,11 +173,15 @@ def make_rhs(wl, dims):
 
 def solver_kwargs(wl, precision, nrhs):
     """Solver parameters of the workload; the mixed form tunes its launch shapes at set-up."""
-    return dict(n_levels=wl["n_levels"], n_vec=tuple(wl["n_vec"]), setup_iters=wl["setup_iters"],
-                n_mr=wl["n_mr"], nu_post=wl["nu_post"], coarse_iters=wl["coarse_iters"],
-                fgmres_m=wl["fgmres_m"], tol=wl["tol"], maxiter=wl.get("maxiter", 500),
-                precision=precision, nrhs_max=min(nrhs, wl.get("nrhs_max", nrhs)), seed=wl.get("vec_seed", 1),
-                autotune=int(precision != "fp64"))
+    kw = dict(n_levels=wl["n_levels"], n_vec=tuple(wl["n_vec"]), setup_iters=wl["setup_iters"],
+              n_mr=wl["n_mr"], nu_post=wl["nu_post"], coarse_iters=wl["coarse_iters"],
+              fgmres_m=wl["fgmres_m"], tol=wl["tol"], maxiter=wl.get("maxiter", 500),
+              precision=precision, nrhs_max=min(nrhs, wl.get("nrhs_max", nrhs)), seed=wl.get("vec_seed", 1),
+              autotune=int(precision != "fp64"))
+    for k in ("inner_iters", "sap_block2", "agg2"):                # three levels: the level-1 parameters
+        if k in wl:
+            kw[k] = tuple(wl[k]) if isinstance(wl[k], (list, tuple)) else wl[k]
+    return kw
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
@@ -405,6 +409,7 @@ def wl_config(wl, name, precision):
     return {"workload": f"{d[0]}^3x{d[3]}" if d[0] == d[1] == d[2] else name,
             "lattice": list(d), "eps": wl["eps"], "c_sw": wl["c_sw"], "m0": wl["m0"],
             "rhs": wl["rhs"], "levels": wl["n_levels"], "n_vec": list(wl["n_vec"]), "n_mr": wl["n_mr"],
+            **({"inner_iters": wl["inner_iters"]} if "inner_iters" in wl else {}),
             "nu_post": wl["nu_post"], "coarse_iters": wl["coarse_iters"], "fgmres_m": wl["fgmres_m"],
             "tol": wl["tol"], "storage": precision, "parallelism": "replicas",
             "l2": "inputs larger than L2 (fields of several GB)"}

@@ -240,7 +240,10 @@ int mg_get_vectors(mg_ctx* ctx, int level, double* out);
 /* The coarse operator of level `level` (1 or 2) as FP64 stencil: out device
  * [coarse site][9][2N][2N] complex128, row-major (row i, column j); direction
  * 0 = self, 1 + 2 mu = +mu, 2 + 2 mu = -mu (mu = x, y, z, t), i.e.
- * (D_c x)(a) = sum_d M_d(a) x(a + offset_d). */
+ * (D_c x)(a) = sum_d M_d(a) x(a + offset_d).  The plain (FP64) form
+ * assembles it in FP64 arithmetic; the mixed form, which stores and applies
+ * it in FP32 and FP16, assembles level 1 in FP32 arithmetic from FP32 copies
+ * of the vectors, links and clover (relative accuracy about 1e-6). */
 int mg_get_coarse_op(mg_ctx* ctx, int level, double* out);
 
 /* v_c = P^dagger v (restriction) and v = P v_c (interpolation) between level

@@ -633,29 +633,29 @@ int launch_store_p0(int prec, const Geom& g, const void* V64, void* Pv, int N, c
 // the 9 partial images of u = v_k|_chi' (self: clover and hops inside a; +-mu:
 // the hop from the neighbouring aggregate across a's face) and projects each
 // onto the 2N columns of P on a.
-template <int MU, int S>
-__device__ __forceinline__ void assemble_hop(const Geom& g, const double2* __restrict__ U, const double2* vk,
-                                             int chi_p, int blk, int loc, bool inside, Cplx<double> (&w)[12]) {
+template <int MU, int S, class R, class T2>
+__device__ __forceinline__ void assemble_hop(const Geom& g, const T2* __restrict__ U, const T2* vk,
+                                             int chi_p, int blk, int loc, bool inside, Cplx<R> (&w)[12]) {
   int nb, nl;
   neighbour(g, blk, loc, MU, S, nb, nl);
   if ((nb == blk) != inside) return;
-  Cplx<double> u[12];
-  load_spinor<double>(vk, nb, nl, u);
+  Cplx<R> u[12];
+  load_spinor<R>(vk, nb, nl, u);
 #pragma unroll
   for (int c = 0; c < 12; ++c)
-    if ((c / 6) != chi_p) u[c] = cmk(0.0, 0.0);
-  Cplx<double> acc[12];
+    if ((c / 6) != chi_p) u[c] = cmk<R>(0, 0);
+  Cplx<R> acc[12];
 #pragma unroll
-  for (int c = 0; c < 12; ++c) acc[c] = cmk(0.0, 0.0);
+  for (int c = 0; c < 12; ++c) acc[c] = cmk<R>(0, 0);
   if (S > 0) hop_fwd<MU>(U, blk, loc, u, acc);
   else hop_bwd<MU>(U, nb, nl, u, acc);
 #pragma unroll
-  for (int c = 0; c < 12; ++c) w[c] = w[c] - 0.5 * acc[c];
+  for (int c = 0; c < 12; ++c) w[c] = w[c] - (R)0.5 * acc[c];
 }
 
-template <int MU>
-__device__ __forceinline__ void assemble_dir(const Geom& g, const double2* U, const double2* vk, int chi_p, int blk,
-                                             int loc, int d, Cplx<double> (&w)[12]) {
+template <int MU, class R, class T2>
+__device__ __forceinline__ void assemble_dir(const Geom& g, const T2* U, const T2* vk, int chi_p, int blk,
+                                             int loc, int d, Cplx<R> (&w)[12]) {
   if (d == 0) {
     assemble_hop<MU, 1>(g, U, vk, chi_p, blk, loc, true, w);
     assemble_hop<MU, -1>(g, U, vk, chi_p, blk, loc, true, w);
@@ -666,8 +666,13 @@ __device__ __forceinline__ void assemble_dir(const Geom& g, const double2* U, co
   }
 }
 
-__global__ void __launch_bounds__(256) assemble0_kernel(const double2* __restrict__ V, const double2* __restrict__ U,
-                                                        const double2* __restrict__ A, double2* __restrict__ M,
+// R = double with FP64 vectors and fields (the plain form, exact to rounding);
+// R = float with FP32 copies (the mixed form, whose coarse operator is stored
+// in FP32 and FP16: FP64 arithmetic is scarce on this GPU).  The entries are
+// written in FP64 either way.
+template <class R, class T2>
+__global__ void __launch_bounds__(256) assemble0_kernel(const T2* __restrict__ V, const T2* __restrict__ U,
+                                                        const T2* __restrict__ A, double2* __restrict__ M,
                                                         Geom g, int N) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double (*red)[4] = reinterpret_cast<double (*)[4]>(smem_raw);   // [8 * N][4]
@@ -675,32 +680,41 @@ __global__ void __launch_bounds__(256) assemble0_kernel(const double2* __restric
   const int n2 = 2 * N, chi_p = j / N, k = j % N;
   const int wid = loc >> 5, lane = loc & 31;
   const long long fs = g.V * 12;
-  const double2* vk = V + k * fs;
+  const T2* vk = V + k * fs;
   for (int d = 0; d < 9; ++d) {
-    Cplx<double> w[12];
+    Cplx<R> w[12];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) w[c] = cmk(0.0, 0.0);
+    for (int c = 0; c < 12; ++c) w[c] = cmk<R>(0, 0);
     if (d == 0) {
-      Cplx<double> u[12];
-      load_spinor<double>(vk, blk, loc, u);
+      Cplx<R> u[12];
+      load_spinor<R>(vk, blk, loc, u);
 #pragma unroll
       for (int c = 0; c < 12; ++c)
-        if ((c / 6) != chi_p) u[c] = cmk(0.0, 0.0);
-      clover_apply<double>(A, blk, loc, u, w);
+        if ((c / 6) != chi_p) u[c] = cmk<R>(0, 0);
+      clover_apply<R>(A, blk, loc, u, w);
     }
     assemble_dir<0>(g, U, vk, chi_p, blk, loc, d, w);
     assemble_dir<1>(g, U, vk, chi_p, blk, loc, d, w);
     assemble_dir<2>(g, U, vk, chi_p, blk, loc, d, w);
     assemble_dir<3>(g, U, vk, chi_p, blk, loc, d, w);
-    // project onto v_i|_chi on this block
+    // project onto v_i|_chi on this block; for d > 0 only the sites on the
+    // block's face towards direction d have a non-zero image (the others would
+    // add exact zeros, so skipping them changes no bit)
+    bool live = true;
+    if (d > 0) {
+      const int mu = (d - 1) >> 1, cmu = (loc >> (2 * mu)) & 3;
+      live = (d & 1) ? cmu == 3 : cmu == 0;
+    }
     for (int i = 0; i < N; ++i) {
-      const double2* vi = V + i * fs + (size_t)blk * 12 * 256 + loc;
-      Cplx<double> d0 = cmk(0.0, 0.0), d1 = cmk(0.0, 0.0);
+      const T2* vi = V + i * fs + (size_t)blk * 12 * 256 + loc;
+      Cplx<R> d0 = cmk<R>(0, 0), d1 = cmk<R>(0, 0);
+      if (live) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) { double2 t = vi[c * 256]; cfma_conj(d0, cmk(t.x, t.y), w[c]); }
+        for (int c = 0; c < 6; ++c) { const T2 t = vi[c * 256]; cfma_conj(d0, cmk<R>(t.x, t.y), w[c]); }
 #pragma unroll
-      for (int c = 6; c < 12; ++c) { double2 t = vi[c * 256]; cfma_conj(d1, cmk(t.x, t.y), w[c]); }
-      double a = warp_sum(d0.re), b = warp_sum(d0.im), c2 = warp_sum(d1.re), e = warp_sum(d1.im);
+        for (int c = 6; c < 12; ++c) { const T2 t = vi[c * 256]; cfma_conj(d1, cmk<R>(t.x, t.y), w[c]); }
+      }
+      const R a = warp_sum(d0.re), b = warp_sum(d0.im), c2 = warp_sum(d1.re), e = warp_sum(d1.im);
       if (lane == 0) { double* q = red[wid * N + i]; q[0] = a; q[1] = b; q[2] = c2; q[3] = e; }
     }
     __syncthreads();
@@ -715,12 +729,19 @@ __global__ void __launch_bounds__(256) assemble0_kernel(const double2* __restric
   }
 }
 
-int launch_assemble0(const Geom& g, const void* V64, const void* U64, const void* A64, void* M64, int N,
+int launch_assemble0(const Geom& g, int prec, const void* V, const void* U, const void* A, void* M64, int N,
                      cudaStream_t s) {
   dim3 grid(g.nblocks, 2 * N);
   const size_t smem = sizeof(double) * 4 * 8 * N;
-  assemble0_kernel<<<grid, 256, smem, s>>>((const double2*)V64, (const double2*)U64, (const double2*)A64,
-                                           (double2*)M64, g, N); count_launches(1);
+  if (prec == P64)
+    assemble0_kernel<double, double2><<<grid, 256, smem, s>>>((const double2*)V, (const double2*)U,
+                                                              (const double2*)A, (double2*)M64, g, N);
+  else if (prec == P32)
+    assemble0_kernel<float, float2><<<grid, 256, smem, s>>>((const float2*)V, (const float2*)U, (const float2*)A,
+                                                            (double2*)M64, g, N);
+  else
+    return MG_ERR_ARG;
+  count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }

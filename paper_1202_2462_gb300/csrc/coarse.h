@@ -37,7 +37,10 @@ int launch_transfer0(bool restrict_, int prec, const Geom& g, const void* in, vo
                      int nrhs, bool tf32, cudaStream_t s);
 int launch_block_gs0(const Geom& g, void* V64, int N, cudaStream_t s);
 int launch_store_p0(int prec, const Geom& g, const void* V64, void* Pv, int N, cudaStream_t s);
-int launch_assemble0(const Geom& g, const void* V64, const void* U64, const void* A64, void* M64, int N,
+// D_c = P^dagger D P into the FP64 M64 from the locally orthonormal vectors V,
+// links U and clover A, all of type prec (P64: FP64 arithmetic; P32: FP32
+// copies and FP32 arithmetic, the mixed form).
+int launch_assemble0(const Geom& g, int prec, const void* V, const void* U, const void* A, void* M64, int N,
                      cudaStream_t s);
 
 // Coarse levels.
@@ -64,12 +67,13 @@ int launch_coarse_apply_mma(const CGeom& c, int store, const void* M, const void
 
 // Intermediate level of a three-level hierarchy (coarse1.cu).
 // The colour pass of launch_coarse_sap for 1 <= nrhs <= 12 right-hand sides in one
-// CTA per box (FP32 operator and vectors; each operator entry loaded once for all
-// of them); bit for bit the one-RHS-per-CTA results.
-int launch_coarse_sap_mrhs(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
-                           int n_mr, int nrhs, cudaStream_t s);
+// CTA per box (FP32 vectors; FP32 operator, or its FP16 copy with m16; each
+// operator entry loaded once for all of them); bit for bit the one-RHS-per-CTA
+// results with the same operator.
+int launch_coarse_sap_mrhs(const CGeom& c, const Box4& bx, const void* M, bool m16, void* z, const void* b,
+                           int colour, int n_mr, int nrhs, cudaStream_t s);
 int launch_coarse_sap(int prec, const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
-                      int n_mr, int nrhs, cudaStream_t s);
+                      int n_mr, int nrhs, cudaStream_t s, bool m16 = false);
 int launch_transfer1(bool restrict_, int prec, const CGeom& c, const Box4& ag, const void* in, void* out,
                      const void* W, int N1, int nrhs, cudaStream_t s);
 int launch_block_gs1(const CGeom& c, const Box4& ag, void* W64, int N1, cudaStream_t s);

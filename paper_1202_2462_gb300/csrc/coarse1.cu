@@ -188,15 +188,15 @@ static int coarse_sap_t(const CGeom& c, const Box4& bx, const void* M, void* z, 
 }
 
 // The same colour pass for all right-hand sides in one CTA per box (FP32
-// operator and vectors): each operator entry is loaded once for every
+// vectors, FP32 or FP16 operator): each operator entry is loaded once for every
 // right-hand side, where the one-RHS-per-CTA form above reads the box's
 // operator (16 sites x 9 x n2^2 entries) once per right-hand side and MR step
 // from memory.  Per right-hand side every sum runs in the order of the kernel
 // above (the same residual and MR sums, the same block reduction), so the two
 // give the same results bit for bit.  rho and e in shared memory as
 // [box site][n2][NR]; NR >= nrhs, a compile-time bound on the right-hand sides.
-template <int NR>
-__global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const float2* __restrict__ M, float2* __restrict__ z,
+template <int NR, class TM>
+__global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const TM* __restrict__ M, float2* __restrict__ z,
                                                                const float2* __restrict__ b, CGeom c, Box4 bx,
                                                                int colour, int n_mr, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -224,12 +224,12 @@ __global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const float2* __r
         acc[r] = r0 + r < nrhs ? Io<float, float2>::ldc(b + (r0 + r) * fs + (size_t)site * n2 + i) : cmk(0.f, 0.f);
       for (int d = 0; d < 9; ++d) {
         const size_t xo = (size_t)stencil_nb(c, site, d) * n2;
-        const float2* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
+        const TM* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
         Cplx<float> t[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) t[r] = cmk(0.f, 0.f);
         for (int j = 0; j < n2; ++j) {
-          const Cplx<float> mv = Io<float, float2>::ld(m + (size_t)j * n2);
+          const Cplx<float> mv = Io<float, TM>::ld(m + (size_t)j * n2);
 #pragma unroll
           for (int r = 0; r < 4; ++r)
             if (r0 + r < nrhs) cfma(t[r], mv, Io<float, float2>::ldc(z + (r0 + r) * fs + xo + j));
@@ -261,10 +261,10 @@ __global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const float2* __r
           for (int m = 0; m < mu; ++m) stride *= bx.b[m];
           ln = s + step * stride;
         }
-        const float2* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
+        const TM* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
         const Cplx<float>* rn = rs + (size_t)ln * n2 * NR;
         for (int j = 0; j < n2; ++j) {
-          const Cplx<float> mv = Io<float, float2>::ld(m + (size_t)j * n2);
+          const Cplx<float> mv = Io<float, TM>::ld(m + (size_t)j * n2);
 #pragma unroll
           for (int r = 0; r < NR; ++r) cfma(p[r], mv, rn[j * NR + r]);
         }
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const float2* __r
       }
 }
 
-template <int NR>
+template <int NR, class TM>
 static int coarse_sap_mrhs_t(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
                              int n_mr, int nrhs, cudaStream_t s) {
   const int threads = ((bx.sites * c.n2 + 31) / 32) * 32;
@@ -315,31 +315,41 @@ static int coarse_sap_mrhs_t(const CGeom& c, const Box4& bx, const void* M, void
   if (smem > 227 * 1024) return MG_ERR_ARG;
   static bool attr = false;
   if (!attr) {
-    SAPMG_CUDA_TRY(cudaFuncSetAttribute(coarse_sap_mrhs_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SAPMG_CUDA_TRY(cudaFuncSetAttribute(coarse_sap_mrhs_kernel<NR, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         227 * 1024));
     attr = true;
   }
-  coarse_sap_mrhs_kernel<NR><<<(unsigned)(bx.nboxes / 2), threads, smem, s>>>(
-      (const float2*)M, (float2*)z, (const float2*)b, c, bx, colour, n_mr, nrhs);
+  coarse_sap_mrhs_kernel<NR, TM><<<(unsigned)(bx.nboxes / 2), threads, smem, s>>>(
+      (const TM*)M, (float2*)z, (const float2*)b, c, bx, colour, n_mr, nrhs);
   count_launches(1);
   SAPMG_CUDA_TRY(cudaGetLastError());
   return MG_OK;
 }
 
-int launch_coarse_sap_mrhs(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
-                           int n_mr, int nrhs, cudaStream_t s) {
-  if (nrhs <= 2) return coarse_sap_mrhs_t<2>(c, bx, M, z, b, colour, n_mr, nrhs, s);
-  if (nrhs <= 4) return coarse_sap_mrhs_t<4>(c, bx, M, z, b, colour, n_mr, nrhs, s);
-  if (nrhs <= 8) return coarse_sap_mrhs_t<8>(c, bx, M, z, b, colour, n_mr, nrhs, s);
-  if (nrhs <= 12) return coarse_sap_mrhs_t<12>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+template <class TM>
+static int coarse_sap_mrhs_any(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
+                               int n_mr, int nrhs, cudaStream_t s) {
+  if (nrhs <= 2) return coarse_sap_mrhs_t<2, TM>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+  if (nrhs <= 4) return coarse_sap_mrhs_t<4, TM>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+  if (nrhs <= 8) return coarse_sap_mrhs_t<8, TM>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+  if (nrhs <= 12) return coarse_sap_mrhs_t<12, TM>(c, bx, M, z, b, colour, n_mr, nrhs, s);
   return MG_ERR_ARG;
 }
 
+int launch_coarse_sap_mrhs(const CGeom& c, const Box4& bx, const void* M, bool m16, void* z, const void* b,
+                           int colour, int n_mr, int nrhs, cudaStream_t s) {
+  return m16 ? coarse_sap_mrhs_any<__half2>(c, bx, M, z, b, colour, n_mr, nrhs, s)
+             : coarse_sap_mrhs_any<float2>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+}
+
 int launch_coarse_sap(int prec, const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
-                      int n_mr, int nrhs, cudaStream_t s) {
+                      int n_mr, int nrhs, cudaStream_t s, bool m16) {
+  if (m16 && prec != P32) return MG_ERR_ARG;
   switch (prec) {
     case P64: return coarse_sap_t<double, double2, double2>(c, bx, M, z, b, colour, n_mr, nrhs, s);
-    case P32: return coarse_sap_t<float, float2, float2>(c, bx, M, z, b, colour, n_mr, nrhs, s);
+    case P32:
+      return m16 ? coarse_sap_t<float, __half2, float2>(c, bx, M, z, b, colour, n_mr, nrhs, s)
+                 : coarse_sap_t<float, float2, float2>(c, bx, M, z, b, colour, n_mr, nrhs, s);
     default: return MG_ERR_ARG;
   }
 }

@@ -150,6 +150,8 @@ struct mg_ctx {
   int dirac_pair = 1;     // paired Dirac kernel for an even number of FP32-arithmetic RHS (SAPMG_DIRAC_PAIR=0: off)
   int graphs = 1;         // coarse solves of the mixed form replayed as CUDA graphs (SAPMG_GRAPHS=0: plain launches)
   int coarse_sap_mrhs = 1; // level-1 Schwarz with all RHS per CTA (SAPMG_COARSE_SAP_MRHS=0: one RHS per CTA)
+  int coarse_sap_fp16 = 1; // level-1 Schwarz reads the FP16 operator copy (SAPMG_COARSE_SAP_FP16=0: FP32)
+  int setup_fp32 = 1;      // mixed form: set-up part 1 on FP32 vectors (SAPMG_SETUP_FP32=0: FP64 vectors)
   cudaStream_t cap_s = nullptr;            // stream the coarse-solve graphs are captured on
   cudaGraphExec_t cgraph[3][33] = {};      // [level][right-hand sides]: the captured fixed-step coarse GMRES
   int cgraph_kernels[3][33] = {};          // kernels in each graph (for the launch counter)
@@ -488,18 +490,23 @@ static int coarse_solve(mg_ctx* c, int level, int R) {
 }
 
 // Schwarz sweeps on level 1 (boxes of coarse sites, red-black as on the fine level).
-// FP32 operator: all right-hand sides in one CTA per box (each operator entry
-// loaded once for all of them), unless SAPMG_COARSE_SAP_MRHS=0.
+// Mixed form: all right-hand sides in one CTA per box (each operator entry
+// loaded once for all of them), unless SAPMG_COARSE_SAP_MRHS=0, reading the
+// FP16 copy of the level-1 operator that the level-1 Krylov operator already
+// uses (the pass reads the box's operator once per MR step: half the bytes),
+// unless SAPMG_COARSE_SAP_FP16=0.
 static int smoother_sweeps1(mg_ctx* c, const void* b, void* z, int n_sweeps, int R) {
   const bool mrhs = c->coarse_sap_mrhs && c->c1.store == P32 && R >= 2 && R <= 12;
+  const bool m16 = c->coarse_sap_fp16 && c->c1.store == P32 && c->c1.Mh != nullptr;
+  const void* M = m16 ? c->c1.Mh : c->c1.M;
   for (int it = 0; it < n_sweeps; ++it)
     for (int col = 0; col < 2; ++col) {
       ProfScope ps(c->prof, FAM_SAP1, c->s);
-      count_bytes((double)c->c1.cg.nsites / 2 * 9.0 * c->c1.cg.n2 * c->c1.cg.n2 * complex_bytes(c->c1.store) *
-                  (mrhs ? 1.0 : R) * (c->p.n_mr + 1));
-      if (mrhs) TRY(launch_coarse_sap_mrhs(c->c1.cg, c->sap1, c->c1.M, z, b, col, c->p.n_mr, R, c->s));
-      else TRY(launch_coarse_sap(c->c1.store == P64 ? P64 : P32, c->c1.cg, c->sap1, c->c1.M, z, b, col, c->p.n_mr, R,
-                                 c->s));
+      count_bytes((double)c->c1.cg.nsites / 2 * 9.0 * c->c1.cg.n2 * c->c1.cg.n2 *
+                  complex_bytes(m16 ? P16 : c->c1.store) * (mrhs ? 1.0 : R) * (c->p.n_mr + 1));
+      if (mrhs) TRY(launch_coarse_sap_mrhs(c->c1.cg, c->sap1, M, m16, z, b, col, c->p.n_mr, R, c->s));
+      else TRY(launch_coarse_sap(c->c1.store == P64 ? P64 : P32, c->c1.cg, c->sap1, M, z, b, col, c->p.n_mr, R, c->s,
+                                 m16));
     }
   return MG_OK;
 }
@@ -1103,17 +1110,20 @@ static int check_finite(mg_ctx* c, const double* x, size_t n_doubles) {
 
 // Global orthonormalisation of the N set-up vectors (FP64): classical
 // Gram-Schmidt against the previous vectors, applied twice, then normalise.
-static int orthonormalise(mg_ctx* c, void* V, int N, size_t n) {
+// Classical Gram-Schmidt with a second pass of N vectors (type P64, or P32
+// for the mixed form's set-up vectors).
+static int orthonormalise(mg_ctx* c, void* V, int N, size_t n, int type = P64) {
   const BVec one = bvec(n, 1, n);
-  auto Vk = [&](int k) { return (void*)((char*)V + (size_t)k * n * 16); };
+  const size_t eb = type == P64 ? 16 : 8;
+  auto Vk = [&](int k) { return (void*)((char*)V + (size_t)k * n * eb); };
   std::vector<const void*> vl;
   for (int k = 0; k < N; ++k) {
     for (int pass = 0; pass < 2 && k > 0; ++pass) {
-      TRY(blas_multidot(P64, one, vl.data(), k, Vk(k), c->hd, c->ldh, 0, nullptr, c->partial, c->s));
-      TRY(blas_multiaxpy(P64, one, Vk(k), vl.data(), k, c->hd, c->ldh, -1.0, c->s));
+      TRY(blas_multidot(type, one, vl.data(), k, Vk(k), c->hd, c->ldh, 0, nullptr, c->partial, c->s));
+      TRY(blas_multiaxpy(type, one, Vk(k), vl.data(), k, c->hd, c->ldh, -1.0, c->s));
     }
-    TRY(dot_to(c, P64, one, Vk(k), Vk(k), c->hd + c->ldh - 1, 1));
-    TRY(blas_normalize(P64, one, Vk(k), Vk(k), c->hd + c->ldh - 1, 1, nullptr, 0, c->s));
+    TRY(dot_to(c, type, one, Vk(k), Vk(k), c->hd + c->ldh - 1, 1));
+    TRY(blas_normalize(type, one, Vk(k), Vk(k), c->hd + c->ldh - 1, 1, nullptr, 0, c->s));
     vl.push_back(Vk(k));
   }
   return MG_OK;
@@ -1137,7 +1147,17 @@ static int build_level0_operators(mg_ctx* c) {
   const size_t msz = (size_t)L.cg.nsites * 9 * L.cg.n2 * L.cg.n2;
   if (!L.M64) L.M64 = c->alloc(msz * 16);
   if (!L.M64) return fail(MG_ERR_OOM, "coarse operator");
-  TRY(launch_assemble0(c->g, c->V64, c->U64, c->A64, L.M64, N, c->s));
+  // the mixed form stores D_c in FP32 and FP16: assemble it from FP32 copies in
+  // FP32 arithmetic (the flexible basis, free during the set-up, holds the
+  // vectors) unless SAPMG_SETUP_FP32=0 or the basis is too small
+  const bool f32 = c->vt == P32 && c->setup_fp32 && c->U32 && c->A32 && c->Z &&
+                   (size_t)c->m * c->p.nrhs_max >= (size_t)N;
+  if (f32) {
+    TRY(blas_axpby2(P64, scal_all(1.0, N), c->V64, n, P32, scal_all(0.0, N), c->Z, n, n, N, c->s));
+    TRY(launch_assemble0(c->g, P32, c->Z, c->U32, c->A32, L.M64, N, c->s));
+  } else {
+    TRY(launch_assemble0(c->g, P64, c->V64, c->U64, c->A64, L.M64, N, c->s));
+  }
   L.store = c->dc_prec;
   if (c->dc_prec == P64) {
     L.M = L.M64;
@@ -1337,6 +1357,21 @@ static int setup_part2(mg_ctx* c, void* V2) {
   return MG_OK;
 }
 
+// verbose: wall time of the set-up's phases (synchronising the stream; only then)
+struct PhaseClock {
+  const mg_ctx* c;
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  explicit PhaseClock(const mg_ctx* c_) : c(c_) {}
+  double lap() {
+    if (!c->p.verbose) return 0.0;
+    cudaStreamSynchronize(c->s);
+    const auto n = std::chrono::steady_clock::now();
+    const double s = std::chrono::duration<double>(n - t).count();
+    t = n;
+    return s;
+  }
+};
+
 static int setup_level0(mg_ctx* c) {
   const size_t n = c->fine_n();
   const int N = c->N0;
@@ -1353,7 +1388,24 @@ static int setup_level0(mg_ctx* c) {
     TRY(launch_draw_vectors(c->g, c->V64, N, p.seed, 3ull /* test-vector stream */, c->s));
   }
   // bootstrap part 1: nu sweeps of the smoother's iteration matrix (SAP on D x = 0), kept orthonormal
-  for (int it = 0; it < p.setup_iters; ++it) {
+  PhaseClock clk(c);
+  double t_sweep = 0, t_orth = 0;
+  // Mixed form: the vectors stay FP32 through part 1 (in the flexible basis,
+  // free until the first solve) and are orthonormalised in FP32; the sweeps
+  // are FP32 anyway, and FP64 arithmetic is scarce on this GPU.  The FP64
+  // form, or a basis too small for N vectors, keeps them FP64.
+  const bool f32 = c->vt == P32 && c->setup_fp32 && p.setup_iters > 0 && (size_t)c->m * p.nrhs_max >= (size_t)N;
+  if (f32) {
+    TRY(blas_axpby2(P64, scal_all(1.0, N), c->V64, n, P32, scal_all(0.0, N), c->Z, n, n, N, c->s));
+    for (int it = 0; it < p.setup_iters; ++it) {
+      for (int k = 0; k < N; ++k) TRY(smoother_sweeps(c, c->zero_f, (char*)c->Z + (size_t)k * n * 8, 1, 1));
+      t_sweep += clk.lap();
+      TRY(orthonormalise(c, c->Z, N, n, P32));
+      t_orth += clk.lap();
+    }
+    TRY(blas_axpby2(P32, scal_all(1.0, N), c->Z, n, P64, scal_all(0.0, N), c->V64, n, n, N, c->s));
+  }
+  for (int it = 0; it < p.setup_iters && !f32; ++it) {
     for (int k = 0; k < N; ++k) {
       void* vk = (char*)c->V64 + (size_t)k * n * 16;
       if (c->vt == P64) {
@@ -1365,8 +1417,13 @@ static int setup_level0(mg_ctx* c) {
         TRY(blas_axpby2(P32, one, c->io_b, n, P64, zero, vk, n, n, 1, c->s));
       }
     }
+    t_sweep += clk.lap();
     TRY(orthonormalise(c, c->V64, N, n));
+    t_orth += clk.lap();
   }
+  if (p.verbose)
+    std::fprintf(stderr, "[sapmg] set-up part 1: %d sweeps of %d vectors %.3f s, orthonormalisation %.3f s\n",
+                 p.setup_iters, N, t_sweep, t_orth);
   if (p.n_levels == 3) {                   // the smoothed vectors start level 1 (restricted below)
     c->Vs64 = c->alloc((size_t)N * n * 16);
     if (!c->Vs64) return fail(MG_ERR_OOM, "set-up vectors");
@@ -1379,7 +1436,9 @@ static int setup_level0(mg_ctx* c) {
     SAPMG_CUDA_TRY(cudaMemcpyAsync((char*)V2 + (size_t)N * n * 16, c->V64, (size_t)N * n * 16,
                                    cudaMemcpyDeviceToDevice, c->s));
   }
+  clk.lap();
   TRY(build_level0_operators(c));
+  if (p.verbose) std::fprintf(stderr, "[sapmg] block Gram-Schmidt, P and D_c %.3f s\n", clk.lap());
   if (p.setup2_iters > 0 && p.n_levels == 2) {
     TRY(setup_part2(c, V2));
     SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
@@ -1641,7 +1700,9 @@ static int do_setup(mg_ctx* c, const double* U) {
     TRY(alloc_coarse_ws(c, c->c2, p.coarse_iters, R));
     TRY(alloc_fgmres1_ws(c, p.inner_iters, R));
   }
+  PhaseClock clk(c);
   if (p.autotune) TRY(autotune(c));
+  if (p.verbose && p.autotune) std::fprintf(stderr, "[sapmg] autotune %.3f s\n", clk.lap());
   SAPMG_CUDA_TRY(cudaStreamSynchronize(c->s));
   return MG_OK;
 }
@@ -1853,6 +1914,8 @@ static int setup_context(mg_ctx* c, const double* U, double c_sw, double m0, con
   c->dirac_pair = std::getenv("SAPMG_DIRAC_PAIR") ? std::atoi(std::getenv("SAPMG_DIRAC_PAIR")) : 1;
   c->graphs = std::getenv("SAPMG_GRAPHS") ? std::atoi(std::getenv("SAPMG_GRAPHS")) : 1;
   c->coarse_sap_mrhs = std::getenv("SAPMG_COARSE_SAP_MRHS") ? std::atoi(std::getenv("SAPMG_COARSE_SAP_MRHS")) : 1;
+  c->coarse_sap_fp16 = std::getenv("SAPMG_COARSE_SAP_FP16") ? std::atoi(std::getenv("SAPMG_COARSE_SAP_FP16")) : 1;
+  c->setup_fp32 = std::getenv("SAPMG_SETUP_FP32") ? std::atoi(std::getenv("SAPMG_SETUP_FP32")) : 1;
   c->xfer_batch = std::getenv("SAPMG_XFER_BATCH") ? std::max(1, std::atoi(std::getenv("SAPMG_XFER_BATCH"))) : 16;
   if (const char* ct = std::getenv("SAPMG_COARSE_TUNE")) {        // "batch,stages,ctas"
     int b = 16, st = 2, k = 0;

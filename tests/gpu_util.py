@@ -27,6 +27,12 @@ def rel(a, b):
     return float(np.linalg.norm((np.asarray(a) - np.asarray(b)).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
 
 
+def emax(a, b):
+    """Element-wise: max |a - b| / max |b| (one wrong element shows at any size)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
 def round_storage(x, prec):
     """Round every real component as the library stores it: double -> float -> half/bf16."""
     import torch as _t

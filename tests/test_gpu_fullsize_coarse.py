@@ -12,7 +12,9 @@ a CTA, sites from 7296 on are in the last stride).
   own parity is checked at small size) and compares its nine 40 x 40 blocks
   at the centre with the library's FP64 D_c.  The centre aggregate's
   couplings involve only links, clover and vectors inside the patch's
-  interior, so the patch wrap does not reach them.
+  interior, so the patch wrap does not reach them.  The mixed form
+  assembles D_c in FP32 arithmetic (it stores and applies it in FP32 and
+  FP16), so the entries agree to FP32 accuracy, 5e-6 of the largest.
 * Restriction P^dagger and interpolation P (Sec. 3) of 12 FP32 vectors at
   once (the cycle's batched tensor-core transfers, TF32 inputs): against the
   oracle's transfers with the FP16-rounded P and TF32-rounded vectors on the
@@ -113,7 +115,7 @@ def test_fullsize_coarse_operator_sampled_sites(big):
             ref += [op.fwd[mu][1, 1, 1, 1], op.bwd[mu][1, 1, 1, 1]]
         ref = np.stack(ref)
         got = host(m[a])
-        assert _maxrel(got, ref) < 1e-11, (a, _maxrel(got, ref))
+        assert _maxrel(got, ref) < 5e-6, (a, _maxrel(got, ref))
 
 
 def _rhs(dims, seed):
