@@ -281,8 +281,8 @@ int mg_coarse_solve(mg_ctx* ctx, int level, const void* in, void* out, int prec)
  * inside the library's own device memory (every device that loads the library
  * holds it until the process exits); the result is written straight to `out`,
  * which starts from zero.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  Every call shares the one array,
+ * device address (cudaGetSymbolAddress) with the device current.  Every call
+ * shares the one array,
  * which keeps the previous call's contents, so calls that overlap on the GPU
  * (other streams, other contexts on the same device) race: serialise them.
  * Two-level contexts only (level 1 is then the coarsest level, solved by
