@@ -61,6 +61,13 @@ extern "C" {
 /* OR-ed into dirac_apply's prec: apply D^dagger = gamma5 D gamma5 instead of D
  * (MG_FP64 or MG_FP32 only). */
 #define MG_DAGGER 0x200
+/* OR-ed into dirac_apply's prec with MG_FP64 (not with MG_DAGGER): the same
+ * FP64 operator on FP64 data, with the arithmetic in double-float (pairs of
+ * FP32 numbers, about 48 significand bits) on the FP32 units.  Measured
+ * slower than the FP64 units on GB300 (96 against 51 ms for 12 right-hand
+ * sides at 32^3 x 64), so the solver does not use it unless the environment
+ * sets SAPMG_FP64_ON_FP32=1. */
+#define MG_FP64_ON_FP32 0x400
 
 typedef struct mg_ctx mg_ctx;
 

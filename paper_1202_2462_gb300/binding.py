@@ -27,6 +27,7 @@ MG_FP16 = 2
 MG_BF16 = 3
 MG_BLOCKED = 0x100
 MG_DAGGER = 0x200
+MG_FP64_ON_FP32 = 0x400
 
 PRECISIONS = {"fp64": MG_FP64, "fp32": MG_FP32, "fp16": MG_FP16, "bf16": MG_BF16}
 

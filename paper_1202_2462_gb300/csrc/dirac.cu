@@ -7,6 +7,7 @@
 // folded into the stored links.
 #include "internal.h"
 #include "stencil.cuh"
+#include "dfloat.cuh"
 
 namespace sapmg {
 
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 3 : 1)) dirac_kernel(TS
 #pragma unroll
   for (int c = 0; c < 12; ++c) acc[c] = (R)(-0.5) * acc[c];
   store_spinor<R>(out, blk, loc, acc);
-  if (NORM) {
+  if constexpr (NORM) {
     __shared__ double ws[8];
     R t = 0;
 #pragma unroll
@@ -81,6 +82,10 @@ int launch_dirac_ex(int prec, const Geom& g, void* out, const void* in, const vo
                     bool dag, double* part, cudaStream_t s) {
   switch (prec) {
     case P64: run_ex<double, double2, double2>(g, out, in, U, A, nrhs, dag, part, s); break;
+    case P64E:                             // FP64 data, double-float arithmetic (dfloat.cuh)
+      if (dag || part) return MG_ERR_ARG;
+      run<DF, double2, double2, false, false>(g, out, in, U, A, nrhs, nullptr, s);
+      break;
     case P32: run_ex<float, float2, float2>(g, out, in, U, A, nrhs, dag, part, s); break;
     case P16:
       if (dag || part) return MG_ERR_ARG;

@@ -11,6 +11,8 @@ namespace sapmg {
 
 // Storage precisions of fields; equal to the public MG_FP64 ... MG_BF16.
 enum { P64 = MG_FP64, P32 = MG_FP32, P16 = MG_FP16, PBF = MG_BF16 };
+// FP64 data with double-float arithmetic on the FP32 units (dirac.cu only)
+enum { P64E = 16 };
 
 inline size_t complex_bytes(int prec) { return prec == P64 ? 16 : (prec == P32 ? 8 : 4); }
 // Krylov basis vectors kept in FP16 are stored multiplied by this power of two

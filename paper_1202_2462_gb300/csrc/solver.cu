@@ -152,6 +152,7 @@ struct mg_ctx {
   int coarse_sap_mrhs = 1; // level-1 Schwarz with all RHS per CTA (SAPMG_COARSE_SAP_MRHS=0: one RHS per CTA)
   int coarse_sap_fp16 = 1; // level-1 Schwarz reads the FP16 operator copy (SAPMG_COARSE_SAP_FP16=0: FP32)
   int setup_fp32 = 1;      // mixed form: set-up part 1 on FP32 vectors (SAPMG_SETUP_FP32=0: FP64 vectors)
+  int fp64_on_fp32 = 0;    // mixed form: FP64 residuals in double-float arithmetic (SAPMG_FP64_ON_FP32=1; slower)
   cudaStream_t cap_s = nullptr;            // stream the coarse-solve graphs are captured on
   cudaGraphExec_t cgraph[3][33] = {};      // [level][right-hand sides]: the captured fixed-step coarse GMRES
   int cgraph_kernels[3][33] = {};          // kernels in each graph (for the launch counter)
@@ -267,12 +268,14 @@ static int smoother_sweeps(mg_ctx* c, const void* b, void* z, int n_sweeps, int 
 }
 
 static int fine_dirac(mg_ctx* c, int prec, void* out, const void* in, int nrhs) {
-  const void* U = prec == P64 ? c->U64 : (prec == P32 ? c->U32 : c->Us);
-  const void* A = prec == P64 ? c->A64 : (prec == P32 ? c->A32 : c->As);
+  const bool f64 = prec == P64 || prec == P64E;
+  const void* U = f64 ? c->U64 : (prec == P32 ? c->U32 : c->Us);
+  const void* A = f64 ? c->A64 : (prec == P32 ? c->A32 : c->As);
   if (!U || !A) return fail(MG_ERR_STATE, "requested precision not set up in this context");
   ProfScope ps(c->prof, FAM_DIRAC, c->s);
-  count_bytes((double)c->g.V * (nrhs * 2 * 12 * vec_bytes(prec) + fields_bytes(prec)));
-  if (c->dirac_pair && prec != P64 && nrhs >= 2 && nrhs % 2 == 0)
+  const int bp = f64 ? P64 : prec;
+  count_bytes((double)c->g.V * (nrhs * 2 * 12 * vec_bytes(bp) + fields_bytes(bp)));
+  if (c->dirac_pair && !f64 && nrhs >= 2 && nrhs % 2 == 0)
     return launch_dirac_pair(prec, c->g, out, in, U, A, nrhs, c->s);
   return launch_dirac(prec, c->g, out, in, U, A, nrhs, c->s);
 }
@@ -931,7 +934,7 @@ static int solve_batch(mg_ctx* c, int R, int& iters, int& restarts, double& relr
     for (int q = 0; q < R; ++q) step = std::max(step, done[q]);
     iters += step;
     restarts += 1;
-    TRY(fine_dirac(c, P64, c->r64, c->x64, R));
+    TRY(fine_dirac(c, c->fp64_on_fp32 ? P64E : P64, c->r64, c->x64, R));
     BLAS(blas_axpby2(P64, one, c->b64, n, P64, minus, c->r64, n, n, R, c->s));
     if (step == 0) return MG_NOT_CONVERGED;
   }
@@ -1916,6 +1919,7 @@ static int setup_context(mg_ctx* c, const double* U, double c_sw, double m0, con
   c->coarse_sap_mrhs = std::getenv("SAPMG_COARSE_SAP_MRHS") ? std::atoi(std::getenv("SAPMG_COARSE_SAP_MRHS")) : 1;
   c->coarse_sap_fp16 = std::getenv("SAPMG_COARSE_SAP_FP16") ? std::atoi(std::getenv("SAPMG_COARSE_SAP_FP16")) : 1;
   c->setup_fp32 = std::getenv("SAPMG_SETUP_FP32") ? std::atoi(std::getenv("SAPMG_SETUP_FP32")) : 1;
+  c->fp64_on_fp32 = c->vt == P32 && std::getenv("SAPMG_FP64_ON_FP32") && std::atoi(std::getenv("SAPMG_FP64_ON_FP32"));
   c->xfer_batch = std::getenv("SAPMG_XFER_BATCH") ? std::max(1, std::atoi(std::getenv("SAPMG_XFER_BATCH"))) : 16;
   if (const char* ct = std::getenv("SAPMG_COARSE_TUNE")) {        // "batch,stages,ctas"
     int b = 16, st = 2, k = 0;
@@ -2072,8 +2076,10 @@ int dirac_apply(mg_ctx* c, const void* in, void* out, int prec, int nrhs) {
   if (!c || !in || !out || nrhs < 1) return fail(MG_ERR_ARG, "bad argument");
   const bool blocked = (prec & MG_BLOCKED) != 0;
   const bool dag = (prec & MG_DAGGER) != 0;
+  const bool emul = (prec & MG_FP64_ON_FP32) != 0;
   prec &= 0xff;
   if (prec < MG_FP64 || prec > MG_BF16) return fail(MG_ERR_ARG, "unknown precision");
+  if (emul && (prec != MG_FP64 || dag)) return fail(MG_ERR_ARG, "MG_FP64_ON_FP32 goes with MG_FP64 and without MG_DAGGER");
   if (dag && prec != MG_FP64 && prec != MG_FP32) return fail(MG_ERR_ARG, "D^dagger is applied in MG_FP64 or MG_FP32");
   if (dag && prec == MG_FP32 && !c->U32) return fail(MG_ERR_STATE, "requested precision not set up in this context");
   if (!blocked && nrhs > c->p.nrhs_max) return fail(MG_ERR_ARG, "nrhs exceeds nrhs_max for canonical layout");
@@ -2084,7 +2090,7 @@ int dirac_apply(mg_ctx* c, const void* in, void* out, int prec, int nrhs) {
   if (dag)
     TRY(cgn_dirac(c, prec, dst, src, nrhs, true, nullptr));
   else
-    TRY(fine_dirac(c, prec, dst, src, nrhs));
+    TRY(fine_dirac(c, emul ? P64E : prec, dst, src, nrhs));
   if (!blocked) TRY(launch_unpack_spinor(t, dst, t, out, c->g, nrhs, c->s));
   return MG_OK;
 }

@@ -34,6 +34,32 @@ def test_dirac_fp64_parity(dims, eps, m0, ap):
 
 
 @pytest.mark.parametrize("dims,eps,m0,ap", CASES)
+def test_dirac_fp64_on_fp32_units_parity(dims, eps, m0, ap):
+    """MG_FP64_ON_FP32: the FP64 operator on FP64 data with double-float
+    arithmetic (about 48 significand bits) against the oracle, element by
+    element, and against the native FP64 kernel; an odd number of
+    right-hand sides, and the flag refused with D^dagger or a non-FP64
+    precision."""
+    torch = torch_cuda()
+    import paper_1202_2462_gb300 as G
+    u = synth.random_gauge_field(dims, eps, 15)
+    op = WilsonClover(u, m0, 1.0, antiperiodic_t=ap)
+    psi = synth.random_spinor(dims, 16, nvec=3)
+    ref = op.apply(psi)
+    s = _solver(torch, u, 1.0, m0, ap, nrhs_max=3, precision="bf16")
+    x = dev(torch, psi)
+    out = host(s.dirac(x, G.MG_FP64 | G.MG_FP64_ON_FP32))
+    nat = host(s.dirac(x, G.MG_FP64))
+    for bad in (G.MG_FP64 | G.MG_FP64_ON_FP32 | G.MG_DAGGER, G.MG_FP32 | G.MG_FP64_ON_FP32):
+        with pytest.raises(G.MgError) as e:
+            s.dirac(x, bad)
+        assert e.value.code == G.MG_ERR_ARG
+    s.close()
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(out - nat)) < 1e-12 * np.max(np.abs(nat))
+
+
+@pytest.mark.parametrize("dims,eps,m0,ap", CASES)
 def test_dirac_fp32_parity(dims, eps, m0, ap):
     """FP32 storage and arithmetic: <= 1e-5 relative against the exact FP64 operator."""
     torch = torch_cuda()
