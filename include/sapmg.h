@@ -281,8 +281,8 @@ int mg_coarse_solve(mg_ctx* ctx, int level, const void* in, void* out, int prec)
 /* The coarse solve of mg_coarse_solve without any device allocation.
  * The paper has no counterpart: this entry point is for callers that cannot
  * call cudaMalloc at the time they solve -- code running under an allocator
- * that forbids new device memory (a memory pool sized up front, or a budget
- * that another framework owns), or on a real-time path where an allocation's
+ * that forbids new device memory (a memory pool sized up front, or an
+ * allowance that another framework owns), or on a real-time path where an allocation's
  * implicit synchronisation or its failure is not acceptable.  Its Krylov
  * basis, Hessenberg matrix and reduction partials live in a fixed 8 MiB array
  * inside the library's own device memory (every device that loads the library

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 2 : 1))
 #pragma unroll
     for (int c = 0; c < 12; ++c) p[c] = (R)(-2) * p[c];
     // the empty asm statements keep the compiler from hoisting the next
-    // direction's loads (which would raise register pressure past the budget)
+    // direction's loads (which would raise register pressure past the limit)
     block_hops_dir<0>(U, rs, blk, loc, p);
     asm volatile("" ::: "memory");
     block_hops_dir<1>(U, rs, blk, loc, p);

@@ -5,8 +5,8 @@
 //
 // The layout and the steps are those of the solve's Schwarz pass
 // (r = b - (D - lambda) z on the block, n_MR MR steps with D_j - lambda, z += e);
-// it runs a few times per set-up, so it is written plainly (no register
-// budget tuning) and kept apart from the solve's kernel.
+// it runs a few times per set-up, so it is written plainly (no tuning of
+// its register use) and kept apart from the solve's kernel.
 #include "internal.h"
 #include "stencil.cuh"
 
