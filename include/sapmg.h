@@ -136,7 +136,10 @@ int mg_default_params(mg_params* p);
  * fine level, smoothed by S(lambda), merged with the part-1 vectors by the
  * (DV)^dagger DV reduction; P and D_c rebuilt; with three levels, level 1 is
  * then rebuilt from the new vectors as part 1 builds it), and allocates all
- * solve workspace.  Synchronises.  *out receives the context.
+ * solve workspace.  The plain form does all of this in FP64; the mixed form
+ * keeps the test vectors FP32 through the part-1 sweeps and their global
+ * Gram-Schmidt and assembles the level-1 D_c in FP32 arithmetic (the local
+ * orthonormalisation stays FP64).  Synchronises.  *out receives the context.
  * Errors: MG_ERR_ARG (dims, params), MG_ERR_NONFINITE (U), MG_ERR_OOM, MG_ERR_CUDA. */
 int mg_setup(const double* U, double c_sw, double m0, const mg_params* p, mg_ctx** out);
 
