@@ -194,9 +194,10 @@ static int coarse_sap_t(const CGeom& c, const Box4& bx, const void* M, void* z, 
 // from memory.  Per right-hand side every sum runs in the order of the kernel
 // above (the same residual and MR sums, the same block reduction), so the two
 // give the same results bit for bit.  rho and e in shared memory as
-// [box site][n2][NR]; NR >= nrhs, a compile-time bound on the right-hand sides.
-template <int NR, class TM>
-__global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const TM* __restrict__ M, float2* __restrict__ z,
+// [box site][n2][NR]; NR >= nrhs, an even compile-time bound on the right-hand
+// sides.
+template <int NR, class TM, int MAXT>
+__global__ void __launch_bounds__(MAXT) coarse_sap_mrhs_kernel(const TM* __restrict__ M, float2* __restrict__ z,
                                                                const float2* __restrict__ b, CGeom c, Box4 bx,
                                                                int colour, int n_mr, int nrhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -247,9 +248,12 @@ __global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const TM* __restr
   }
   for (int it = 0; it < n_mr; ++it) {
     __syncthreads();
-    Cplx<float> p[NR];
+    // p = D_box rho: the right-hand sides in pairs, each FMA the packed two-wide
+    // FP32 instruction (lane by lane the cfma of the kernel above: the same
+    // products in the same order), the pair's rho read as one 16-byte word
+    float2 pre[NR / 2], pim[NR / 2];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) p[r] = cmk(0.f, 0.f);
+    for (int q = 0; q < NR / 2; ++q) { pre[q] = make_float2(0.f, 0.f); pim[q] = make_float2(0.f, 0.f); }
     if (act) {
       for (int d = 0; d < 9; ++d) {
         int ln = s;
@@ -262,13 +266,28 @@ __global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const TM* __restr
           ln = s + step * stride;
         }
         const TM* m = M + (((size_t)site * 9 + d) * n2) * n2 + i;
-        const Cplx<float>* rn = rs + (size_t)ln * n2 * NR;
+        const float4* rn = reinterpret_cast<const float4*>(rs + (size_t)ln * n2 * NR);
         for (int j = 0; j < n2; ++j) {
           const Cplx<float> mv = Io<float, TM>::ld(m + (size_t)j * n2);
+          const float2 mr = make_float2(mv.re, mv.re), mi = make_float2(mv.im, mv.im);
+          const float2 nmi = make_float2(-mv.im, -mv.im);
 #pragma unroll
-          for (int r = 0; r < NR; ++r) cfma(p[r], mv, rn[j * NR + r]);
+          for (int q = 0; q < NR / 2; ++q) {
+            const float4 x = rn[j * (NR / 2) + q];                // (re_r, im_r, re_r+1, im_r+1)
+            const float2 xre = make_float2(x.x, x.z), xim = make_float2(x.y, x.w);
+            pre[q] = __ffma2_rn(mr, xre, pre[q]);
+            pre[q] = __ffma2_rn(nmi, xim, pre[q]);
+            pim[q] = __ffma2_rn(mr, xim, pim[q]);
+            pim[q] = __ffma2_rn(mi, xre, pim[q]);
+          }
         }
       }
+    }
+    Cplx<float> p[NR];
+#pragma unroll
+    for (int q = 0; q < NR / 2; ++q) {
+      p[2 * q] = cmk(pre[q].x, pim[q].x);
+      p[2 * q + 1] = cmk(pre[q].y, pim[q].y);
     }
     // block sums, per right-hand side as block_reduce_n forms them
 #pragma unroll
@@ -306,6 +325,24 @@ __global__ void __launch_bounds__(1024) coarse_sap_mrhs_kernel(const TM* __restr
       }
 }
 
+// MAXT: the block size the kernel is compiled for (768 leaves 85 registers a
+// thread, enough for 12 right-hand sides without spills; 1024 for 2N > 48)
+template <int NR, class TM, int MAXT>
+static int coarse_sap_mrhs_launch(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b,
+                                  int colour, int n_mr, int nrhs, cudaStream_t s, int threads, size_t smem) {
+  static bool attr = false;
+  if (!attr) {
+    SAPMG_CUDA_TRY(cudaFuncSetAttribute(coarse_sap_mrhs_kernel<NR, TM, MAXT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  coarse_sap_mrhs_kernel<NR, TM, MAXT><<<(unsigned)(bx.nboxes / 2), threads, smem, s>>>(
+      (const TM*)M, (float2*)z, (const float2*)b, c, bx, colour, n_mr, nrhs);
+  count_launches(1);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+}
+
 template <int NR, class TM>
 static int coarse_sap_mrhs_t(const CGeom& c, const Box4& bx, const void* M, void* z, const void* b, int colour,
                              int n_mr, int nrhs, cudaStream_t s) {
@@ -313,17 +350,8 @@ static int coarse_sap_mrhs_t(const CGeom& c, const Box4& bx, const void* M, void
   if (threads > 1024 || nrhs > NR) return MG_ERR_ARG;
   const size_t smem = sizeof(Cplx<float>) * 2 * bx.sites * c.n2 * NR + sizeof(float) * 3 * NR * 32;
   if (smem > 227 * 1024) return MG_ERR_ARG;
-  static bool attr = false;
-  if (!attr) {
-    SAPMG_CUDA_TRY(cudaFuncSetAttribute(coarse_sap_mrhs_kernel<NR, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        227 * 1024));
-    attr = true;
-  }
-  coarse_sap_mrhs_kernel<NR, TM><<<(unsigned)(bx.nboxes / 2), threads, smem, s>>>(
-      (const TM*)M, (float2*)z, (const float2*)b, c, bx, colour, n_mr, nrhs);
-  count_launches(1);
-  SAPMG_CUDA_TRY(cudaGetLastError());
-  return MG_OK;
+  return threads <= 768 ? coarse_sap_mrhs_launch<NR, TM, 768>(c, bx, M, z, b, colour, n_mr, nrhs, s, threads, smem)
+                        : coarse_sap_mrhs_launch<NR, TM, 1024>(c, bx, M, z, b, colour, n_mr, nrhs, s, threads, smem);
 }
 
 template <class TM>
