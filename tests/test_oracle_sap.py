@@ -65,42 +65,56 @@ def test_mr_converges_to_dense_lu(setting):
 def test_sap_error_propagator_dense(setting):
     """One sweep with exact block solves: e_new = (1 - B_1 D)(1 - B_0 D) e_old, and
     this equals the multiplicative Schwarz product over all blocks of Eq. 2.1 taken
-    colour by colour (same-coloured factors commute)."""
+    colour by colour (same-coloured factors commute).  Both operators are applied
+    to random probe vectors, built from the dense D and dense block inverses: a
+    matrix difference that vanishes on random probes vanishes with probability 1."""
     op, bl, dense_blocks, d = setting
     n = d.shape[0]
-    bsum = []
-    singles = []
-    for c in (0, 1):
-        bc = np.zeros((n, n), dtype=np.complex128)
-        for blk, (cols, mat) in dense_blocks[c].items():
-            bi = np.zeros((n, n), dtype=np.complex128)
-            bi[np.ix_(cols, cols)] = np.linalg.inv(mat)
-            bc += bi
-            singles.append(bi)
-        bsum.append(bc)
-    eye = np.eye(n)
-    prop = (eye - bsum[1] @ d) @ (eye - bsum[0] @ d)
-    mult = eye
-    for bi in singles:                       # colour 0 blocks first, then colour 1
-        mult = (eye - bi @ d) @ mult
-    assert np.max(np.abs(prop - mult)) < 1e-11
+    inv = [[(np.asarray(cols), np.linalg.inv(mat)) for cols, mat in dense_blocks[c].values()]
+           for c in (0, 1)]
+
+    def colour_factor(c, x):                 # (1 - B_c D) x, B_c the colour-c block sum
+        r = d @ x
+        y = x.copy()
+        for cols, bi in inv[c]:
+            y[cols] -= bi @ r[cols]
+        return y
+
+    def prop(x):
+        return colour_factor(1, colour_factor(0, x))
+
+    def mult(x):                             # colour 0 blocks first, then colour 1
+        for c in (0, 1):
+            for cols, bi in inv[c]:
+                x = x.copy()
+                x[cols] -= bi @ (d[cols] @ x)
+        return x
+
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal((n, 8)) + 1j * rng.standard_normal((n, 8))
+    pv = prop(v)
+    assert np.max(np.abs(pv - mult(v))) < 1e-11 * np.max(np.abs(pv))
+    assert np.max(np.abs(pv - v)) > 0.1 * np.max(np.abs(v))    # the factor is not the identity
     b = synth.random_spinor(DIMS, 4)
     z0 = synth.random_spinor(DIMS, 5)
     xs = np.linalg.solve(d, b.ravel())
     z1 = sap_sweep(op, bl, b, z0, 0, exact=dense_blocks)
-    assert np.max(np.abs((z1.ravel() - xs) - prop @ (z0.ravel() - xs))) < 1e-11
+    assert np.max(np.abs((z1.ravel() - xs) - prop(z0.ravel() - xs))) < 1e-11
 
 
 def test_same_colour_blocks_independent(setting):
+    """B_1 D B_2 D = 0 for two blocks of one colour.  B_i is the inverse of the
+    block's diagonal part embedded at its rows and columns, so the product's only
+    nonzero rows are block 1's: inv(D_11) D_12 inv(D_22) D[block 2 rows, :]."""
     op, bl, dense_blocks, d = setting
-    n = d.shape[0]
     items = list(dense_blocks[0].items())
     (c1, m1), (c2, m2) = items[0][1], items[1][1]
-    b1 = np.zeros((n, n), dtype=np.complex128)
-    b2 = np.zeros((n, n), dtype=np.complex128)
-    b1[np.ix_(c1, c1)] = np.linalg.inv(m1)
-    b2[np.ix_(c2, c2)] = np.linalg.inv(m2)
-    assert np.max(np.abs(b1 @ d @ b2 @ d)) < 1e-12
+    c1, c2 = np.asarray(c1), np.asarray(c2)
+    prod = np.linalg.inv(m1) @ d[np.ix_(c1, c2)] @ np.linalg.inv(m2) @ d[c2]
+    assert np.max(np.abs(prod)) < 1e-12
+    # the blocks of the other colour do touch block 1
+    touching = [np.max(np.abs(d[np.ix_(c1, np.asarray(c))])) for c, _ in dense_blocks[1].values()]
+    assert max(touching) > 0.1
 
 
 def test_mr_step_matches_definition_on_one_block(setting):
