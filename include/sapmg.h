@@ -47,6 +47,7 @@ extern "C" {
 #define MG_ERR_CUDA (-4)      /* a CUDA call failed; see mg_last_error() */
 #define MG_ERR_TIMEOUT (-5)   /* a bounded device wait gave up */
 #define MG_ERR_STATE (-6)     /* the call needs a part the context was not set up with */
+#define MG_ERR_BOUNDS (-7)    /* MG_DEBUG builds only: a device-side index check failed */
 
 /* Precisions.  MG_FP64: storage and arithmetic in binary64 (the plain form).
  * MG_FP32 / MG_FP16 / MG_BF16: binary32 arithmetic with links, clover blocks,
@@ -398,8 +399,30 @@ int mg_get_history(mg_ctx* ctx, double* out, int max_entries);
 /* Wait for the context's stream and report a device-side wait that gave up
  * since the last check (MG_ERR_TIMEOUT; the flag is then cleared).  The
  * asynchronous entry points (sap_smooth, dirac_apply, the transfers) leave
- * such a flag for the next synchronising call; this one only checks it. */
+ * such a flag for the next synchronising call; this one only checks it.
+ * In an MG_DEBUG build the synchronising calls also report a failed
+ * device-side index check (MG_ERR_BOUNDS, see mg_debug_failures). */
 int mg_sync(mg_ctx* ctx);
+
+/* The MG_DEBUG build (libsapmg_debug.so, compiled with -DMG_DEBUG) checks in
+ * its kernels the indices they compute -- neighbour sites and blocks, the
+ * blocks of a colour, coarse sites and their neighbours, aggregates, kernel
+ * block indices -- and the 16-byte alignment of every bulk copy.  A failed
+ * check never traps: it is recorded on the device and the kernel carries on
+ * with index 0 (or skips the copy), so results are then wrong but every
+ * barrier and wait behaves as in the release build.  This call synchronises
+ * the device and returns the number of failed checks since the previous call
+ * (clearing them), with mg_last_error() describing the first one (file, kind,
+ * value, source line); MG_ERR_CUDA if the records cannot be read.  In the
+ * release build (libsapmg.so) it returns -1: no checks are compiled. */
+long long mg_debug_failures(void);
+
+/* MG_DEBUG build: one device-side check of value against [0, bound) in a
+ * one-thread kernel that touches no memory (a failure is recorded as a
+ * "block" check of solver.cu), for tests of the reporting path.
+ * Asynchronous on the legacy default stream; MG_OK.  Release build:
+ * MG_ERR_STATE. */
+int mg_debug_check(long long value, long long bound);
 
 /* Bound on the main-loop waits of the kernels that stage data with bulk
  * copies (the coarse stencils, the block-resident Schwarz pass): a wait that

@@ -2,7 +2,10 @@
 
 Each translation unit compiles in parallel to an object under ``_build/``; the
 objects are linked into ``libsapmg.so`` next to this file.  Only sources whose
-object is older than the source (or any header) are recompiled.
+object is older than the source (or any header) are recompiled.  With
+debug=True (``python -m paper_1202_2462_gb300._build --debug``) the same
+sources are compiled with -DMG_DEBUG, the device-side index checks, into
+``_build_debug/`` and ``libsapmg_debug.so``.
 """
 
 import concurrent.futures
@@ -16,6 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsapmg.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libsapmg_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -35,8 +40,8 @@ def _newest_header():
     return max(os.path.getmtime(h) for h in hs)
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, extra, build_dir):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     newest = max(os.path.getmtime(src), _newest_header())
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj, ""
@@ -47,24 +52,28 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(verbose=False, extra=()):
-    """Compile every CUDA source and link libsapmg.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, extra=(), debug=False):
+    """Compile every CUDA source and link libsapmg.so (libsapmg_debug.so with
+    debug=True); returns the library path."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    flags = list(extra) + (["-DMG_DEBUG"] if debug else [])
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
+        results = list(ex.map(lambda s: _compile(s, flags, build_dir), srcs))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:
             if log:
                 print(log)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [_nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", LIB] + objs
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        cmd = [_nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", lib] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True))
+    import sys
+    print(build(verbose=True, debug="--debug" in sys.argv[1:]))

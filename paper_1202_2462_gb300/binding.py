@@ -3,14 +3,17 @@
 Every function here has the name of the C entry point it calls and takes the
 same arguments, with torch tensors accepted wherever the C side takes a device
 pointer.  All computation happens in libsapmg.so; if the library is missing or
-cannot be loaded the first call raises, there is no fallback.
+cannot be loaded the first call raises, there is no fallback.  With
+SAPMG_LIBRARY=debug in the environment the binding loads libsapmg_debug.so,
+the build with device-side index checks (mg_debug_failures).
 """
 
 import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsapmg.so")
+LIB_PATH = os.path.join(HERE, "libsapmg_debug.so" if os.environ.get("SAPMG_LIBRARY") == "debug"
+                        else "libsapmg.so")
 
 MG_OK = 0
 MG_NOT_CONVERGED = 1
@@ -20,6 +23,7 @@ MG_ERR_OOM = -3
 MG_ERR_CUDA = -4
 MG_ERR_TIMEOUT = -5
 MG_ERR_STATE = -6
+MG_ERR_BOUNDS = -7
 
 MG_FP64 = 0
 MG_FP32 = 1
@@ -108,6 +112,8 @@ _SIGNATURES = {
     "mg_reset_profile": (_I, [_VP]),
     "mg_launch_count": (ctypes.c_longlong, []),
     "mg_sync": (_I, [_VP]),
+    "mg_debug_failures": (ctypes.c_longlong, []),
+    "mg_debug_check": (_I, [ctypes.c_longlong, ctypes.c_longlong]),
     "mg_get_history": (_I, [_VP, _VP, _I]),
     "mg_get_tuning": (_I, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "mg_set_wait_limit": (_I, [_VP, _I]),
@@ -131,7 +137,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build(), the "
+                               "MG_DEBUG variant with python -m paper_1202_2462_gb300._build --debug "
                                "(there is no CPU fallback)")
         handle = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in _SIGNATURES.items():
@@ -371,6 +378,17 @@ def mg_get_history(ctx):
 
 def mg_sync(ctx):
     return _check(lib().mg_sync(ctx), "mg_sync")
+
+
+def mg_debug_failures():
+    """Failed device-side index checks since the previous call (MG_DEBUG
+    build), or -1 for the release build."""
+    n = lib().mg_debug_failures()
+    return _check(n, "mg_debug_failures") if n < -1 else n
+
+
+def mg_debug_check(value, bound):
+    return _check(lib().mg_debug_check(value, bound), "mg_debug_check")
 
 
 def mg_set_wait_limit(ctx, spins):

@@ -5,6 +5,8 @@
 #pragma once
 #include <stdint.h>
 
+#include "debug.cuh"
+
 namespace sapmg {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -19,7 +21,21 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// Completes `bytes` of the barrier's expected transactions without a copy.
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+#ifdef MG_DEBUG
+  // both addresses and the size must be multiples of 16 bytes; a copy that is
+  // not is skipped and its bytes completed by hand, so the wait still ends
+  const uint32_t bad = (smem_u32(dst) | (uint32_t)reinterpret_cast<uintptr_t>(src) | bytes) & 15u;
+  if (!MG_CHECK(kBulkCopy, bad, 1)) {
+    mbar_complete_tx(bar, bytes);
+    return;
+  }
+#endif
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))

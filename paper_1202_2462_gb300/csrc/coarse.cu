@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256) restrict0_kernel(const TS* __restrict__ i
                                                         const TV* __restrict__ Pv, int N, int nrhs, int nblocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R (*red)[4] = reinterpret_cast<R (*)[4]>(smem_raw);        // [8 * N][4]
-  const int blk = blockIdx.x / nrhs, rhs = blockIdx.x % nrhs, loc = threadIdx.x;
+  const int blk = MG_CLAMP(kAggregate, blockIdx.x / nrhs, nblocks), rhs = blockIdx.x % nrhs, loc = threadIdx.x;
   const int wid = loc >> 5, lane = loc & 31;
   const size_t off = (size_t)rhs * nblocks * 12 * 256;       // rhs stride (one field)
   Cplx<R> r[12];
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) prolong0_kernel(const TC* __restrict__ in
                                                        const TV* __restrict__ Pv, int N, int nrhs, int nblocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<R>* e = reinterpret_cast<Cplx<R>*>(smem_raw);             // [2N]
-  const int blk = blockIdx.x / nrhs, rhs = blockIdx.x % nrhs, loc = threadIdx.x;
+  const int blk = MG_CLAMP(kAggregate, blockIdx.x / nrhs, nblocks), rhs = blockIdx.x % nrhs, loc = threadIdx.x;
   const int n2 = 2 * N;
   const TC* ein = in + (size_t)rhs * nblocks * n2 + (size_t)blk * n2;
   for (int t = loc; t < n2; t += 256) e[t] = Io<R, TC>::ldc(ein + t);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) restrict0_mrhs_kernel(const float2* __res
   // chirality) run back to back and share its P rows through L2
   const int ngrp = (nrhs + RG - 1) / RG;
   const int r0 = (blockIdx.x % ngrp) * RG;
-  const int blk = blockIdx.x / ngrp / 2, chi = (blockIdx.x / ngrp) % 2;
+  const int blk = MG_CLAMP(kAggregate, blockIdx.x / ngrp / 2, nblocks), chi = (blockIdx.x / ngrp) % 2;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const size_t fs = (size_t)nblocks * 12 * 256;
   const int rg = min(RG, nrhs - r0);
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) prolong0_mrhs_kernel(const float2* __rest
                                                             int nblocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* es = reinterpret_cast<float2*>(smem_raw);              // [nrhs][N] of this chirality
-  const int blk = blockIdx.x, c = blockIdx.y, loc = threadIdx.x;
+  const int blk = MG_CLAMP(kAggregate, blockIdx.x, nblocks), c = blockIdx.y, loc = threadIdx.x;
   const int chi = c / 6, n2 = 2 * N;
   for (int e = loc; e < nrhs * N; e += 256) {
     const int r = e / N, k = e % N;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) restrict0_mma_kernel(const float2* __rest
   constexpr size_t STAGE = restrict_stage_bytes<TV>();
   auto sP = [&](int st) { return reinterpret_cast<TV*>(smem_raw + st * STAGE); };
   auto sX = [&](int st) { return reinterpret_cast<float2*>(smem_raw + st * STAGE + PB); };
-  const int blk = blockIdx.x >> 1, chi = blockIdx.x & 1;
+  const int blk = MG_CLAMP(kAggregate, blockIdx.x >> 1, nblocks), chi = blockIdx.x & 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, tig = lane & 3, p1 = tig & 1;
   const size_t fs = (size_t)nblocks * 12 * 256;
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256) prolong0_mma_kernel(const float2* __restr
   const size_t PB = prolong_stage_bytes<TV>(Np);
   auto sP = [&](int st) { return reinterpret_cast<TV*>(smem_raw + st * PB); };
   float* eb = reinterpret_cast<float*>(smem_raw + kRStages * PB);   // [2 Np][16]
-  const int blk = blockIdx.x >> 1, chi = blockIdx.x & 1;
+  const int blk = MG_CLAMP(kAggregate, blockIdx.x >> 1, nblocks), chi = blockIdx.x & 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, tig = lane & 3, a = g & 1;
   const size_t fs = (size_t)nblocks * 12 * 256;
@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(256) assemble0_kernel(const T2* __restrict__ V
                                                         Geom g, int N) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double (*red)[4] = reinterpret_cast<double (*)[4]>(smem_raw);   // [8 * N][4]
-  const int blk = blockIdx.x, j = blockIdx.y, loc = threadIdx.x;
+  const int blk = MG_CLAMP(kAggregate, blockIdx.x, g.nblocks), j = blockIdx.y, loc = threadIdx.x;
   const int n2 = 2 * N, chi_p = j / N, k = j % N;
   const int wid = loc >> 5, lane = loc & 31;
   const long long fs = g.V * 12;
@@ -762,7 +762,7 @@ __device__ __forceinline__ int cg_neighbour(const CGeom& c, int site, int d) {
   for (int m = 0; m < mu; ++m) stride *= c.L[m];
   const int x = (site / stride) % c.L[mu];
   const int nx = (x + step + c.L[mu]) % c.L[mu];
-  return site + (nx - x) * stride;
+  return MG_CLAMP(kCoarseNeighbour, site + (nx - x) * stride, c.nsites);
 }
 
 // K5: out_r[site][i] = sum_d sum_j M[site][d][j][i] x_r[nb_d(site)][j] for RB

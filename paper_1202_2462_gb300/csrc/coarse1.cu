@@ -18,11 +18,12 @@ __device__ __forceinline__ int c_coord(const CGeom& c, int site, int mu) {
 }
 
 __device__ __forceinline__ int c_site(const CGeom& c, const int (&x)[4]) {
-  return ((x[3] * c.L[2] + x[2]) * c.L[1] + x[1]) * c.L[0] + x[0];
+  return MG_CLAMP(kCoarseSite, ((x[3] * c.L[2] + x[2]) * c.L[1] + x[1]) * c.L[0] + x[0], c.nsites);
 }
 
 // Box index and box coordinates -> the k-th box of a colour ((sum of box coords) mod 2).
 __device__ __forceinline__ int colour_box(const Box4& bx, int k, int colour, int (&bc)[4]) {
+  k = MG_CLAMP(kBlock, k, bx.nboxes >> 1);
   const int half = bx.nb[0] >> 1;
   const int j = k % half;
   int rest = k / half;
@@ -52,7 +53,7 @@ __device__ __forceinline__ int stencil_nb(const CGeom& c, int site, int d) {
   int stride = 1;
   for (int m = 0; m < mu; ++m) stride *= c.L[m];
   const int x = (site / stride) % c.L[mu];
-  return site + (((x + step + c.L[mu]) % c.L[mu]) - x) * stride;
+  return MG_CLAMP(kCoarseNeighbour, site + (((x + step + c.L[mu]) % c.L[mu]) - x) * stride, c.nsites);
 }
 
 // The MR step's scalar products and updates with every product and sum rounded
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(1024) restrict1_kernel(const TX* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R (*red)[4] = reinterpret_cast<R (*)[4]>(smem_raw);               // [nwarps * N1][4]
   const int n2 = c.n2, N0 = n2 / 2;
-  const int rhs = blockIdx.x % nrhs, A = blockIdx.x / nrhs;
+  const int rhs = blockIdx.x % nrhs, A = MG_CLAMP(kAggregate, blockIdx.x / nrhs, ag.nboxes);
   int bc[4];
   {
     int q = A;
@@ -440,6 +441,7 @@ __global__ void prolong1_kernel(const TX* __restrict__ e, TX* __restrict__ out, 
     A += (c_coord(c, site, mu) / ag.b[mu]) * stride;
     stride *= ag.nb[mu];
   }
+  A = MG_CLAMP(kAggregate, A, nsites2);
   const int chi = i / N0;
   const TX* ea = e + (size_t)rhs * nsites2 * 2 * N1 + (size_t)A * 2 * N1 + chi * N1;
   Cplx<R> acc = cmk<R>(0, 0);
@@ -479,7 +481,7 @@ int launch_transfer1(bool restrict_, int prec, const CGeom& c, const Box4& ag, c
 // Modified Gram-Schmidt of W_0..W_{N1-1} on every (aggregate, chirality), in order.
 __global__ void __launch_bounds__(1024) block_gs1_kernel(double2* __restrict__ W, CGeom c, Box4 ag, int N1) {
   __shared__ double red[32][2];
-  const int A = blockIdx.x, chi = blockIdx.y;
+  const int A = MG_CLAMP(kAggregate, blockIdx.x, ag.nboxes), chi = blockIdx.y;
   const int n2 = c.n2, N0 = n2 / 2;
   int bc[4];
   {
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(1024) assemble1_kernel(const double2* __restri
                                                          int N1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double (*red)[4] = reinterpret_cast<double (*)[4]>(smem_raw);     // [nwarps * N1][4]
-  const int A = blockIdx.x, j = blockIdx.y;
+  const int A = MG_CLAMP(kAggregate, blockIdx.x, ag.nboxes), j = blockIdx.y;
   const int n2 = c.n2, N0 = n2 / 2, m2 = 2 * N1;
   const int chi_p = j / N1, k = j % N1;
   int bc[4];

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) coarse_apply_tma_kernel(const float2* __r
   }
   __syncthreads();
   auto tile_src = [&](int t) {
-    const int site = (int)blockIdx.x + (t / 9) * (int)gridDim.x;
+    const int site = MG_CLAMP(kCoarseSite, (int)blockIdx.x + (t / 9) * (int)gridDim.x, c.nsites);
     return M + ((size_t)site * 9 + (t % 9)) * tile;
   };
   if (tid == 0) {
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) coarse_apply_tma_kernel(const float2* __r
   int tfail = -1;
   for (int t = 0; t < T; ++t) {
     const int d = t % 9;
-    const int site = (int)blockIdx.x + (t / 9) * (int)gridDim.x;
+    const int site = MG_CLAMP(kCoarseSite, (int)blockIdx.x + (t / 9) * (int)gridDim.x, c.nsites);
     if (d == 0) {
 #pragma unroll
       for (int a = 0; a < APT; ++a) acc_re[a] = acc_im[a] = 0.f;
@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(256) coarse_apply_tma_kernel(const float2* __r
         const int xc = (site / stride) % c.L[mu];
         nb = site + (((xc + step + c.L[mu]) % c.L[mu]) - xc) * stride;
       }
+      nb = MG_CLAMP(kCoarseNeighbour, nb, c.nsites);
       for (int e = tid; e < RB * n2; e += blockDim.x) xs[e] = xr[(size_t)(e / n2) * fs + (size_t)nb * n2 + e % n2];
     }
     const bool waited = mbar_wait(&bar[t & 1], (uint32_t)((t >> 1) & 1), spins);
@@ -226,11 +227,11 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restr
   // thread 0: all copies of block t into stage t % kStages
   auto issue = [&](int t) {
     const int st = t % kStages;
-    const int site = site_of(t), d = t % 9;
+    const int site = MG_CLAMP(kCoarseSite, site_of(t), c.nsites), d = t % 9;
     uint64_t* b = &bar[st];
     mbar_expect_tx(b, tile_bytes + nr * row_bytes);
     bulk_copy_g2s(stage_tile(st), M + ((size_t)site * 9 + d) * tile, tile_bytes, b);
-    const int nb = neighbour(site, d);
+    const int nb = MG_CLAMP(kCoarseNeighbour, neighbour(site, d), c.nsites);
     float2* xs = stage_x(st);
     for (int r = 0; r < nr; ++r) bulk_copy_g2s(xs + r * xst, xr + (size_t)r * fs + (size_t)nb * n2, row_bytes, b);
   };
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma_kernel(const TM* __restr
   int tfail = -1;
   for (int t = 0; t < T; ++t) {
     const int d = t % 9;
-    const int site = site_of(t);
+    const int site = MG_CLAMP(kCoarseSite, site_of(t), c.nsites);
     if (d == 0) {
 #pragma unroll
       for (int q = 0; q < 2; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
@@ -377,11 +378,11 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
   };
   auto issue = [&](int t) {
     const int st = t % ST;
-    const int site = site_of(t), d = t % 9;
+    const int site = MG_CLAMP(kCoarseSite, site_of(t), c.nsites), d = t % 9;
     uint64_t* b = &bar[st];
     mbar_expect_tx(b, tile_bytes + nr * row_bytes);
     bulk_copy_g2s((void*)stage_tile(st), M + ((size_t)site * 9 + d) * tile, tile_bytes, b);
-    const int nb = neighbour(site, d);
+    const int nb = MG_CLAMP(kCoarseNeighbour, neighbour(site, d), c.nsites);
     unsigned char* xs = smem + st * stage_bytes + tile_bytes;
     for (int r = 0; r < nr; ++r)
       bulk_copy_g2s(xs + (size_t)r * xst * xb, xr + ((size_t)r * fs + (size_t)nb * n2) * xb, row_bytes, b);
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(256) coarse_apply_mma16_kernel(const __half2* 
   int tfail = -1;
   for (int t = 0; t < T; ++t) {
     const int d = t % 9;
-    const int site = site_of(t);
+    const int site = MG_CLAMP(kCoarseSite, site_of(t), c.nsites);
     if (d == 0) {
 #pragma unroll
       for (int q = 0; q < 2; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;

@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "debug.cuh"
+
 namespace sapmg {
 
 // ---------------------------------------------------------------- complex
@@ -122,7 +124,8 @@ __device__ __forceinline__ int block_coord(const Geom& g, int blk, int mu) {
 }
 
 // Neighbour (blk', loc') of (blk, loc) one step in direction mu (step = +1 / -1).
-__device__ __forceinline__ void neighbour(const Geom& g, int blk, int loc, int mu, int step, int& nblk, int& nloc) {
+__device__ __forceinline__ void neighbour_unchecked(const Geom& g, int blk, int loc, int mu, int step, int& nblk,
+                                                    int& nloc) {
   const int ls = loc_stride(mu);
   const int c = (loc >> (2 * mu)) & 3;
   if (step > 0) {
@@ -137,9 +140,17 @@ __device__ __forceinline__ void neighbour(const Geom& g, int blk, int loc, int m
     nloc = loc + 3 * ls;
   }
 }
+__device__ __forceinline__ void neighbour(const Geom& g, int blk, int loc, int mu, int step, int& nblk, int& nloc) {
+  neighbour_unchecked(g, blk, loc, mu, step, nblk, nloc);
+#ifdef MG_DEBUG
+  nblk = MG_CLAMP(kNeighbourBlock, nblk, g.nblocks);
+  nloc = MG_CLAMP(kNeighbourSite, nloc, 256);
+#endif
+}
 
 // The k-th block of colour c ((bx+by+bz+bt) mod 2 == c); nb[0] is even.
 __device__ __forceinline__ int colour_block(const Geom& g, int k, int colour) {
+  k = MG_CLAMP(kColourBlock, k, g.nblocks >> 1);
   const int half = g.nb[0] >> 1;
   const int j = k % half;
   const int rest = k / half;               // = by + nb1*(bz + nb2*bt)
@@ -147,7 +158,8 @@ __device__ __forceinline__ int colour_block(const Geom& g, int k, int colour) {
   const int bz = (rest / g.nb[1]) % g.nb[2];
   const int bt = rest / (g.nb[1] * g.nb[2]);
   const int bx = 2 * j + ((by + bz + bt + colour) & 1);
-  return bx + g.nb[0] * rest;
+  const int blk = bx + g.nb[0] * rest;
+  return MG_CLAMP(kColourBlock, blk, g.nblocks);
 }
 
 // Canonical site index of (blk, loc).

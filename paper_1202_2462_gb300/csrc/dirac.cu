@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256, (sizeof(R) == 4 ? 3 : 1)) dirac_kernel(TS
                                                     int nrhs, double* __restrict__ part) {
   // right-hand side fastest in the grid: the CTAs of one block run back to
   // back and share its links and clover through L2
-  const int blk = blockIdx.x / nrhs;
+  const int blk = MG_CLAMP(kBlock, blockIdx.x / nrhs, g.nblocks);
   const int loc = threadIdx.x;
   const size_t off = (size_t)(blockIdx.x % nrhs) * g.V * 12;
   in += off;

@@ -17,7 +17,7 @@ template <class TG>
 __global__ void __launch_bounds__(256, 2)
     dirac_pair_kernel(float2* __restrict__ out, const float2* __restrict__ in, const TG* __restrict__ U,
                       const TG* __restrict__ A, Geom g, int npairs) {
-  const int blk = blockIdx.x / npairs;
+  const int blk = MG_CLAMP(kBlock, blockIdx.x / npairs, g.nblocks);
   const int loc = threadIdx.x;
   const size_t stride = (size_t)g.V * 12;
   const size_t off = (size_t)(blockIdx.x % npairs) * 2 * stride;

@@ -24,11 +24,12 @@ __device__ __forceinline__ long long canon_index(const Geom& g, const Coord& c) 
 __device__ __forceinline__ void blocked_of(const Geom& g, const Coord& c, int& blk, int& loc) {
   blk = (c.x[0] >> 2) + g.nb[0] * ((c.x[1] >> 2) + g.nb[1] * ((c.x[2] >> 2) + g.nb[2] * (c.x[3] >> 2)));
   loc = (c.x[0] & 3) + 4 * ((c.x[1] & 3) + 4 * ((c.x[2] & 3) + 4 * (c.x[3] & 3)));
+  blk = MG_CLAMP(kBlock, blk, g.nblocks);
 }
 
 __device__ __forceinline__ long long shifted(const Geom& g, Coord c, int mu, int step) {
   c.x[mu] = (c.x[mu] + step + g.L[mu]) % g.L[mu];
-  return canon_index(g, c);
+  return MG_CLAMP(kNeighbourSite, canon_index(g, c), g.V);
 }
 
 // ------------------------------------------------------------ gauge packing

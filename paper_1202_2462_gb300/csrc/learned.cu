@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) gconv_forward_kernel(Geom g, const TG* __
                                                             const float2* __restrict__ x, float2* __restrict__ y,
                                                             int cin) {
   extern __shared__ float2 ws[];                                // [cin][9][16]
-  const int blk = blockIdx.x, a = blockIdx.y, loc = threadIdx.x;
+  const int blk = MG_CLAMP(kBlock, blockIdx.x, g.nblocks), a = blockIdx.y, loc = threadIdx.x;
   const size_t fs = (size_t)g.V * 12;
   for (int e = loc; e < cin * 9 * 16; e += 256) {
     const Cplx<float> w = Io<float, TW>::ldc(W + (size_t)a * cin * 9 * 16 + e);
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) gconv_backward_input_kernel(Geom g, const
                                                                    const float2* __restrict__ gy,
                                                                    float2* __restrict__ gx, int cin, int cout) {
   extern __shared__ float2 ws[];                                // [cout][9][16] for this b
-  const int blk = blockIdx.x, b = blockIdx.y, loc = threadIdx.x;
+  const int blk = MG_CLAMP(kBlock, blockIdx.x, g.nblocks), b = blockIdx.y, loc = threadIdx.x;
   const size_t fs = (size_t)g.V * 12;
   for (int e = loc; e < cout * 9 * 16; e += 256) {
     const int a = e / (9 * 16), r = e % (9 * 16);

@@ -11,7 +11,7 @@ namespace sapmg {
 // v: N fine fields in the blocked layout; phi: [nblocks][2N]; one CTA per block.
 __global__ void __launch_bounds__(256) prolong_v64_kernel(const double2* __restrict__ v, int N, size_t n,
                                                           const double2* __restrict__ phi, double2* __restrict__ out) {
-  const int blk = blockIdx.x, loc = threadIdx.x;
+  const int blk = MG_CLAMP(kBlock, blockIdx.x, n / (12 * 256)), loc = threadIdx.x;
   const double2* ph = phi + (size_t)blk * 2 * N;
   for (int c = 0; c < 12; ++c) {
     const size_t i = ((size_t)blk * 12 + c) * 256 + loc;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) prolong_v64_kernel(const double2* __restr
 __global__ void __launch_bounds__(256) restrict_v64_kernel(const double2* __restrict__ v, int N, size_t n,
                                                            const double2* __restrict__ x, double2* __restrict__ out) {
   __shared__ double red[8][4];
-  const int blk = blockIdx.x, loc = threadIdx.x, w = loc >> 5, lane = loc & 31;
+  const int blk = MG_CLAMP(kBlock, blockIdx.x, n / (12 * 256)), loc = threadIdx.x, w = loc >> 5, lane = loc & 31;
   double2 xs[12];
 #pragma unroll
   for (int c = 0; c < 12; ++c) xs[c] = x[((size_t)blk * 12 + c) * 256 + loc];

@@ -33,6 +33,50 @@ static int fail(int code, const std::string& m) {
   return code;
 }
 
+// ---- device-side index checks (MG_DEBUG builds; debug.cuh)
+namespace dbg {
+const char* kind_name(int kind) {
+  static const char* names[kKinds] = {"none",        "neighbour block",  "neighbour site",
+                                      "block of a colour", "block",      "coarse site",
+                                      "coarse neighbour",  "aggregate",  "bulk-copy alignment"};
+  return (kind > 0 && kind < kKinds) ? names[kind] : "unknown";
+}
+struct ReaderEntry {
+  Reader read;
+  const char* unit;
+};
+static std::vector<ReaderEntry>& readers() {
+  static std::vector<ReaderEntry> r;
+  return r;
+}
+int add_reader(Reader r, const char* unit) {
+  readers().push_back({r, unit});
+  return (int)readers().size();
+}
+// Failed checks of every unit since the last collection (the records are
+// cleared); msg describes the first one.  -1 if a record could not be read.
+static long long collect(std::string* msg) {
+  long long total = 0;
+  for (const ReaderEntry& e : readers()) {
+    unsigned long long first = 0, fails = 0;
+    if (e.read(&first, &fails) != 0) return -1;
+    if (fails && total == 0 && msg) {
+      const char* base = std::strrchr(e.unit, '/');
+      *msg = std::string("device-side index check failed in ") + (base ? base + 1 : e.unit) + ": " +
+             kind_name((int)(first >> 56)) + " " + std::to_string((int)(uint32_t)first) + " out of range (line " +
+             std::to_string((int)((first >> 32) & 0xffffff)) + ")";
+    }
+    total += (long long)fails;
+  }
+  if (total && msg) *msg += ", " + std::to_string(total) + " failed check(s) in all";
+  return total;
+}
+#ifdef MG_DEBUG
+// one check of v against [0, n) by one thread, with no memory access
+__global__ void selftest_kernel(long long v, long long n) { (void)MG_CHECK(kBlock, v, n); }
+#endif
+}  // namespace dbg
+
 #define TRY(x)                  \
   do {                          \
     int rc__ = (x);             \
@@ -313,6 +357,12 @@ static int check_device_error(mg_ctx* c) {
     SAPMG_CUDA_TRY(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->s));
     return fail(MG_ERR_TIMEOUT, "a bounded device wait gave up");
   }
+#ifdef MG_DEBUG
+  std::string msg;
+  const long long n = dbg::collect(&msg);
+  if (n < 0) return fail(MG_ERR_CUDA, "could not read the device-side index checks");
+  if (n > 0) return fail(MG_ERR_BOUNDS, msg);
+#endif
   return MG_OK;
 }
 
@@ -2490,6 +2540,32 @@ int mg_get_history(mg_ctx* c, double* out, int max_entries) {
 int mg_sync(mg_ctx* c) {
   if (!c) return fail(MG_ERR_ARG, "bad argument");
   return check_device_error(c);
+}
+
+int mg_debug_check(long long value, long long bound) {
+#ifdef MG_DEBUG
+  dbg::selftest_kernel<<<1, 1>>>(value, bound);
+  count_launches(1);
+  SAPMG_CUDA_TRY(cudaGetLastError());
+  return MG_OK;
+#else
+  (void)value;
+  (void)bound;
+  return fail(MG_ERR_STATE, "mg_debug_check needs the MG_DEBUG build");
+#endif
+}
+
+long long mg_debug_failures(void) {
+#ifdef MG_DEBUG
+  SAPMG_CUDA_TRY(cudaDeviceSynchronize());
+  std::string msg;
+  const long long n = dbg::collect(&msg);
+  if (n < 0) return fail(MG_ERR_CUDA, "could not read the device-side index checks");
+  if (n > 0) g_err = msg;
+  return n;
+#else
+  return -1;
+#endif
 }
 
 int mg_probe_peaks(void* stream, double* fp32_tflops, double* fp32x2_tflops, double* smem_gbs) {

@@ -92,3 +92,22 @@ def test_new_entry_points_reject_bad_arguments_on_host():
     assert lib.mg_harmonic_ritz(0, None, None, None) == b.MG_ERR_ARG
     assert lib.mg_eigh(0, None, None, None) == b.MG_ERR_ARG
     assert len(lib.mg_last_error()) > 0
+
+
+def test_release_build_has_no_device_index_checks():
+    """mg_debug_failures and mg_debug_check answer without a device in the
+    release build: no checks compiled (-1), and the self-check refused."""
+    b = _lib()
+    if b.LIB_PATH.endswith("libsapmg_debug.so"):
+        pytest.skip("the MG_DEBUG build is loaded")
+    assert b.lib().mg_debug_failures() == -1
+    assert b.lib().mg_debug_check(5, 3) == b.MG_ERR_STATE
+
+
+def test_debug_build_exports_the_same_entry_points():
+    from paper_1202_2462_gb300 import _build
+    if not os.path.exists(_build.LIB_DEBUG):
+        pytest.skip("libsapmg_debug.so not built (python -m paper_1202_2462_gb300._build --debug)")
+    handle = ctypes.CDLL(_build.LIB_DEBUG)
+    missing = [n for n in declared_functions() if not hasattr(handle, n)]
+    assert not missing, missing
