@@ -168,6 +168,42 @@ def test_fgmres_restarted_converges():
     assert hist[-1] <= 1e-11
 
 
+def _min_residual_step(a, m_pre, r, k):
+    """M y with y minimising ||r - A M y|| over K_k(A M, r): least squares on
+    the explicit power basis (independent of any Arnoldi process)."""
+    am = a @ m_pre
+    basis = [r]
+    for _ in range(k - 1):
+        basis.append(am @ basis[-1])
+    kr = np.stack(basis, axis=1)
+    coef, *_ = np.linalg.lstsq(am @ kr, r, rcond=None)
+    return m_pre @ (kr @ coef)
+
+
+def test_fgmres_restart_cycles_are_krylov_minimisers():
+    """Restarted flexible GMRES(m) with a fixed linear preconditioner M (Sec. 2,
+    Sec. 4): every cycle adds the minimiser of the residual over
+    M K_m(A M, r) for the true residual r at the restart, and the history
+    holds the true residuals at the restarts."""
+    a = _rand_matrix(30, 80)
+    m_pre = np.eye(30) + 0.3 * _rand_matrix(30, 81)
+    b = _rand_matrix(30, 82)[:, 0]
+    m = 3
+    x_ref = np.zeros(30, dtype=np.complex128)
+    hist_ref = []
+    for cycles in (1, 2, 3):
+        x, it, hist, ok = fgmres(lambda v: a @ v, lambda v: m_pre @ v, b, m, 1e-14, m * cycles)
+        r = b - a @ x_ref
+        hist_ref.append(np.linalg.norm(r) / np.linalg.norm(b))
+        x_ref = x_ref + _min_residual_step(a, m_pre, r, m)
+        assert it == m * cycles and not ok
+        assert np.max(np.abs(x - x_ref)) < 1e-10 * np.max(np.abs(x_ref))
+        assert np.allclose(hist[:-1], hist_ref, rtol=1e-10, atol=0)
+        assert abs(hist[-1] - np.linalg.norm(b - a @ x_ref) / np.linalg.norm(b)) < 1e-12
+    # a restart that forgot the previous cycles' x, or restarted from b, would differ
+    assert np.linalg.norm(b - a @ x_ref) < 0.9 * np.linalg.norm(b - a @ _min_residual_step(a, m_pre, b, m))
+
+
 def test_global_orthonormalise():
     v = orthonormalise(list(synth.test_vector_draw((2, 2, 2, 2), 4, 68)))
     g = np.array([[np.vdot(a, b) for b in v] for a in v])
