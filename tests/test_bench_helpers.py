@@ -35,3 +35,32 @@ def test_reported_kernel_names_exist():
         for name in found:
             # a __global__ function of that name (launch bounds and line breaks in between)
             assert re.search(r"__global__[^;{]*?\b" + name + r"\s*\(", src, re.S), (family, name)
+
+
+class _DoneProcess:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_summary():
+    """The clocks summary of the bench line from nvidia-smi's CSV rows (index,
+    SM MHz, max SM MHz, power, active mask, then the four reasons): median SM
+    clock under load, the maximum, and every throttle reason seen active."""
+    cs = bench.ClockSampler.__new__(bench.ClockSampler)
+    cs.proc = _DoneProcess()
+    cs.lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1399.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    out = cs.stop()
+    assert out["sm_mhz"] == 2070 and out["sm_max_mhz"] == 2070 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    cs.lines = ["0, 1500, 2070, 800, 0x8, Active, Not Active, Active, Not Active"]
+    out = cs.stop()
+    assert out["sm_mhz"] == 1500 and out["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
